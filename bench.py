@@ -1,0 +1,362 @@
+"""Benchmark: deep + shallow column convection over 884,736 columns x 30 levels.
+
+One step = one call of the fused deep->shallow path over the whole grid (the
+768 x 1152 resolution of the paper's R3 grid, Sec. V-A, with a clustered 30%
+convecting fraction), inputs resident in HBM (425 MB of FP64 profiles, larger
+than the 129 MB L2, so no L2 flush is needed between steps).
+
+Arms:
+  default              the CUDA library (libconvgb.so) through the C ABI;
+  --impl reference     the FP64 CPU oracle on this machine's cores (OpenMP,
+                       dynamic schedule) over a bounded sample of the grid.
+
+Prints one JSON line (rank 0).  Multi-GPU (torchrun): every rank processes its
+own full grid, no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "convection columns/s (deep+shallow, 884,736x30)"
+UNIT = "columns/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--path", default="plain", choices=["plain", "compact"])
+    p.add_argument("--frac", type=float, default=0.30)
+    p.add_argument("--nlat", type=int, default=768)
+    p.add_argument("--nlon", type=int, default=1152)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+def op_counts(workload: str):
+    path = os.path.join(ROOT, "oracle", "op_counts.json")
+    with open(path) as fh:
+        return json.load(fh)["workloads"][workload]["total_per_column"]
+
+
+def fp64_alu_roofline(counts, kernel_s, n_cols, L):
+    """Arithmetic roofline of an FP64 kernel: the time the algorithmic operation
+    counts need at the device's measured FP64 throughput per operation class
+    (adds and multiplies paired into FMAs), expressed in FMA-equivalent FLOP/s."""
+    r = {op: L.op_rate(op, L.CONV_ARITH_FP64) for op in
+         (L.CONV_OP_FMA, L.CONV_OP_EXP, L.CONV_OP_LOG, L.CONV_OP_DIV, L.CONV_OP_POW)}
+    t_col = (max(counts["add"], counts["mul"]) / r[L.CONV_OP_FMA]
+             + counts["div"] / r[L.CONV_OP_DIV] + counts["exp"] / r[L.CONV_OP_EXP]
+             + counts["log"] / r[L.CONV_OP_LOG] + counts["pow"] / r[L.CONV_OP_POW])
+    t_bound = t_col * n_cols
+    peak = 2.0 * r[L.CONV_OP_FMA]  # FLOP/s, one FMA = 2 FLOP
+    achieved = peak * t_bound / kernel_s
+    rates = {"fma": r[L.CONV_OP_FMA], "exp": r[L.CONV_OP_EXP], "log": r[L.CONV_OP_LOG],
+             "div": r[L.CONV_OP_DIV], "pow": r[L.CONV_OP_POW]}
+    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s (FP64 FMA-equivalent)", "frac": t_bound / kernel_s,
+            "traffic": None, "peak_source": "measured FP64 FMA rate (conv_bench_op_rate)",
+            "op_rates_per_s": rates}
+
+
+def hbm_bytes_per_column(pver, real_bytes):
+    # read T, q, ps; write deep and shallow dTdt, dqdt; 4 doubles + 5 int32 per scheme
+    return 2 * pver * real_bytes + 8 + 4 * pver * real_bytes + 2 * (4 * 8 + 5 * 4)
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_rate(g, budget_s):
+    """Columns/s of the FP64 oracle on all host cores over a strided sample of g."""
+    from oracle import oracle as O
+    from paper_1711_00289_gb300 import soundings as S
+
+    threads = os.cpu_count() or 1
+
+    def sample(stride):
+        return S.Columns(g.name, g.pver, np.ascontiguousarray(g.T[:, ::stride]),
+                         np.ascontiguousarray(g.q[:, ::stride]), g.ps[::stride].copy(),
+                         g.hyai, g.hybi)
+
+    probe = sample(max(1, g.n_cols // 20000))
+    t0 = time.perf_counter()
+    O.deep_shallow(probe, threads=threads)
+    rate = probe.n_cols / (time.perf_counter() - t0)
+    want = min(g.n_cols, max(probe.n_cols, int(rate * budget_s)))
+    sub = sample(max(1, g.n_cols // want))
+    # repeat the sample until the time budget is spent (the whole grid may take
+    # well under it on a many-core host)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        O.deep_shallow(sub, threads=threads)
+        done += sub.n_cols
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return done / el, done, threads, el
+
+
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------------ arms
+def reference_arm(args, rank):
+    from oracle import oracle as O  # noqa: F401  (reference arm = the oracle)
+    from paper_1711_00289_gb300 import soundings as S
+
+    if rank != 0:
+        return
+    g = S.clustered_grid(args.frac, args.nlat, args.nlon)
+    per_step = max(1.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        rate, ncols, threads, el = cpu_oracle_rate(g, per_step)
+        if i >= args.warmup:
+            vals.append(rate)
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * g.n_cols / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": g.name, "columns": g.n_cols, "levels": g.pver,
+                       "convecting_fraction": args.frac, "dt_s": g.dt},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{ncols} column evaluations per step (strided sample of the grid, "
+                                       f"repeated), OpenMP dynamic(8) on {threads} threads, "
+                                       f"{cpu_model()}"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ours_arm(args, rank, world, local_rank):
+    import torch
+
+    from paper_1711_00289_gb300 import _lib as L
+    from paper_1711_00289_gb300 import api
+    from paper_1711_00289_gb300 import soundings as S
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    g = S.clustered_grid(args.frac, args.nlat, args.nlon)
+    n, pver = g.n_cols, g.pver
+    prec = args.precision
+    rd = api.real_dtype(prec)
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    T = torch.tensor(g.T, device=dev).to(rd)
+    q = torch.tensor(g.q, device=dev).to(rd)
+    ps = torch.tensor(g.ps, device=dev)
+    od = api.new_outputs(pver, n, prec, dev)
+    os_ = api.new_outputs(pver, n, prec, dev)
+    ws = api.Workspace(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        api.deep_shallow(T, q, ps, vg, dt=g.dt, precision=prec, path=args.path, out_deep=od,
+                         out_shallow=os_, workspace=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    launches_per_step = 1 if args.path == "plain" else 3
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+    value = world * n / (ms * 1e-3)
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        hT = torch.tensor(g.T).to(rd).pin_memory()
+        hq = torch.tensor(g.q).to(rd).pin_memory()
+        hps = torch.tensor(g.ps).pin_memory()
+        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
+                    for o in (od, os_) for k, v in o.items()}
+        names = [(i, k) for i, o in enumerate((od, os_)) for k in o]
+        hout = {(i, k): torch.empty(o[k].shape, dtype=o[k].dtype).pin_memory()
+                for i, o in enumerate((od, os_)) for k in o}
+        del host_out
+
+        def e2e_step():
+            T.copy_(hT, non_blocking=True)
+            q.copy_(hq, non_blocking=True)
+            ps.copy_(hps, non_blocking=True)
+            step()
+            for (i, k) in names:
+                hout[(i, k)].copy_((od, os_)[i][k], non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        k2 = max(2, args.steps // 2)
+        e0.record(stream)
+        for _ in range(k2):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2 = e0.elapsed_time(e1) / k2
+        h2d = sum(x.numel() * x.element_size() for x in (hT, hq, hps))
+        d2h = sum(v.numel() * v.element_size() for v in hout.values())
+        e2e = {"value": world * n / (ms2 * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        return
+    roof = None
+    if prec == "fp64":
+        roof = fp64_alu_roofline(op_counts(g.name), ms * 1e-3, n, L)
+    roof = roof or {}
+    roof["hbm_algorithmic_bytes_per_column"] = hbm_bytes_per_column(pver, 8 if prec == "fp64"
+                                                                    else 4)
+    roof["hbm_frac_of_measured"] = (roof["hbm_algorithmic_bytes_per_column"] * n / (ms * 1e-3)
+                                    / 1e9 / measured_hbm())
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, ncols, threads, el = cpu_oracle_rate(g, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{ncols} column evaluations of this grid (strided sample, repeated) "
+                         f"in {el:.1f} s, FP64 oracle, OpenMP dynamic(8) on {threads} threads, "
+                         f"{cpu_model()}"}
+    act = int(((od["flags"] & 2) > 0).sum().item())
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": g.name, "columns": n, "levels": pver,
+                       "convecting_fraction": args.frac, "deep_active_columns": act,
+                       "precision": prec, "path": args.path, "dt_s": g.dt,
+                       "l2": "inputs (%d MB) larger than L2; no flush" % (
+                           (T.numel() + q.numel()) * T.element_size() // 2**20),
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    ours_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * conv.h -- C ABI of the GB300 column-convection library (libconvgb.so).
+ *
+ * What is computed.  The physics step of the atmosphere model applies deep
+ * convection and then shallow convection to every vertical column, each column
+ * independently of all others (paper Sec. II-A and Alg. 1).  Deep convection is
+ * the Zhang-McFarlane mass-flux scheme with an entrainment loop and a
+ * precipitation loop over levels that each invert a conserved thermodynamic
+ * variable (Alg. 2); shallow convection is the University of Washington plume,
+ * which leaves a column at several thermodynamic checks and then zeroes that
+ * column's outputs (Alg. 3).  The paper gives no equations; this library
+ * implements the column equations it freezes (listed with every reading of the
+ * paper in the design notes): launch level of maximum moist static energy,
+ * Newton LCL, undilute parcel and CAPE trigger, entraining updraft with
+ * implicit rain, saturated downdraft, flux-form tendencies, CAPE-relaxation
+ * closure with a moisture limiter, and a CIN-closed shallow plume.
+ *
+ * Data layout (the paper's transposed, padded layout, Sec. III-C, turned for
+ * a GPU: columns innermost so that a warp reads 32 adjacent columns of one
+ * level in one coalesced access):
+ *   profile arrays  [pver][ld], element (k, i) at k*ld + i,
+ *                   k = 0 model top .. pver-1 lowest layer, i = column;
+ *   column arrays   [ld];
+ *   ld >= n_cols (a multiple of 32 is recommended); columns n_cols..ld-1 are
+ *   neither read nor written.
+ *
+ * Precision.  CONV_FP64: T, q, dTdt, dqdt are double; everything is computed in
+ * FP64.  CONV_MIXED: T, q, dTdt, dqdt are float and the bulk of the arithmetic
+ * is FP32, with FP64 kept for the LCL Newton iteration, the CAPE integral that
+ * drives the trigger and the column conservation sums.  Column scalars (ps,
+ * lambda, tau, prec, cape, mb, cons_err) are double in both modes.
+ *
+ * Ownership and blocking.  Every pointer in conv_in / conv_out / workspace is a
+ * DEVICE pointer owned by the caller; hyai/hybi in conv_grid are HOST pointers
+ * read during the call.  Run calls are asynchronous on the given stream: they
+ * validate arguments on the host, enqueue kernels and return.  The library
+ * never allocates on a run path and never synchronises the stream.  Calls on
+ * different streams with disjoint buffers may run concurrently.
+ *
+ * Errors.  Argument errors are detected on the host before anything is
+ * enqueued (CONV_ERR_ARG / CONV_ERR_WORKSPACE / CONV_ERR_UNSUPPORTED); a launch
+ * failure returns CONV_ERR_CUDA.  Data problems never abort: they are reported
+ * per column in `flags`:
+ *   bit 0  CONV_FLAG_TRIGGERED  deep: CAPE > capelmt; shallow: passed exits E1-E3
+ *   bit 1  CONV_FLAG_ACTIVE     scheme produced non-zero tendencies
+ *   bit 2  CONV_FLAG_LIMITED    deep mass flux cut by the q >= q_min limiter
+ *   bit 3  CONV_FLAG_NEWTON     a Newton solve's last correction exceeded 1e-4 K
+ *   bit 4  CONV_FLAG_BADINPUT   T outside (100, 400) K, q outside [0, 0.1),
+ *                               ps outside (5e4, 1.2e5) Pa or not finite;
+ *                               all outputs of the column are zero
+ *   bits 8-10 (shallow)         exit stage: 1 LCL too high, 2 no LFC,
+ *                               3 CIN too large, 4 plume dies at the LCL; 0 none
+ */
+#ifndef CONV_H
+#define CONV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* conv_stream; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  CONV_OK = 0,
+  CONV_ERR_ARG = 1,         /* invalid argument (NULL, size, range)          */
+  CONV_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed          */
+  CONV_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned    */
+  CONV_ERR_UNSUPPORTED = 4, /* valid request this build does not implement   */
+  CONV_ERR_TIMEOUT = 5      /* reserved: a bounded device wait gave up       */
+} conv_status;
+
+typedef enum { CONV_FP64 = 0, CONV_MIXED = 1 } conv_precision;
+
+enum {
+  CONV_FLAG_TRIGGERED = 1,
+  CONV_FLAG_ACTIVE = 2,
+  CONV_FLAG_LIMITED = 4,
+  CONV_FLAG_NEWTON = 8,
+  CONV_FLAG_BADINPUT = 16,
+  CONV_EXIT_SHIFT = 8
+};
+
+#define CONV_MAX_LEVELS 32
+
+/* Vertical grid.  Interface pressure p_i = hyai[i]*p0 + hybi[i]*ps for
+ * i = 0 (model top) .. pver (surface); mid-layer p_k = (p_k + p_k+1)/2.
+ * hyai/hybi: HOST arrays of pver+1 doubles, copied into kernel parameters. */
+typedef struct {
+  int32_t pver;   /* 4 .. 32 levels                                   */
+  int32_t n_cols; /* columns to process (>= 0)                        */
+  int32_t ld;     /* leading dimension of profile arrays, >= n_cols   */
+  int32_t reserved;
+  const double* hyai;
+  const double* hybi;
+  double p0; /* Pa */
+} conv_grid;
+
+/* Deep scheme parameters (defaults in brackets; conv_deep_defaults fills them). */
+typedef struct {
+  double capelmt;        /* CAPE trigger threshold, J/kg [70]                      */
+  double lambda_default; /* entrainment rate at the launch level, 1/m [1e-3]       */
+  double tau_default;    /* CAPE relaxation time, s [3600]                         */
+  double c0;             /* rain conversion rate, 1/m [2e-3]                       */
+  double alpha_dd;       /* downdraft evaporation fraction [0.2]                   */
+  double p_launch_min;   /* launch level searched where p_mid >= this, Pa [6e4]    */
+  double p_top_lim;      /* no plume/parcel above p_mid < this, Pa [4e3]           */
+  double q_min;          /* limiter floor on q + dt dq/dt, kg/kg [1e-12]           */
+  double ent_zscale;     /* entrainment decays as zscale/(dz + zscale), m [1000]   */
+  int32_t n_newton_lcl;  /* LCL Newton steps [6]                                   */
+  int32_t n_newton_h;    /* moist-inversion Newton steps after the first [4]       */
+} conv_deep_params;
+
+/* Shallow scheme parameters. */
+typedef struct {
+  double eps_s;     /* plume mixing rate, 1/m [2e-3]                           */
+  double tke;       /* boundary-layer TKE, m2/s2 [1]                           */
+  double c_m;       /* cloud-base mass-flux coefficient [0.03]                 */
+  double cin_scale; /* CIN e-folding in units of tke [10]                      */
+  double cin_max;   /* exit E3 above this CIN, J/kg [50]                       */
+  double a_w;       /* buoyancy coefficient of the w2 equation [1]             */
+  double b_w;       /* drag coefficient of the w2 equation [2]                 */
+  double ql_crit;   /* liquid left in the plume, kg/kg [1e-3]                  */
+  double p_lcl_min; /* exit E1 if the LCL pressure is below, Pa [7e4]          */
+  double p_lfc_min; /* exit E2 if no LFC at p >= this, Pa [5e4]                */
+  double p_top_lim; /* Pa [4e3]                                                */
+  int32_t n_newton_lcl;
+  int32_t n_newton_h;
+} conv_shallow_params;
+
+/* Inputs (DEVICE pointers). T,q: [pver][ld] double (FP64) or float (MIXED);
+ * ps, lambda, tau: [ld] double.  lambda/tau may be NULL (parameter defaults). */
+typedef struct {
+  const void* T;
+  const void* q;
+  const double* ps;
+  const double* lambda;
+  const double* tau;
+} conv_in;
+
+/* Outputs of one scheme (DEVICE pointers).  dTdt (K/s), dqdt (kg/kg/s):
+ * [pver][ld], element type as T.  prec (kg m-2 s-1), cape (deep: CAPE J/kg;
+ * shallow: CIN J/kg), mb (cloud-base mass flux, kg m-2 s-1), cons_err (relative
+ * column enthalpy + water residual, computed in FP64): [ld] double.  flags and
+ * level indices: [ld] int32; kb = launch/source layer, klcl = LCL layer,
+ * ktop = cloud-top layer (-1 unless active), kaux = deep: downdraft top layer
+ * (-1 unless active) / shallow: LFC layer (-1 if none).
+ * dTdt, dqdt, prec and flags are required; the rest may be NULL. */
+typedef struct {
+  void* dTdt;
+  void* dqdt;
+  double* prec;
+  int32_t* flags;
+  int32_t* kb;
+  int32_t* klcl;
+  int32_t* ktop;
+  int32_t* kaux;
+  double* cape;
+  double* mb;
+  double* cons_err;
+} conv_out;
+
+/* Kernel variant.  CONV_PATH_PLAIN: one thread per column runs the whole scheme
+ * (no compaction; the FP64 baseline).  CONV_PATH_COMPACT: a trigger pass over
+ * all columns compacts the convecting ones into device queues (warp ballot,
+ * one atomic per warp) and plume passes run only over the queues.
+ * block_threads 0 = library default. */
+typedef enum { CONV_PATH_AUTO = 0, CONV_PATH_PLAIN = 1, CONV_PATH_COMPACT = 2 } conv_path;
+typedef struct {
+  int32_t path;
+  int32_t block_threads;
+  int32_t reserved0;
+  int32_t reserved1;
+} conv_launch;
+
+/* Fill parameter structs with the defaults listed above. */
+void conv_deep_defaults(conv_deep_params* p);
+void conv_shallow_defaults(conv_shallow_params* p);
+
+/* Human-readable name of a status code (static string). */
+const char* conv_status_str(conv_status s);
+
+/* Device workspace a run call needs for this grid, precision and launch
+ * (launch may be NULL = defaults).  Zero for the plain path.  The workspace
+ * must be 256-byte aligned; its contents need not be initialised. */
+size_t conv_workspace_bytes(const conv_grid* grid, conv_precision prec,
+                            const conv_launch* launch);
+
+/* Deep convection (Alg. 2) on the state in `in`; writes `out`. dt (s) is used
+ * by the moisture limiter.  Returns after enqueueing on `stream`. */
+conv_status conv_deep_run(const conv_grid* grid, const conv_in* in, const conv_deep_params* par,
+                          double dt, conv_precision prec, const conv_out* out,
+                          const conv_launch* launch, void* ws, size_t ws_bytes,
+                          conv_stream stream);
+
+/* Shallow convection (Alg. 3) on the state in `in` (lambda/tau ignored). */
+conv_status conv_shallow_run(const conv_grid* grid, const conv_in* in,
+                             const conv_shallow_params* par, conv_precision prec,
+                             const conv_out* out, const conv_launch* launch, void* ws,
+                             size_t ws_bytes, conv_stream stream);
+
+/* Deep convection, then shallow convection on T + dt*dTdt_deep, q + dt*dqdt_deep
+ * (the order of Alg. 1), fused: the intermediate state never leaves the chip. */
+conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
+                                  const conv_deep_params* dpar, const conv_shallow_params* spar,
+                                  double dt, conv_precision prec, const conv_out* deep_out,
+                                  const conv_out* shallow_out, const conv_launch* launch,
+                                  void* ws, size_t ws_bytes, conv_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONV_H */

@@ -1,0 +1,45 @@
+/*
+ * conv_bench.h -- measurement support of libconvgb.so (no counterpart in the
+ * paper, whose timings are wall-clock seconds of CESM loops, Sec. V).
+ *
+ * The column schemes are bound by floating-point throughput, not by a dense
+ * contraction or by HBM, so the roofline of a kernel is the time its
+ * algorithmic operation counts need at the device's measured per-operation
+ * throughput.  This entry point measures that throughput on the current device.
+ */
+#ifndef CONV_BENCH_H
+#define CONV_BENCH_H
+
+#include "conv.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CONV_OP_FMA = 0, /* a*b + c              */
+  CONV_OP_EXP = 1, /* exp                  */
+  CONV_OP_LOG = 2, /* log                  */
+  CONV_OP_DIV = 3, /* a / b                */
+  CONV_OP_POW = 4, /* pow(a, b)            */
+  CONV_OP_SQRT = 5 /* sqrt                 */
+} conv_op;
+
+typedef enum {
+  CONV_ARITH_FP64 = 0,      /* double, library functions                       */
+  CONV_ARITH_FP32 = 1,      /* float, accurate library functions               */
+  CONV_ARITH_FP32_FAST = 2  /* float, hardware approximations (__expf, ...)    */
+} conv_arith;
+
+/* Measure how many `op` evaluations per second the current device sustains in
+ * `arith` (a grid of 8 independent dependency chains per thread, sized to fill
+ * every SM; `iters` evaluations per chain; timed with CUDA events on a private
+ * stream, synchronised).  Writes the rate to *ops_per_s.  Allocates and frees
+ * 8 MB of device memory internally.  CONV_ERR_ARG for an unknown op/arith or
+ * iters < 1; CONV_ERR_CUDA on a CUDA failure. */
+conv_status conv_bench_op_rate(int op, int arith, int iters, double* ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CONV_BENCH_H */

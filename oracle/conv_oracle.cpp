@@ -906,9 +906,13 @@ int oracle_deep_shallow(int n_cols, int pver, int ld, const double* hyai, const 
                         lambda ? lambda[i] : DP.lambda_default, tau ? tau[i] : DP.tau_default,
                         DP, dt, s);
     store_deep(s, pver, ld, i, deep);
+    // Shallow input: the deep-updated state, humidity floored at zero (the deep
+    // limiter keeps it >= q_min up to rounding of q - (q - q_min)); a column the
+    // deep scheme rejected as bad input is passed on unchanged.
     for (int k = 0; k < pver; ++k) {
       T2[k] = Tc[k] + dt * s.dTdt[k];
       q2[k] = qc[k] + dt * s.dqdt[k];
+      if (!s.bad && q2[k] < 0.0) q2[k] = 0.0;
     }
     ShalState<double> t;
     shallow_column<double>(pver, hyai, hybi, p0, T2, q2, ps[i], SP, t);
@@ -978,6 +982,7 @@ int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const dou
     for (int k = 0; k < pver; ++k) {
       T2[k] = Tc[k] + dt * s.dTdt[k].v;
       q2[k] = qc[k] + dt * s.dqdt[k].v;
+      if (!s.bad && q2[k].v < 0.0) q2[k] = Cnt(0.0);
     }
     ShalState<Cnt> t;
     shallow_column<Cnt>(pver, hyai, hybi, p0, T2, q2, Cnt(ps[i]), SP, t);

@@ -1,0 +1,212 @@
+"""PyTorch-facing API over the C ABI (device memory and streams come from torch;
+every step of the computation runs in libconvgb.so kernels).
+
+Profile tensors are level-major ``[pver, ld]`` (columns innermost, the layout of
+include/conv.h); column tensors are ``[ld]``.  ``ld`` may exceed the number of
+columns processed (``n_cols``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_OUT_FIELDS = ("dTdt", "dqdt", "prec", "flags", "kb", "klcl", "ktop", "kaux", "cape", "mb",
+               "cons_err")
+_PREC = {"fp64": L.CONV_FP64, "mixed": L.CONV_MIXED}
+_PATH = {"auto": L.CONV_PATH_AUTO, "plain": L.CONV_PATH_PLAIN, "compact": L.CONV_PATH_COMPACT}
+
+
+def real_dtype(precision: str) -> torch.dtype:
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _require_cuda(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def new_outputs(pver: int, ld: int, precision: str, device="cuda") -> dict:
+    """Allocate one scheme's output tensors."""
+    rd = real_dtype(precision)
+    f64, i32 = torch.float64, torch.int32
+    return dict(dTdt=torch.empty((pver, ld), dtype=rd, device=device),
+                dqdt=torch.empty((pver, ld), dtype=rd, device=device),
+                prec=torch.empty(ld, dtype=f64, device=device),
+                flags=torch.empty(ld, dtype=i32, device=device),
+                kb=torch.empty(ld, dtype=i32, device=device),
+                klcl=torch.empty(ld, dtype=i32, device=device),
+                ktop=torch.empty(ld, dtype=i32, device=device),
+                kaux=torch.empty(ld, dtype=i32, device=device),
+                cape=torch.empty(ld, dtype=f64, device=device),
+                mb=torch.empty(ld, dtype=f64, device=device),
+                cons_err=torch.empty(ld, dtype=f64, device=device))
+
+
+def _out_struct(o: dict, pver: int, ld: int, precision: str) -> L.Out:
+    rd = real_dtype(precision)
+    for k in ("dTdt", "dqdt"):
+        _require_cuda(o[k], k, rd, (pver, ld))
+    for k in ("prec", "cape", "mb", "cons_err"):
+        if o.get(k) is not None:
+            _require_cuda(o[k], k, torch.float64, (ld,))
+    for k in ("flags", "kb", "klcl", "ktop", "kaux"):
+        if o.get(k) is not None:
+            _require_cuda(o[k], k, torch.int32, (ld,))
+    return L.Out(*[_ptr(o.get(k)) for k in _OUT_FIELDS])
+
+
+class VerticalGrid:
+    """Hybrid interface coefficients (host arrays of pver+1 doubles) and p0."""
+
+    def __init__(self, hyai, hybi, p0: float = 1.0e5):
+        self.hyai = np.ascontiguousarray(hyai, dtype=np.float64)
+        self.hybi = np.ascontiguousarray(hybi, dtype=np.float64)
+        if self.hyai.shape != self.hybi.shape or self.hyai.ndim != 1:
+            raise ValueError("hyai/hybi must be 1-D of equal length")
+        self.pver = self.hyai.shape[0] - 1
+        self.p0 = float(p0)
+
+    def struct(self, n_cols: int, ld: int) -> L.Grid:
+        dp = C.POINTER(C.c_double)
+        return L.Grid(self.pver, int(n_cols), int(ld), 0, self.hyai.ctypes.data_as(dp),
+                      self.hybi.ctypes.data_as(dp), self.p0)
+
+
+def _launch(path: str, block_threads: int = 0) -> L.Launch:
+    return L.Launch(_PATH[path], int(block_threads), 0, 0)
+
+
+def workspace_bytes(vgrid: VerticalGrid, n_cols: int, ld: int, precision="fp64",
+                    path="plain") -> int:
+    g = vgrid.struct(n_cols, ld)
+    lc = _launch(path)
+    return int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
+
+
+class Workspace:
+    """Caller-owned device workspace, grown on demand (allocation happens here, in
+    torch, never inside the library's run calls)."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int):
+        if nbytes == 0:
+            return None, 0
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.buf.data_ptr()
+        off = (-base) % 256
+        return C.c_void_p(base + off), self.buf.numel() - off
+
+
+_default_ws = {}
+
+
+def _ws_for(device, ws: Workspace | None):
+    if ws is not None:
+        return ws
+    key = str(device)
+    if key not in _default_ws:
+        _default_ws[key] = Workspace(device)
+    return _default_ws[key]
+
+
+def _common(T, q, ps, vgrid, n_cols, precision, lam, tau):
+    if precision not in _PREC:
+        raise ValueError(f"precision must be one of {list(_PREC)}")
+    rd = real_dtype(precision)
+    if T.dim() != 2:
+        raise ValueError("T must be [pver, ld]")
+    pver, ld = T.shape
+    if pver != vgrid.pver:
+        raise ValueError(f"T has {pver} levels, vertical grid has {vgrid.pver}")
+    _require_cuda(T, "T", rd, (pver, ld))
+    _require_cuda(q, "q", rd, (pver, ld))
+    _require_cuda(ps, "ps", torch.float64, (ld,))
+    for name, t in (("lam", lam), ("tau", tau)):
+        if t is not None:
+            _require_cuda(t, name, torch.float64, (ld,))
+    n = ld if n_cols is None else int(n_cols)
+    inp = L.In(_ptr(T), _ptr(q), _ptr(ps), _ptr(lam), _ptr(tau))
+    return pver, ld, n, inp
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64",
+                 lam=None, tau=None, deep_params=None, shallow_params=None, path="plain",
+                 block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
+                 workspace: Workspace | None = None, stream=None):
+    """Deep then shallow convection (Alg. 1 order) in one fused call.
+
+    Returns ``(deep_out, shallow_out)`` dicts of output tensors."""
+    pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
+    od = out_deep if out_deep is not None else new_outputs(pver, ld, precision, T.device)
+    os_ = out_shallow if out_shallow is not None else new_outputs(pver, ld, precision, T.device)
+    dp = deep_params or L.deep_defaults()
+    sp = shallow_params or L.shallow_defaults()
+    g = vgrid.struct(n, ld)
+    lc = _launch(path, block_threads)
+    nb = int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
+    wp, wn = _ws_for(T.device, workspace).get(nb)
+    st = L.lib().conv_deep_shallow_run(
+        C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp), float(dt), _PREC[precision],
+        C.byref(_out_struct(od, pver, ld, precision)),
+        C.byref(_out_struct(os_, pver, ld, precision)), C.byref(lc), wp, wn, _stream(stream))
+    L.check(st, "conv_deep_shallow_run")
+    return od, os_
+
+
+def deep(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64", lam=None,
+         tau=None, params=None, path="plain", block_threads=0, n_cols=None, out=None,
+         workspace: Workspace | None = None, stream=None):
+    """Deep convection only (Alg. 2)."""
+    pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
+    o = out if out is not None else new_outputs(pver, ld, precision, T.device)
+    dp = params or L.deep_defaults()
+    g = vgrid.struct(n, ld)
+    lc = _launch(path, block_threads)
+    nb = int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
+    wp, wn = _ws_for(T.device, workspace).get(nb)
+    st = L.lib().conv_deep_run(C.byref(g), C.byref(inp), C.byref(dp), float(dt),
+                               _PREC[precision], C.byref(_out_struct(o, pver, ld, precision)),
+                               C.byref(lc), wp, wn, _stream(stream))
+    L.check(st, "conv_deep_run")
+    return o
+
+
+def shallow(T, q, ps, vgrid: VerticalGrid, *, precision="fp64", params=None, path="plain",
+            block_threads=0, n_cols=None, out=None, workspace: Workspace | None = None,
+            stream=None):
+    """Shallow convection only (Alg. 3) on the given state."""
+    pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, None, None)
+    o = out if out is not None else new_outputs(pver, ld, precision, T.device)
+    sp = params or L.shallow_defaults()
+    g = vgrid.struct(n, ld)
+    lc = _launch(path, block_threads)
+    nb = int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
+    wp, wn = _ws_for(T.device, workspace).get(nb)
+    st = L.lib().conv_shallow_run(C.byref(g), C.byref(inp), C.byref(sp), _PREC[precision],
+                                  C.byref(_out_struct(o, pver, ld, precision)), C.byref(lc),
+                                  wp, wn, _stream(stream))
+    L.check(st, "conv_shallow_run")
+    return o

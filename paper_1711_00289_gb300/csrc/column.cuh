@@ -1,0 +1,623 @@
+// column.cuh -- per-column deep and shallow convection for the GB300 kernels.
+//
+// Device code only; included by the kernel translation units.  Every routine is
+// a template over the working precision R:
+//   R = double  the FP64 path (all arithmetic FP64);
+//   R = float   the mixed path: bulk FP32 with FP64 islands for the LCL Newton
+//               iteration, the CAPE integral that drives the trigger and the
+//               column conservation sums.
+//
+// The schemes (paper Sec. II-A; Alg. 1 deep then shallow; Alg. 2 entrainment and
+// precipitation loops; Alg. 3 shallow early exits with zeroed outputs) follow the
+// column equations frozen for this library:
+//  * levels  p_i = A_i p0 + B_i ps, p_k = (p_k + p_k+1)/2, m_k = dp_k/g;
+//  * heights hypsometric from the virtual temperature, z = 0 at the surface;
+//  * es      Bolton (1980) eq. 10, qs = eps es/max(p - (1-eps) es, 1e-3 p);
+//  * LCL     Newton on ln es(T) - ln e_b - (cp/Rd) ln(T/T_b) from Bolton eq. 22;
+//  * parcel  dry adiabat below the LCL layer, saturated MSE conservation above,
+//            inverted by Newton (first step from the environment, then n_h);
+//  * CAPE    sum of Rd (Tv_p - Tv) dln p from the LCL layer up to the highest
+//            positively buoyant layer; trigger CAPE > capelmt;
+//  * updraft eta = (1 + dz/z_e)^(lambda z_e); MSE and total water mixed per unit
+//            cloud-base flux; implicit rain eta c0 dz l/(1 + c0 dz); cloud top the
+//            first layer at/above the minimum-h* layer with h_u <= h*;
+//  * downdraft from the minimum-h* layer between top and LCL down to the launch
+//            layer, saturated by rain evaporation, scaled so that P >= 0;
+//  * tendencies in flux form with upwind compensating motion;
+//  * closure M_b = -CAPE/(tau F), F the parcel-fixed d(CAPE)/d(M_b), limited so
+//            that q + dt dq/dt >= q_min;
+//  * shallow source = lowest layer, exits E1 (LCL above p_lcl_min), E2 (no LFC
+//            below p_lfc_min), E3 (CIN > cin_max), E4 (plume dies at the LCL);
+//            M_b = rho c_m sqrt(tke) exp(-CIN/(cin_scale tke)); constant-mass-flux
+//            plume mixing 1 - exp(-eps dz) per layer; w2 from the LFC with
+//            dw2/dz = 2 a B - 2 b eps w2 integrated exactly per layer.
+#pragma once
+
+#include <cstdint>
+
+#include "conv.h"
+
+namespace cvg {
+
+// ---------------------------------------------------------------- constants
+constexpr double GRAV = 9.80616;
+constexpr double RD = 287.04;
+constexpr double RV = 461.5;
+constexpr double CP = 1004.64;
+constexpr double LV = 2.501e6;
+constexpr double EPSV = RD / RV;
+constexpr double ZVIR = RV / RD - 1.0;
+constexpr double ONE_M_EPS = 1.0 - EPSV;
+constexpr double INV_KAPPA = CP / RD;
+constexpr double KAPPA = RD / CP;
+constexpr double ES0 = 611.2;
+constexpr double ESA = 17.67;
+constexpr double EST0 = 273.15;
+constexpr double EST1 = 29.65;
+constexpr double ESC = 243.5;
+constexpr double NEWTON_TOL = 1e-4;  // K
+constexpr int MAXL = CONV_MAX_LEVELS;
+
+// Kernel-parameter copy of the vertical grid.
+struct Levels {
+  double a[MAXL + 1];
+  double b[MAXL + 1];
+  double p0;
+  int pver;
+};
+
+// ---------------------------------------------------------------- math per precision
+template <class R>
+struct Mth;
+// ex: fast where the result only scales a quantity.  es (the saturation
+// exponential, which sets the Newton fixed point of every moist inversion), lg
+// (layer thicknesses, accumulated into heights and moist static energy) and pw
+// (the dry adiabat of the parcel, integrated into CIN) feed thresholds and the
+// exp(-CIN) closure, so they use the accurate FP32 library functions.
+template <>
+struct Mth<double> {
+  static __device__ __forceinline__ double es(double x) { return exp(x); }
+  static __device__ __forceinline__ double ex(double x) { return exp(x); }
+  static __device__ __forceinline__ double lg(double x) { return log(x); }
+  static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double pw(double a, double b) { return pow(a, b); }
+};
+template <>
+struct Mth<float> {
+  static __device__ __forceinline__ float es(float x) { return expf(x); }
+  static __device__ __forceinline__ float ex(float x) { return __expf(x); }
+  static __device__ __forceinline__ float lg(float x) { return logf(x); }
+  static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+  static __device__ __forceinline__ float pw(float a, float b) { return powf(a, b); }
+};
+
+// Virtual temperature T (1 + z q) with every operation rounded on its own (no
+// contraction into FMA): parcel and environment values of the same air must be
+// bit-identical so that their difference is exactly zero, as it is in FP64 math.
+__device__ __forceinline__ double virt(double T, double q) {
+  return __dmul_rn(T, __dadd_rn(1.0, __dmul_rn(ZVIR, q)));
+}
+__device__ __forceinline__ float virt(float T, float q) {
+  return __fmul_rn(T, __fadd_rn(1.0f, __fmul_rn((float)ZVIR, q)));
+}
+
+// ---------------------------------------------------------------- thermodynamics
+// Saturation specific humidity and its T derivative (branch-consistent clamp).
+template <class R>
+__device__ __forceinline__ void sat_qs_dqs(R T, R p, R& qs, R& dqs) {
+  const R rt = Mth<R>::dv(R(1), T - R(EST1));
+  const R es = R(ES0) * Mth<R>::es(R(ESA) * (T - R(EST0)) * rt);
+  const R D = p - R(ONE_M_EPS) * es;
+  const R Dmin = R(1e-3) * p;
+  const R dlnes = R(ESA * ESC) * rt * rt;
+  if (D < Dmin) {
+    qs = Mth<R>::dv(R(EPSV) * es, Dmin);
+    dqs = qs * dlnes;
+  } else {
+    const R rD = Mth<R>::dv(R(1), D);
+    qs = R(EPSV) * es * rD;
+    dqs = qs * p * rD * dlnes;
+  }
+}
+template <class R>
+__device__ __forceinline__ R sat_qs(R T, R p) {
+  const R es = R(ES0) * Mth<R>::es(Mth<R>::dv(R(ESA) * (T - R(EST0)), T - R(EST1)));
+  R D = p - R(ONE_M_EPS) * es;
+  const R Dmin = R(1e-3) * p;
+  if (D < Dmin) D = Dmin;
+  return Mth<R>::dv(R(EPSV) * es, D);
+}
+
+// Saturated MSE inversion: T with cp T + gz + Lv qs(T,p) = h; 1 + n_extra Newton
+// steps from T (the environment).  Tracks the largest final correction.
+template <class R>
+__device__ __forceinline__ R moist_invert(R h, R gz, R p, R T, int n_extra, float& newton) {
+  R step = R(0);
+  for (int it = 0; it <= n_extra; ++it) {
+    R qs, dqs;
+    sat_qs_dqs(T, p, qs, dqs);
+    const R f = R(CP) * T + gz + R(LV) * qs - h;
+    const R fp = R(CP) + R(LV) * dqs;
+    step = Mth<R>::dv(f, fp);
+    T -= step;
+  }
+  newton = fmaxf(newton, (float)fabs((double)step));
+  return T;
+}
+
+// LCL of a parcel (FP64 island in both precisions).
+__device__ __forceinline__ void lcl_fp64(double Tb, double qb, double pb, int n_newton,
+                                         double& TL, double& pL, float& newton) {
+  const double esb = ES0 * exp(ESA * (Tb - EST0) / (Tb - EST1));
+  double Db = pb - ONE_M_EPS * esb;
+  if (Db < 1e-3 * pb) Db = 1e-3 * pb;
+  if (qb >= EPSV * esb / Db) {
+    TL = Tb;
+    pL = pb;
+    return;
+  }
+  const double eb = qb * pb / (EPSV + ONE_M_EPS * qb);
+  const double rh = eb / esb;
+  double T = 1.0 / (1.0 / (Tb - 55.0) - log(rh) / 2840.0) + 55.0;
+  const double c0 = log(ES0) - log(eb);
+  double step = 0.0;
+  for (int it = 0; it < n_newton; ++it) {
+    const double r = 1.0 / (T - EST1);
+    const double G = c0 + ESA * (T - EST0) * r - INV_KAPPA * log(T / Tb);
+    const double Gp = ESA * ESC * r * r - INV_KAPPA / T;
+    step = G / Gp;
+    T -= step;
+  }
+  newton = fmaxf(newton, (float)fabs(step));
+  TL = T;
+  pL = pb * pow(TL / Tb, INV_KAPPA);
+}
+
+// Entraining mass-flux profile (1 + dz/z_e)^(lambda z_e).
+template <class R>
+__device__ __forceinline__ R entrain_growth(R lam, R ze, R dz) {
+  return Mth<R>::ex(lam * ze * Mth<R>::lg(R(1) + Mth<R>::dv(dz, ze)));
+}
+
+// ---------------------------------------------------------------- column state
+template <class R>
+struct Column {
+  R T[MAXL], q[MAXL];
+  R p_mid[MAXL], dlnp[MAXL], m[MAXL];
+  R z_mid[MAXL], z_int[MAXL + 1], Tv[MAXL], h[MAXL], hs[MAXL];
+  int pver, ktl;
+  double ps;
+};
+
+template <class R>
+__device__ __forceinline__ bool column_valid(const Column<R>& c) {
+  if (!(c.ps > 5.0e4 && c.ps < 1.2e5)) return false;
+  bool ok = true;
+  for (int k = 0; k < c.pver; ++k) {
+    const double t = (double)c.T[k], q = (double)c.q[k];
+    ok = ok && (t > 100.0 && t < 400.0) && (q >= 0.0 && q < 0.1);
+  }
+  return ok;
+}
+
+// Levels, heights, moist static energies, top limit (shared by both schemes).
+template <class R>
+__device__ __forceinline__ void prologue(const Levels& L, double p_top_lim, Column<R>& c,
+                                         bool need_hs) {
+  const int pver = c.pver;
+  double pi_lo = __dadd_rn(__dmul_rn(L.a[pver], L.p0), __dmul_rn(L.b[pver], c.ps));
+  R zi = R(0);
+  c.z_int[pver] = R(0);
+  int ktl = pver - 1;
+  for (int k = pver - 1; k >= 0; --k) {
+    const double pi_hi = __dadd_rn(__dmul_rn(L.a[k], L.p0), __dmul_rn(L.b[k], c.ps));
+    const double pm = __dmul_rn(0.5, __dadd_rn(pi_hi, pi_lo));
+    const R pmR = (R)pm;
+    c.p_mid[k] = pmR;
+    c.m[k] = (R)((pi_lo - pi_hi) / GRAV);
+    const R tv = virt(c.T[k], c.q[k]);
+    c.Tv[k] = tv;
+    const R scale = R(RD / GRAV) * tv;
+    const R dl = Mth<R>::lg((R)(pi_lo / pi_hi));
+    c.dlnp[k] = dl;
+    const R zm = zi + scale * Mth<R>::lg((R)(pi_lo / pm));
+    zi = zi + scale * dl;
+    c.z_int[k] = zi;
+    c.z_mid[k] = zm;
+    const R sdry = R(CP) * c.T[k] + R(GRAV) * zm;
+    c.h[k] = sdry + R(LV) * c.q[k];
+    if (need_hs) c.hs[k] = sdry + R(LV) * sat_qs(c.T[k], pmR);
+    if (pm >= p_top_lim) ktl = k;
+    pi_lo = pi_hi;
+  }
+  c.ktl = ktl;
+}
+
+// ---------------------------------------------------------------- deep scheme
+template <class R>
+struct DeepOut {
+  R dT[MAXL], dq[MAXL];  // dT/dt, dq/dt of the column
+  double prec, cape, mb, cons;
+  int flags, kb, klcl, ktop, kaux;
+};
+
+template <class R>
+struct DeepTrig {
+  int kb, klcl, kel;
+  double cape;
+  bool triggered;
+  float newton;
+  R Tp[MAXL];
+};
+
+// Launch level, LCL, undilute parcel, CAPE and trigger (deep "stage A").
+template <class R>
+__device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep_params& P,
+                                             DeepTrig<R>& t) {
+  const int pver = c.pver, ktl = c.ktl;
+  int kb = pver - 1;
+  for (int k = pver - 2; k >= 0 && (double)c.p_mid[k] >= P.p_launch_min; --k)
+    if (c.h[k] > c.h[kb]) kb = k;
+  t.kb = kb;
+  t.kel = -1;
+  t.cape = 0.0;
+  t.triggered = false;
+  t.newton = 0.f;
+  double TL, pL;
+  lcl_fp64((double)c.T[kb], (double)c.q[kb], (double)c.p_mid[kb], P.n_newton_lcl, TL, pL,
+           t.newton);
+  int klcl = -1;
+  for (int k = kb; k >= 0; --k)
+    if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
+  t.klcl = klcl;
+  if (klcl < ktl) return;
+  const R hb = c.h[kb];
+  // Undilute parcel up from the LCL layer; CAPE accumulated in FP64, bottom up,
+  // and captured at the highest positively buoyant layer.
+  double run = 0.0;
+  int kel = -1;
+  double cape = 0.0;
+  for (int k = klcl; k >= ktl; --k) {
+    const R Tp = moist_invert(hb, R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
+                              t.newton);
+    t.Tp[k] = Tp;
+    const R b = virt(Tp, sat_qs(Tp, c.p_mid[k])) - c.Tv[k];
+    run += (double)(R(RD) * b * c.dlnp[k]);
+    if (b > R(0)) {
+      kel = k;
+      cape = run;
+    }
+  }
+  t.kel = kel;
+  if (kel < 0) return;
+  if (cape < 0.0) cape = 0.0;
+  t.cape = cape;
+  t.triggered = cape > P.capelmt;
+}
+
+// Updraft, downdraft, tendencies, closure and limiter of a triggered column
+// (deep "stage B": the entrainment and precipitation loops of Alg. 2).
+template <class R>
+__device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_params& P,
+                                           double dt, R lam, R tau, DeepTrig<R>& t,
+                                           DeepOut<R>& o) {
+  const int pver = c.pver, ktl = c.ktl, kb = t.kb, klcl = t.klcl, kel = t.kel;
+  const R ze = (R)P.ent_zscale;
+  // minimum h* layer above the LCL (ties: lowest)
+  int khmin = -1;
+  for (int k = klcl - 1; k >= ktl; --k)
+    if (khmin < 0 || c.hs[k] < c.hs[khmin]) khmin = k;
+  R eta[MAXL], hu[MAXL], qtu[MAXL];
+  eta[kb] = R(1);
+  hu[kb] = c.h[kb];
+  qtu[kb] = c.q[kb];
+  const R zb = c.z_mid[kb];
+  const R c0 = (R)P.c0;
+  int jt = -1;
+  R sumR = R(0);
+  for (int k = kb - 1; k >= ktl; --k) {
+    const R e = entrain_growth(lam, ze, c.z_mid[k] - zb);
+    eta[k] = e;
+    const R de = e - eta[k + 1];
+    const R re = Mth<R>::dv(R(1), e);
+    hu[k] = (eta[k + 1] * hu[k + 1] + de * c.h[k]) * re;
+    if ((k <= khmin && hu[k] <= c.hs[k]) || k == ktl) {
+      jt = k;
+      break;
+    }
+    const R qt = (eta[k + 1] * qtu[k + 1] + de * c.q[k]) * re;
+    const R Ts = moist_invert(hu[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
+                              t.newton);
+    R l = qt - sat_qs(Ts, c.p_mid[k]);
+    if (l < R(0)) l = R(0);
+    const R dz = c.z_int[k] - c.z_int[k + 1];
+    const R rain = Mth<R>::dv(e * c0 * dz * l, R(1) + c0 * dz);
+    qtu[k] = qt - rain * re;
+    sumR += rain;
+  }
+  if (jt < 0 || jt >= klcl) return;
+
+  // downdraft start: minimum h* strictly between cloud top and LCL (ties: lowest)
+  int jd = -1;
+  for (int k = klcl - 1; k > jt; --k)
+    if (jd < 0 || c.hs[k] < c.hs[jd]) jd = k;
+  R etad[MAXL], hd[MAXL], qd[MAXL];
+  R sumE = R(0), alpha = R(0);
+  if (jd >= 0) {
+    const R zd = c.z_mid[jd];
+    R qprev = R(0), eprev = R(0);
+    for (int k = jd; k <= kb - 1; ++k) {
+      const R e = entrain_growth(lam, ze, zd - c.z_mid[k]);
+      etad[k] = e;
+      hd[k] = (k == jd) ? c.h[jd] : Mth<R>::dv(eprev * hd[k - 1] + (e - eprev) * c.h[k], e);
+      const R Td = moist_invert(hd[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
+                                t.newton);
+      qd[k] = sat_qs(Td, c.p_mid[k]);
+      sumE += e * qd[k] - eprev * qprev - (e - eprev) * c.q[k];
+      qprev = qd[k];
+      eprev = e;
+    }
+    alpha = (R)P.alpha_dd;
+    if (alpha * sumE > sumR) alpha = Mth<R>::dv(sumR, sumE);
+  }
+
+  // unit tendencies (per M_b) in flux form
+  // (the closure reads dT/dq on k_el..klcl, which may reach above the cloud top)
+  R dh[MAXL], dq[MAXL], dT[MAXL];
+  for (int k = 0; k < pver; ++k) dh[k] = dq[k] = dT[k] = R(0);
+  for (int k = jt + 1; k <= kb; ++k) {
+    dh[k] += eta[k] * (c.h[k - 1] - c.h[k]);
+    dq[k] += eta[k] * (c.q[k - 1] - c.q[k]);
+  }
+  dh[jt] += eta[jt + 1] * (hu[jt + 1] - c.h[jt]);
+  dq[jt] += eta[jt + 1] * (qtu[jt + 1] - c.q[jt]);
+  if (jd >= 0) {
+    for (int k = jd; k <= kb - 1; ++k) {
+      const R D = alpha * etad[k];
+      dh[k] += D * (c.h[k + 1] - c.h[k]);
+      dq[k] += D * (c.q[k + 1] - c.q[k]);
+    }
+    const R D = alpha * etad[kb - 1];
+    dh[kb] += D * (hd[kb - 1] - c.h[kb]);
+    dq[kb] += D * (qd[kb - 1] - c.q[kb]);
+  }
+  for (int k = jt; k <= kb; ++k) {
+    const R rm = Mth<R>::dv(R(1), c.m[k]);
+    dh[k] *= rm;
+    dq[k] *= rm;
+    dT[k] = (dh[k] - R(LV) * dq[k]) * R(1.0 / CP);
+  }
+
+  // closure
+  R F = R(0);
+  for (int k = klcl; k >= kel; --k) {
+    R qsp, dqsp;
+    sat_qs_dqs(t.Tp[k], c.p_mid[k], qsp, dqsp);
+    const R dTvp = Mth<R>::dv((R(1) + R(ZVIR) * qsp) + R(ZVIR) * t.Tp[k] * dqsp,
+                              R(CP) + R(LV) * dqsp);
+    const R dTv = (R(1) + R(ZVIR) * c.q[k]) * dT[k] + R(ZVIR) * c.T[k] * dq[k];
+    F += R(RD) * c.dlnp[k] * (dTvp * dh[kb] - dTv);
+  }
+  if (!(F < R(0))) return;
+  R mb = Mth<R>::dv((R)(-t.cape), tau * F);
+  bool limited = false;
+  for (int k = jt; k <= kb; ++k) {
+    if (dq[k] < R(0)) {
+      const R ml = Mth<R>::dv(c.q[k] - (R)P.q_min, -(R)dt * dq[k]);
+      if (ml < mb) {
+        mb = ml;
+        limited = true;
+      }
+    }
+  }
+  if (!(mb > R(0))) return;
+  R net = sumR - alpha * sumE;
+  if (net < R(0)) net = R(0);
+  o.flags |= CONV_FLAG_ACTIVE | (limited ? CONV_FLAG_LIMITED : 0);
+  o.mb = (double)mb;
+  o.prec = (double)(mb * net);
+  o.ktop = jt;
+  o.kaux = jd;
+  double se = 0.0, sw = 0.0, sc = 0.0;
+  for (int k = jt; k <= kb; ++k) {
+    const R a = mb * dT[k];
+    const R b = mb * dq[k];
+    o.dT[k] = a;
+    o.dq[k] = b;
+    const double mk = (double)c.m[k];
+    se += mk * CP * (double)a;
+    sw += mk * (double)b;
+    sc += mk * CP * fabs((double)a);
+  }
+  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) / (sc + LV * o.prec + 1e-300);
+}
+
+// Whole deep scheme for one column already loaded into c (T, q, ps, pver).
+template <class R>
+__device__ __forceinline__ void deep_column(const Levels& L, const conv_deep_params& P,
+                                            double dt, R lam, R tau, Column<R>& c,
+                                            DeepOut<R>& o) {
+  for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
+  o.prec = o.cape = o.mb = o.cons = 0.0;
+  o.flags = 0;
+  o.kb = o.klcl = o.ktop = o.kaux = -1;
+  if (!column_valid(c)) {
+    o.flags = CONV_FLAG_BADINPUT;
+    return;
+  }
+  prologue(L, P.p_top_lim, c, true);
+  DeepTrig<R> t;
+  deep_trigger(c, P, t);
+  o.kb = t.kb;
+  o.klcl = t.klcl;
+  o.cape = t.cape;
+  if (t.triggered) {
+    o.flags |= CONV_FLAG_TRIGGERED;
+    deep_plume(c, P, dt, lam, tau, t, o);
+  }
+  if (t.newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+}
+
+// ---------------------------------------------------------------- shallow scheme
+template <class R>
+struct ShalOut {
+  R dT[MAXL], dq[MAXL];
+  double prec, cin, mb, cons;
+  int flags, klcl, ktop, klfc;
+};
+
+// Whole shallow scheme for one column already loaded into c (Alg. 3).
+template <class R>
+__device__ __forceinline__ void shallow_column(const Levels& L, const conv_shallow_params& P,
+                                               Column<R>& c, ShalOut<R>& o) {
+  const int pver = c.pver;
+  for (int k = 0; k < pver; ++k) o.dT[k] = o.dq[k] = R(0);
+  o.prec = o.cin = o.mb = o.cons = 0.0;
+  o.flags = 0;
+  o.klcl = o.ktop = o.klfc = -1;
+  if (!column_valid(c)) {
+    o.flags = CONV_FLAG_BADINPUT;
+    return;
+  }
+  prologue(L, P.p_top_lim, c, false);
+  const int ks = pver - 1, ktl = c.ktl;
+  float newton = 0.f;
+  double TL, pL;
+  lcl_fp64((double)c.T[ks], (double)c.q[ks], (double)c.p_mid[ks], P.n_newton_lcl, TL, pL, newton);
+  int klcl = -1;
+  for (int k = ks; k >= 0; --k)
+    if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
+  o.klcl = klcl;
+  int exit_code = 0;
+  R mb = R(0);
+  int klfc = -1, kts = -1;
+  R hu[MAXL], qtu[MAXL], qpre[MAXL], rf[MAXL];
+  if (pL < P.p_lcl_min || klcl < ktl) {
+    exit_code = 1;
+  } else {
+    // undilute parcel up to the LFC; CIN in FP64
+    const R Ts = c.T[ks], qsrc = c.q[ks], psrc = c.p_mid[ks];
+    double cin = 0.0;
+    for (int k = ks; k >= ktl && (double)c.p_mid[k] >= P.p_lfc_min; --k) {
+      R Tp, qp;
+      if (k > klcl) {
+        Tp = Ts * Mth<R>::pw(Mth<R>::dv(c.p_mid[k], psrc), R(KAPPA));
+        qp = qsrc;
+      } else {
+        Tp = moist_invert(c.h[ks], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
+                          newton);
+        qp = sat_qs(Tp, c.p_mid[k]);
+      }
+      const R b = virt(Tp, qp) - c.Tv[k];
+      if (k <= klcl && b > R(0)) {
+        klfc = k;
+        break;
+      }
+      if (b < R(0)) cin += (double)(R(RD) * (-b) * c.dlnp[k]);
+    }
+    o.klfc = klfc;
+    if (klfc < 0) {
+      exit_code = 2;
+    } else {
+      o.cin = cin;
+      if (cin > P.cin_max) {
+        exit_code = 3;
+      } else {
+        const R rho = Mth<R>::dv(psrc, R(RD) * c.Tv[ks]);
+        mb = rho * (R)(P.c_m * sqrt(P.tke)) * Mth<R>::ex((R)(-cin / (P.cin_scale * P.tke)));
+        // plume
+        hu[ks] = c.h[ks];
+        qtu[ks] = qsrc;
+        qpre[ks] = qsrc;
+        rf[ks] = R(0);
+        const R w2_0 = (R)(2.0 / 3.0 * P.tke);
+        R w2 = w2_0;
+        const R eps = (R)P.eps_s;
+        const double beps = P.b_w * P.eps_s;
+        for (int k = ks - 1; k >= ktl; --k) {
+          const R dz = c.z_int[k] - c.z_int[k + 1];
+          R qt;
+          if (k >= klcl) {
+            hu[k] = hu[k + 1];
+            qt = qtu[k + 1];
+          } else {
+            const R chi = R(1) - Mth<R>::ex(-eps * dz);
+            hu[k] = hu[k + 1] + chi * (c.h[k] - hu[k + 1]);
+            qt = qtu[k + 1] + chi * (c.q[k] - qtu[k + 1]);
+          }
+          qpre[k] = qt;
+          rf[k] = R(0);
+          const R gz = R(GRAV) * c.z_mid[k];
+          const R Tsat = moist_invert(hu[k], gz, c.p_mid[k], c.T[k], P.n_newton_h, newton);
+          const R qsu = sat_qs(Tsat, c.p_mid[k]);
+          R Tu, qv;
+          if (qt >= qsu) {
+            Tu = Tsat;
+            qv = qsu;
+          } else {
+            Tu = (hu[k] - gz - R(LV) * qt) * R(1.0 / CP);
+            qv = qt;
+          }
+          if (k < klfc) {
+            const R B = R(GRAV) * Mth<R>::dv(virt(Tu, qv) - c.Tv[k], c.Tv[k]);
+            if (beps > 0.0) {
+              const R decay = Mth<R>::ex((R)(-2.0 * beps) * dz);
+              w2 = w2 * decay + (R)(P.a_w / beps) * B * (R(1) - decay);
+            } else {
+              w2 = w2 + (R)(2.0 * P.a_w) * B * dz;
+            }
+            if (!(w2 > R(0))) {
+              kts = k + 1;
+              break;
+            }
+          }
+          if (k == ktl) {
+            kts = k;
+            break;
+          }
+          R r = qt - qv - (R)P.ql_crit;
+          if (r < R(0)) r = R(0);
+          rf[k] = r;
+          qtu[k] = qt - r;
+        }
+        if (kts < 0 || kts >= klcl) exit_code = 4;
+      }
+    }
+  }
+  if (exit_code == 0 || exit_code == 4) o.flags |= CONV_FLAG_TRIGGERED;
+  o.flags |= exit_code << CONV_EXIT_SHIFT;
+  if (newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+  if (exit_code != 0) return;
+
+  // tendencies of the constant-mass-flux plume
+  R dh[MAXL], dq[MAXL];
+  dh[ks] = mb * (c.h[ks - 1] - c.h[ks]);
+  dq[ks] = mb * (c.q[ks - 1] - c.q[ks]);
+  R sumr = R(0);
+  for (int k = kts + 1; k <= ks - 1; ++k) {
+    dh[k] = mb * ((hu[k + 1] - hu[k]) + (c.h[k - 1] - c.h[k]));
+    dq[k] = mb * ((qtu[k + 1] - qpre[k]) + (c.q[k - 1] - c.q[k]));
+    sumr += rf[k];
+  }
+  dh[kts] = mb * (hu[kts + 1] - c.h[kts]);
+  dq[kts] = mb * (qtu[kts + 1] - c.q[kts]);
+  o.flags |= CONV_FLAG_ACTIVE;
+  o.mb = (double)mb;
+  o.prec = (double)(mb * sumr);
+  o.ktop = kts;
+  double se = 0.0, sw = 0.0, sc = 0.0;
+  for (int k = kts; k <= ks; ++k) {
+    const R rm = Mth<R>::dv(R(1), c.m[k]);
+    const R dqk = dq[k] * rm;
+    const R dTk = (dh[k] * rm - R(LV) * dqk) * R(1.0 / CP);
+    o.dT[k] = dTk;
+    o.dq[k] = dqk;
+    const double mk = (double)c.m[k];
+    se += mk * CP * (double)dTk;
+    sw += mk * (double)dqk;
+    sc += mk * CP * fabs((double)dTk);
+  }
+  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) / (sc + LV * o.prec + 1e-300);
+}
+
+}  // namespace cvg

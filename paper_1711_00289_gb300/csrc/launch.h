@@ -1,0 +1,49 @@
+// launch.h -- internal interface between the C ABI (conv_api.cu) and the kernel
+// translation units.  Not installed; the public interface is include/conv.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "column.cuh"
+
+namespace cvg {
+
+enum : int { MODE_DEEP = 1, MODE_SHALLOW = 2 };
+
+struct OutP {
+  void* dTdt;
+  void* dqdt;
+  double* prec;
+  int32_t* flags;
+  int32_t* kb;
+  int32_t* klcl;
+  int32_t* ktop;
+  int32_t* kaux;
+  double* cape;
+  double* mb;
+  double* cons_err;
+};
+
+struct RunArgs {
+  Levels L;
+  int n, ld;
+  const void* T;
+  const void* q;
+  const double* ps;
+  const double* lam;
+  const double* tau;
+  conv_deep_params dp;
+  conv_shallow_params sp;
+  double dt;
+  OutP od, os;
+  int mode;
+  int block;
+  cudaStream_t stream;
+};
+
+// Plain path: one thread per column, whole scheme, no compaction.
+cudaError_t launch_plain(const RunArgs& a, bool fp64);
+
+}  // namespace cvg

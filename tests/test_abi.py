@@ -1,0 +1,116 @@
+"""The C-ABI library loads, exports every function include/*.h declares, and
+rejects invalid arguments on the host before enqueueing anything (no GPU is
+touched by these tests)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1711_00289_gb300 import _lib as L
+from paper_1711_00289_gb300 import soundings as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(conv\w*)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_library_exports_declared_symbols():
+    lib = L.lib()
+    names = declared_functions()
+    assert "conv_deep_run" in names and "conv_shallow_run" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_defaults_and_status_strings():
+    dp = L.deep_defaults()
+    assert dp.capelmt == 70.0 and dp.n_newton_lcl == 6 and dp.ent_zscale == 1000.0
+    sp = L.shallow_defaults()
+    assert sp.cin_max == 50.0 and sp.b_w == 2.0
+    for s in range(6):
+        assert L.status_str(s).startswith("CONV_")
+
+
+def _args(pver=30, n=0, ld=0):
+    # n_cols = 0: even if validation wrongly accepted an argument, nothing is
+    # launched (the fake pointers below are never handed to a kernel).
+    a, b = S.hybrid_coefficients(pver)
+    dp = C.POINTER(C.c_double)
+    g = L.Grid(pver, n, ld, 0, a.ctypes.data_as(dp), b.ctypes.data_as(dp), 1e5)
+    fake = C.c_void_p(0x1000)  # never dereferenced: validation fails first
+    inp = L.In(fake, fake, fake, None, None)
+    out = L.Out(fake, fake, fake, fake, None, None, None, None, None, None, None)
+    return g, inp, out, (a, b)
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda g, i, o, d, s: setattr(g, "pver", 33),
+    lambda g, i, o, d, s: setattr(g, "pver", 3),
+    lambda g, i, o, d, s: setattr(g, "ld", -1),
+    lambda g, i, o, d, s: setattr(g, "n_cols", -1),
+    lambda g, i, o, d, s: setattr(i, "T", None),
+    lambda g, i, o, d, s: setattr(o, "flags", None),
+    lambda g, i, o, d, s: setattr(d, "tau_default", -1.0),
+    lambda g, i, o, d, s: setattr(d, "n_newton_lcl", 0),
+    lambda g, i, o, d, s: setattr(s, "tke", 0.0),
+    lambda g, i, o, d, s: setattr(g, "p0", float("nan")),
+])
+def test_invalid_arguments_rejected_on_host(mutate):
+    g, inp, out, keep = _args()
+    dp, sp = L.deep_defaults(), L.shallow_defaults()
+    mutate(g, inp, out, dp, sp)
+    lib = L.lib()
+    st = lib.conv_deep_shallow_run(C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp), 1800.0,
+                                   L.CONV_FP64, C.byref(out), C.byref(out), None, None, 0, None)
+    assert st == L.CONV_ERR_ARG
+
+
+def test_unordered_levels_rejected():
+    g, inp, out, (a, b) = _args()
+    a2, b2 = a[::-1].copy(), b[::-1].copy()
+    g.hyai = a2.ctypes.data_as(C.POINTER(C.c_double))
+    g.hybi = b2.ctypes.data_as(C.POINTER(C.c_double))
+    st = L.lib().conv_deep_run(C.byref(g), C.byref(inp), C.byref(L.deep_defaults()), 1800.0,
+                               L.CONV_FP64, C.byref(out), None, None, 0, None)
+    assert st == L.CONV_ERR_ARG
+
+
+def test_bad_precision_and_dt_rejected():
+    g, inp, out, keep = _args()
+    lib = L.lib()
+    dp = L.deep_defaults()
+    assert lib.conv_deep_run(C.byref(g), C.byref(inp), C.byref(dp), 1800.0, 7, C.byref(out),
+                             None, None, 0, None) == L.CONV_ERR_ARG
+    assert lib.conv_deep_run(C.byref(g), C.byref(inp), C.byref(dp), -5.0, L.CONV_FP64,
+                             C.byref(out), None, None, 0, None) == L.CONV_ERR_ARG
+    assert lib.conv_deep_run(C.byref(g), C.byref(inp), C.byref(dp), float("inf"), L.CONV_FP64,
+                             C.byref(out), None, None, 0, None) == L.CONV_ERR_ARG
+
+
+def test_workspace_size_query_without_device():
+    g, inp, out, keep = _args(n=1000, ld=1024)  # size query only, nothing runs
+    lib = L.lib()
+    plain = L.Launch(L.CONV_PATH_PLAIN, 0, 0, 0)
+    assert lib.conv_workspace_bytes(C.byref(g), L.CONV_FP64, C.byref(plain)) == 0
+    assert lib.conv_workspace_bytes(None, L.CONV_FP64, None) == 0
+
+
+def test_package_has_no_cpu_fallback():
+    """The product modules never import, load or run anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_1711_00289_gb300")
+    bad = re.compile(r"^\s*(import|from)\s+oracle\b|conv_oracle|libconv_oracle|oracle/",
+                     re.M)
+    for f in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
+        if f.endswith((".py", ".cu", ".cuh", ".h")):
+            assert not bad.search(open(f).read()), f

@@ -1,0 +1,161 @@
+"""CUDA path vs the FP64 CPU oracle, through the C ABI, on seeded soundings.
+
+FP64 bar: flags and cloud-base/top level indices bit-exact, tendencies within
+1e-10 of each column's largest reference tendency, column scalars within 1e-10.
+Mixed bar: decision mismatches and trigger flips <= 0.1% of columns; over
+columns with identical decisions, tendency column integrals within 1e-4 and
+precipitation within 1e-3 (relative).
+"""
+import numpy as np
+import pytest
+
+from paper_1711_00289_gb300 import soundings as S
+from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu)
+
+pytestmark = pytest.mark.gpu
+
+PATHS = ["plain"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def latlon():
+    return S.latlon_grid()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_column_set_fp64(oracle, path):
+    g = S.column_set(64)
+    rd, rs = oracle.deep_shallow(g)
+    gd, gs = run_gpu(g, "fp64", path)
+    assert_fp64_parity(gd, rd, what="deep")
+    assert_fp64_parity(gs, rs, what="shallow")
+    assert ((rd["flags"] & 2) > 0).sum() > 5
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_latlon_fp64_deep_shallow(oracle, latlon, path):
+    rd, rs = oracle.deep_shallow(latlon, threads=THREADS)
+    gd, gs = run_gpu(latlon, "fp64", path)
+    assert_fp64_parity(gd, rd, what="deep")
+    assert_fp64_parity(gs, rs, what="shallow")
+    frac = ((rd["flags"] & 1) > 0).mean()
+    assert 0.2 < frac < 0.3
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_separate_entry_points_fp64(oracle, path):
+    g = S.latlon_grid(24, 36)
+    (gd,) = run_gpu(g, "fp64", path, scheme="deep")
+    assert_fp64_parity(gd, oracle.deep(g), what="deep-only")
+    (gs,) = run_gpu(g, "fp64", path, scheme="shallow")
+    assert_fp64_parity(gs, oracle.shallow(g), what="shallow-only")
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("n,pad", [(1, 0), (31, 1), (33, 31), (129, 0), (1000, 24), (4099, 61)])
+def test_ragged_sizes_and_padding_untouched(oracle, path, n, pad):
+    g = S.column_set(n, seed=777 + n)
+    ld = n + pad
+    (gd, gs), (hd, hs) = run_gpu(g, "fp64", path, ld=ld, sentinel=True)
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    assert_fp64_parity(gd, rd, what=f"deep n={n}")
+    assert_fp64_parity(gs, rs, what=f"shallow n={n}")
+    for h in (hd, hs):
+        for k, v in h.items():
+            tail = v[:, n:] if v.ndim == 2 else v[n:]
+            assert np.all(tail == -7), f"padding of {k} written"
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("pver", [26, 32])
+def test_other_level_counts(oracle, path, pver):
+    g = S.column_set(512, seed=99 + pver, pver=pver)
+    g.lam = np.full(g.n_cols, 1.7e-3)
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    gd, gs = run_gpu(g, "fp64", path)
+    assert_fp64_parity(gd, rd, what=f"deep pver={pver}")
+    assert_fp64_parity(gs, rs, what=f"shallow pver={pver}")
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_bad_inputs_flagged_and_zeroed(oracle, path):
+    g = S.column_set(64, seed=5)
+    g.T[3, 1] = np.nan
+    g.q[29, 2] = -1e-6
+    g.ps[3] = 4.0e4
+    g.T[0, 4] = 450.0
+    g.q[10, 5] = np.inf
+    rd, rs = oracle.deep_shallow(g)
+    gd, gs = run_gpu(g, "fp64", path)
+    for c in range(1, 6):
+        assert gd["flags"][c] == 16 and gs["flags"][c] == 16
+        assert np.all(gd["dTdt"][:, c] == 0) and np.all(gs["dqdt"][:, c] == 0)
+    assert_fp64_parity(gd, rd, what="deep")
+    assert_fp64_parity(gs, rs, what="shallow")
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_zero_columns_is_a_noop(path):
+    import torch
+
+    from paper_1711_00289_gb300 import api
+
+    g = S.column_set(32)
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    T = torch.tensor(g.T, device="cuda")
+    q = torch.tensor(g.q, device="cuda")
+    ps = torch.tensor(g.ps, device="cuda")
+    od = api.new_outputs(30, 32, "fp64")
+    od["flags"].fill_(-3)
+    api.deep(T, q, ps, vg, n_cols=0, out=od, path=path)
+    torch.cuda.synchronize()
+    assert torch.all(od["flags"] == -3)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_deterministic_and_permutation_invariant(path):
+    g = S.latlon_grid(48, 72)
+    a = run_gpu(g, "fp64", path)
+    b = run_gpu(g, "fp64", path)
+    perm = np.random.default_rng(3).permutation(g.n_cols)
+    gp = S.Columns("perm", g.pver, g.T[:, perm], g.q[:, perm], g.ps[perm], g.hyai, g.hybi)
+    c = run_gpu(gp, "fp64", path)
+    for x, y, z in zip(a, b, c):
+        for k in x:
+            assert np.array_equal(x[k], y[k], equal_nan=True), k
+            zz = z[k]
+            xx = x[k][:, perm] if x[k].ndim == 2 else x[k][perm]
+            assert np.array_equal(xx, zz, equal_nan=True), k
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_mixed_precision_budget(oracle, latlon, path):
+    rd, rs = oracle.deep_shallow(latlon, threads=THREADS)
+    gd, gs = run_gpu(latlon, "mixed", path)
+    m = layer_mass(latlon)
+    for tag, got, ref in (("deep", gd, rd), ("shallow", gs, rs)):
+        r = mixed_report(got, ref, m)
+        assert r["trigger_flips"] <= 1e-3 * r["n"], (tag, r)
+        assert r["decision_mismatch"] <= 1e-3 * r["n"], (tag, r)
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, (tag, r)
+        assert r["prec_max"] <= 1e-3, (tag, r)
+
+
+@pytest.mark.parametrize("frac", [0.1, 0.3, 0.6])
+def test_full_resolution_grid_fp64(oracle, frac):
+    """884,736 columns x 30 levels, the launch the benchmark times: every column
+    against the oracle."""
+    g = S.clustered_grid(frac)
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    gd, gs = run_gpu(g, "fp64", "plain")
+    assert_fp64_parity(gd, rd, what=f"deep f={frac}")
+    assert_fp64_parity(gs, rs, what=f"shallow f={frac}")
+    trig = ((rd["flags"] & 1) > 0).mean()
+    assert abs(trig - frac) < 0.02
