@@ -106,10 +106,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline
-def op_counts(workload: str):
+def op_counts(frac: float):
+    """Per-column algorithmic operation counts of the clustered workload with this
+    convecting fraction (per-column counts do not depend on the grid size)."""
     path = os.path.join(ROOT, "oracle", "op_counts.json")
     with open(path) as fh:
-        return json.load(fh)["workloads"][workload]["total_per_column"]
+        w = json.load(fh)["workloads"]
+    key = min((k for k in w if k.startswith("clustered")),
+              key=lambda k: abs(float(k.rsplit("-f", 1)[1]) - frac))
+    return w[key]["total_per_column"], key
 
 
 def fp64_alu_roofline(counts, kernel_s, n_cols, L):
@@ -300,7 +305,9 @@ def ours_arm(args, rank, world, local_rank):
         return
     roof = None
     if prec == "fp64":
-        roof = fp64_alu_roofline(op_counts(g.name), ms * 1e-3, n, L)
+        counts, key = op_counts(args.frac)
+        roof = fp64_alu_roofline(counts, ms * 1e-3, n, L)
+        roof["op_counts_workload"] = key
     roof = roof or {}
     roof["hbm_algorithmic_bytes_per_column"] = hbm_bytes_per_column(pver, 8 if prec == "fp64"
                                                                     else 4)

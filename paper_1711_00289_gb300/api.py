@@ -153,7 +153,7 @@ def _stream(stream):
 
 
 def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64",
-                 lam=None, tau=None, deep_params=None, shallow_params=None, path="plain",
+                 lam=None, tau=None, deep_params=None, shallow_params=None, path="auto",
                  block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
                  workspace: Workspace | None = None, stream=None):
     """Deep then shallow convection (Alg. 1 order) in one fused call.
@@ -177,7 +177,7 @@ def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision
 
 
 def deep(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64", lam=None,
-         tau=None, params=None, path="plain", block_threads=0, n_cols=None, out=None,
+         tau=None, params=None, path="auto", block_threads=0, n_cols=None, out=None,
          workspace: Workspace | None = None, stream=None):
     """Deep convection only (Alg. 2)."""
     pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)

@@ -2,10 +2,14 @@
 //
 // Device code only; included by the kernel translation units.  Every routine is
 // a template over the working precision R:
-//   R = double  the FP64 path (all arithmetic FP64);
+//   R = double  the FP64 path: every operation FP64, every Newton solve with the
+//               fixed iteration counts of the scheme definition;
 //   R = float   the mixed path: bulk FP32 with FP64 islands for the LCL Newton
-//               iteration, the CAPE integral that drives the trigger and the
-//               column conservation sums.
+//               iteration (FP32 iterations, then one FP64 Newton correction with
+//               an FP64 residual), the CAPE integral that drives the trigger and
+//               the column conservation sums.  Moist inversions are warm-started
+//               from the previous level's solution by a tangent predictor and take
+//               kWarmSteps Newton steps to FP32 convergence.
 //
 // The schemes (paper Sec. II-A; Alg. 1 deep then shallow; Alg. 2 entrainment and
 // precipitation loops; Alg. 3 shallow early exits with zeroed outputs) follow the
@@ -13,7 +17,7 @@
 //  * levels  p_i = A_i p0 + B_i ps, p_k = (p_k + p_k+1)/2, m_k = dp_k/g;
 //  * heights hypsometric from the virtual temperature, z = 0 at the surface;
 //  * es      Bolton (1980) eq. 10, qs = eps es/max(p - (1-eps) es, 1e-3 p);
-//  * LCL     Newton on ln es(T) - ln e_b - (cp/Rd) ln(T/T_b) from Bolton eq. 22;
+//  * LCL     root of ln es(T) - ln e_b - (cp/Rd) ln(T/T_b), Newton from Bolton eq. 22;
 //  * parcel  dry adiabat below the LCL layer, saturated MSE conservation above,
 //            inverted by Newton (first step from the environment, then n_h);
 //  * CAPE    sum of Rd (Tv_p - Tv) dln p from the LCL layer up to the highest
@@ -55,40 +59,48 @@ constexpr double ESA = 17.67;
 constexpr double EST0 = 273.15;
 constexpr double EST1 = 29.65;
 constexpr double ESC = 243.5;
-constexpr double NEWTON_TOL = 1e-4;  // K
+constexpr double LN_ES0 = 6.415424628734003;  // ln(611.2)
+constexpr double NEWTON_TOL = 1e-4;           // K
 constexpr int MAXL = CONV_MAX_LEVELS;
+constexpr int kWarmSteps = 3;  // Newton steps after the tangent predictor (mixed path)
 
-// Kernel-parameter copy of the vertical grid.
+// Kernel-parameter copy of the vertical grid (FP64 and FP32 forms of A p0, B).
 struct Levels {
   double a[MAXL + 1];
   double b[MAXL + 1];
+  float ap0f[MAXL + 1];
+  float bf[MAXL + 1];
   double p0;
   int pver;
 };
 
 // ---------------------------------------------------------------- math per precision
-template <class R>
-struct Mth;
 // ex: fast where the result only scales a quantity.  es (the saturation
 // exponential, which sets the Newton fixed point of every moist inversion), lg
 // (layer thicknesses, accumulated into heights and moist static energy) and pw
 // (the dry adiabat of the parcel, integrated into CIN) feed thresholds and the
 // exp(-CIN) closure, so they use the accurate FP32 library functions.
+template <class R>
+struct Mth;
 template <>
 struct Mth<double> {
+  static constexpr bool warm = false;
   static __device__ __forceinline__ double es(double x) { return exp(x); }
   static __device__ __forceinline__ double ex(double x) { return exp(x); }
   static __device__ __forceinline__ double lg(double x) { return log(x); }
   static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
   static __device__ __forceinline__ double pw(double a, double b) { return pow(a, b); }
+  static __device__ __forceinline__ double ab(double a) { return fabs(a); }
 };
 template <>
 struct Mth<float> {
+  static constexpr bool warm = true;
   static __device__ __forceinline__ float es(float x) { return expf(x); }
   static __device__ __forceinline__ float ex(float x) { return __expf(x); }
   static __device__ __forceinline__ float lg(float x) { return logf(x); }
   static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
   static __device__ __forceinline__ float pw(float a, float b) { return powf(a, b); }
+  static __device__ __forceinline__ float ab(float a) { return fabsf(a); }
 };
 
 // Virtual temperature T (1 + z q) with every operation rounded on its own (no
@@ -102,19 +114,21 @@ __device__ __forceinline__ float virt(float T, float q) {
 }
 
 // ---------------------------------------------------------------- thermodynamics
-// Saturation specific humidity and its T derivative (branch-consistent clamp).
+// Saturation specific humidity, its T derivative (branch-consistent clamp) and
+// 1/D, D = max(p - (1-eps) es, 1e-3 p).
 template <class R>
-__device__ __forceinline__ void sat_qs_dqs(R T, R p, R& qs, R& dqs) {
+__device__ __forceinline__ void sat_qs_dqs(R T, R p, R& qs, R& dqs, R& rD) {
   const R rt = Mth<R>::dv(R(1), T - R(EST1));
   const R es = R(ES0) * Mth<R>::es(R(ESA) * (T - R(EST0)) * rt);
   const R D = p - R(ONE_M_EPS) * es;
   const R Dmin = R(1e-3) * p;
   const R dlnes = R(ESA * ESC) * rt * rt;
   if (D < Dmin) {
-    qs = Mth<R>::dv(R(EPSV) * es, Dmin);
+    rD = Mth<R>::dv(R(1), Dmin);
+    qs = R(EPSV) * es * rD;
     dqs = qs * dlnes;
   } else {
-    const R rD = Mth<R>::dv(R(1), D);
+    rD = Mth<R>::dv(R(1), D);
     qs = R(EPSV) * es * rD;
     dqs = qs * p * rD * dlnes;
   }
@@ -128,38 +142,63 @@ __device__ __forceinline__ R sat_qs(R T, R p) {
   return Mth<R>::dv(R(EPSV) * es, D);
 }
 
-// Saturated MSE inversion: T with cp T + gz + Lv qs(T,p) = h; 1 + n_extra Newton
-// steps from T (the environment).  Tracks the largest final correction.
+// Saturated MSE inversion, cp T + gz + Lv qs(T,p) = h.  A solve either starts
+// from the environment temperature with 1 + n_h Newton steps (the scheme
+// definition; always in FP64), or -- mixed path, later levels of a vertical
+// sequence -- from the tangent prediction off the previous level's solution
+//   dT = (dh - d(gz) + Lv qs dp/D) / (cp + Lv dqs/dT)
+// followed by kWarmSteps Newton steps.  Tracks the largest final correction.
 template <class R>
-__device__ __forceinline__ R moist_invert(R h, R gz, R p, R T, int n_extra, float& newton) {
-  R step = R(0);
-  for (int it = 0; it <= n_extra; ++it) {
-    R qs, dqs;
-    sat_qs_dqs(T, p, qs, dqs);
+struct MoistSeq {
+  bool have;
+  R T, qs, dqs, rD, p, gz, h;
+};
+
+template <class R>
+__device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, MoistSeq<R>& s,
+                                          float& newton) {
+  R T;
+  int steps;
+  if (Mth<R>::warm && s.have) {
+    T = s.T + Mth<R>::dv((h - s.h) - (gz - s.gz) + R(LV) * s.qs * (p - s.p) * s.rD,
+                         R(CP) + R(LV) * s.dqs);
+    steps = kWarmSteps;
+  } else {
+    T = T_env;
+    steps = n_h + 1;
+  }
+  R step = R(0), qs = R(0), dqs = R(0), rD = R(0);
+  for (int it = 0; it < steps; ++it) {
+    sat_qs_dqs(T, p, qs, dqs, rD);
     const R f = R(CP) * T + gz + R(LV) * qs - h;
     const R fp = R(CP) + R(LV) * dqs;
     step = Mth<R>::dv(f, fp);
     T -= step;
   }
-  newton = fmaxf(newton, (float)fabs((double)step));
+  s.have = true;
+  s.T = T;
+  s.qs = qs;
+  s.dqs = dqs;
+  s.rD = rD;
+  s.p = p;
+  s.gz = gz;
+  s.h = h;
+  newton = fmaxf(newton, (float)Mth<R>::ab(step));
   return T;
 }
 
-// LCL of a parcel (FP64 island in both precisions).
-__device__ __forceinline__ void lcl_fp64(double Tb, double qb, double pb, int n_newton,
-                                         double& TL, double& pL, float& newton) {
+// LCL of a parcel (Tb, qb, pb): pressure p_L where the dry adiabat saturates.
+// FP64 path: FP64 Newton from the Bolton eq. 22 guess, n_newton steps.
+__device__ __forceinline__ double lcl_p(double Tb, double qb, double pb, int n_newton,
+                                        float& newton) {
   const double esb = ES0 * exp(ESA * (Tb - EST0) / (Tb - EST1));
   double Db = pb - ONE_M_EPS * esb;
   if (Db < 1e-3 * pb) Db = 1e-3 * pb;
-  if (qb >= EPSV * esb / Db) {
-    TL = Tb;
-    pL = pb;
-    return;
-  }
+  if (qb >= EPSV * esb / Db) return pb;
   const double eb = qb * pb / (EPSV + ONE_M_EPS * qb);
   const double rh = eb / esb;
   double T = 1.0 / (1.0 / (Tb - 55.0) - log(rh) / 2840.0) + 55.0;
-  const double c0 = log(ES0) - log(eb);
+  const double c0 = LN_ES0 - log(eb);
   double step = 0.0;
   for (int it = 0; it < n_newton; ++it) {
     const double r = 1.0 / (T - EST1);
@@ -169,8 +208,59 @@ __device__ __forceinline__ void lcl_fp64(double Tb, double qb, double pb, int n_
     T -= step;
   }
   newton = fmaxf(newton, (float)fabs(step));
-  TL = T;
-  pL = pb * pow(TL / Tb, INV_KAPPA);
+  return pb * pow(T / Tb, INV_KAPPA);
+}
+
+// ln(x/y) for x/y near 1 by the atanh series ln r = 2 atanh((r-1)/(r+1)) =
+// 2u(1 + u^2/3 + u^4/5 + ...), u = (x-y)/(x+y); |u| <= 0.12 keeps the truncation
+// below 1e-16 relative; otherwise the library logarithm.
+__device__ __forceinline__ double ln_ratio(double x, double y) {
+  const double u = (x - y) / (x + y);
+  if (fabs(u) > 0.12) return log(x / y);
+  const double u2 = u * u;
+  double s = 1.0 / 15.0;
+  s = fma(s, u2, 1.0 / 13.0);
+  s = fma(s, u2, 1.0 / 11.0);
+  s = fma(s, u2, 1.0 / 9.0);
+  s = fma(s, u2, 1.0 / 7.0);
+  s = fma(s, u2, 1.0 / 5.0);
+  s = fma(s, u2, 1.0 / 3.0);
+  s = fma(s, u2, 1.0);
+  return 2.0 * u * s;
+}
+
+// Mixed path LCL: the same root (written in the difference form
+// ln es(T) - ln es(Tb) - ln RH - (cp/Rd) ln(T/Tb) = 0, exactly equivalent), FP32
+// Newton iterations, then one FP64 Newton correction with the residual, the
+// relative humidity and the logarithms in FP64 (the FP64 island).
+__device__ __forceinline__ double lcl_p(float Tb, float qb, float pb, int n_newton,
+                                        float& newton) {
+  const float esb =
+      (float)ES0 * expf(__fdividef((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
+  float Db = pb - (float)ONE_M_EPS * esb;
+  if (Db < 1e-3f * pb) Db = 1e-3f * pb;
+  if (qb >= __fdividef((float)EPSV * esb, Db)) return (double)pb;
+  const double Tbd = Tb, qbd = qb, pbd = pb;
+  const double eb = qbd * pbd / (EPSV + ONE_M_EPS * qbd);
+  const double lnrh = log(eb) - (LN_ES0 + ESA * (Tbd - EST0) / (Tbd - EST1));
+  const float lnrhf = (float)lnrh;
+  const float c1 = __fdividef((float)(ESA * ESC), Tb - (float)EST1);
+  float T = __fdividef(1.f, __fdividef(1.f, Tb - 55.f) - lnrhf * (1.f / 2840.f)) + 55.f;
+  float rGp = 0.f;
+  for (int it = 0; it < n_newton; ++it) {
+    const float r = __fdividef(1.f, T - (float)EST1);
+    const float G = c1 * (T - Tb) * r - lnrhf - (float)INV_KAPPA * logf(__fdividef(T, Tb));
+    const float Gp = (float)(ESA * ESC) * r * r - __fdividef((float)INV_KAPPA, T);
+    rGp = __fdividef(1.f, Gp);
+    T -= G * rGp;
+  }
+  const double Td = T;
+  const double lr = ln_ratio(Td, Tbd);
+  const double G = ESA * ESC * (Td - Tbd) / ((Td - EST1) * (Tbd - EST1)) - lnrh - INV_KAPPA * lr;
+  const double step = G * (double)rGp;
+  newton = fmaxf(newton, (float)fabs(step));
+  // ln(TL/Tb) = ln(T/Tb) - step/T to second order in the (tiny) step
+  return pbd * exp(INV_KAPPA * (lr - step * (double)__fdividef(1.f, T)));
 }
 
 // Entraining mass-flux profile (1 + dz/z_e)^(lambda z_e).
@@ -189,45 +279,78 @@ struct Column {
   double ps;
 };
 
+__device__ __forceinline__ bool in_range(double T, double q) {
+  return (T > 100.0 && T < 400.0) && (q >= 0.0 && q < 0.1);
+}
+__device__ __forceinline__ bool in_range(float T, float q) {
+  return (T > 100.f && T < 400.f) && (q >= 0.f && q < 0.1f);
+}
+
 template <class R>
 __device__ __forceinline__ bool column_valid(const Column<R>& c) {
   if (!(c.ps > 5.0e4 && c.ps < 1.2e5)) return false;
   bool ok = true;
-  for (int k = 0; k < c.pver; ++k) {
-    const double t = (double)c.T[k], q = (double)c.q[k];
-    ok = ok && (t > 100.0 && t < 400.0) && (q >= 0.0 && q < 0.1);
-  }
+  for (int k = 0; k < c.pver; ++k) ok = ok && in_range(c.T[k], c.q[k]);
   return ok;
 }
+
+// Interface pressures: FP64 path rounds each operation as the definition reads
+// (no contraction); mixed path in FP32.
+struct PressFP64 {
+  const Levels& L;
+  double ps;
+  __device__ __forceinline__ double pi(int i) const {
+    return __dadd_rn(__dmul_rn(L.a[i], L.p0), __dmul_rn(L.b[i], ps));
+  }
+  __device__ __forceinline__ double mid(double lo, double hi) const {
+    return __dmul_rn(0.5, __dadd_rn(hi, lo));
+  }
+};
+struct PressFP32 {
+  const Levels& L;
+  float ps;
+  __device__ __forceinline__ float pi(int i) const { return fmaf(L.bf[i], ps, L.ap0f[i]); }
+  __device__ __forceinline__ float mid(float lo, float hi) const { return 0.5f * (hi + lo); }
+};
+template <class R>
+struct PressOf {
+  using type = PressFP64;
+};
+template <>
+struct PressOf<float> {
+  using type = PressFP32;
+};
 
 // Levels, heights, moist static energies, top limit (shared by both schemes).
 template <class R>
 __device__ __forceinline__ void prologue(const Levels& L, double p_top_lim, Column<R>& c,
                                          bool need_hs) {
+  using Pr = typename PressOf<R>::type;
+  const Pr P{L, (R)c.ps};
   const int pver = c.pver;
-  double pi_lo = __dadd_rn(__dmul_rn(L.a[pver], L.p0), __dmul_rn(L.b[pver], c.ps));
+  const R ptl = (R)p_top_lim;
+  R pi_lo = P.pi(pver);
   R zi = R(0);
   c.z_int[pver] = R(0);
   int ktl = pver - 1;
   for (int k = pver - 1; k >= 0; --k) {
-    const double pi_hi = __dadd_rn(__dmul_rn(L.a[k], L.p0), __dmul_rn(L.b[k], c.ps));
-    const double pm = __dmul_rn(0.5, __dadd_rn(pi_hi, pi_lo));
-    const R pmR = (R)pm;
-    c.p_mid[k] = pmR;
-    c.m[k] = (R)((pi_lo - pi_hi) / GRAV);
+    const R pi_hi = P.pi(k);
+    const R pm = P.mid(pi_lo, pi_hi);
+    c.p_mid[k] = pm;
+    c.m[k] = (pi_lo - pi_hi) * R(1.0 / GRAV);
     const R tv = virt(c.T[k], c.q[k]);
     c.Tv[k] = tv;
     const R scale = R(RD / GRAV) * tv;
-    const R dl = Mth<R>::lg((R)(pi_lo / pi_hi));
+    const R dl = Mth<R>::lg(Mth<R>::dv(pi_lo, pi_hi));
     c.dlnp[k] = dl;
-    const R zm = zi + scale * Mth<R>::lg((R)(pi_lo / pm));
+    const R zm = zi + scale * Mth<R>::lg(Mth<R>::dv(pi_lo, pm));
     zi = zi + scale * dl;
     c.z_int[k] = zi;
     c.z_mid[k] = zm;
     const R sdry = R(CP) * c.T[k] + R(GRAV) * zm;
     c.h[k] = sdry + R(LV) * c.q[k];
-    if (need_hs) c.hs[k] = sdry + R(LV) * sat_qs(c.T[k], pmR);
-    if (pm >= p_top_lim) ktl = k;
+    if (need_hs) c.hs[k] = sdry + R(LV) * sat_qs(c.T[k], pm);
+    if (pm >= ptl) ktl = k;
     pi_lo = pi_hi;
   }
   c.ktl = ktl;
@@ -244,28 +367,29 @@ struct DeepOut {
 template <class R>
 struct DeepTrig {
   int kb, klcl, kel;
-  double cape;
+  double cape, pL;
   bool triggered;
   float newton;
   R Tp[MAXL];
 };
 
 // Launch level, LCL, undilute parcel, CAPE and trigger (deep "stage A").
+// t.Tp holds the parcel temperature on ktl..klcl whenever klcl >= ktl.
 template <class R>
 __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep_params& P,
                                              DeepTrig<R>& t) {
   const int pver = c.pver, ktl = c.ktl;
+  const R plaunch = (R)P.p_launch_min;
   int kb = pver - 1;
-  for (int k = pver - 2; k >= 0 && (double)c.p_mid[k] >= P.p_launch_min; --k)
+  for (int k = pver - 2; k >= 0 && c.p_mid[k] >= plaunch; --k)
     if (c.h[k] > c.h[kb]) kb = k;
   t.kb = kb;
   t.kel = -1;
   t.cape = 0.0;
   t.triggered = false;
   t.newton = 0.f;
-  double TL, pL;
-  lcl_fp64((double)c.T[kb], (double)c.q[kb], (double)c.p_mid[kb], P.n_newton_lcl, TL, pL,
-           t.newton);
+  const double pL = lcl_p(c.T[kb], c.q[kb], c.p_mid[kb], P.n_newton_lcl, t.newton);
+  t.pL = pL;
   int klcl = -1;
   for (int k = kb; k >= 0; --k)
     if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
@@ -274,11 +398,13 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   const R hb = c.h[kb];
   // Undilute parcel up from the LCL layer; CAPE accumulated in FP64, bottom up,
   // and captured at the highest positively buoyant layer.
+  MoistSeq<R> seq;
+  seq.have = false;
   double run = 0.0;
   int kel = -1;
   double cape = 0.0;
   for (int k = klcl; k >= ktl; --k) {
-    const R Tp = moist_invert(hb, R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
+    const R Tp = moist_invert(hb, R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h, seq,
                               t.newton);
     t.Tp[k] = Tp;
     const R b = virt(Tp, sat_qs(Tp, c.p_mid[k])) - c.Tv[k];
@@ -315,6 +441,8 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   const R c0 = (R)P.c0;
   int jt = -1;
   R sumR = R(0);
+  MoistSeq<R> seq;
+  seq.have = false;
   for (int k = kb - 1; k >= ktl; --k) {
     const R e = entrain_growth(lam, ze, c.z_mid[k] - zb);
     eta[k] = e;
@@ -327,7 +455,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
     }
     const R qt = (eta[k + 1] * qtu[k + 1] + de * c.q[k]) * re;
     const R Ts = moist_invert(hu[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                              t.newton);
+                              seq, t.newton);
     R l = qt - sat_qs(Ts, c.p_mid[k]);
     if (l < R(0)) l = R(0);
     const R dz = c.z_int[k] - c.z_int[k + 1];
@@ -346,12 +474,13 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   if (jd >= 0) {
     const R zd = c.z_mid[jd];
     R qprev = R(0), eprev = R(0);
+    seq.have = false;
     for (int k = jd; k <= kb - 1; ++k) {
       const R e = entrain_growth(lam, ze, zd - c.z_mid[k]);
       etad[k] = e;
       hd[k] = (k == jd) ? c.h[jd] : Mth<R>::dv(eprev * hd[k - 1] + (e - eprev) * c.h[k], e);
       const R Td = moist_invert(hd[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                                t.newton);
+                                seq, t.newton);
       qd[k] = sat_qs(Td, c.p_mid[k]);
       sumE += e * qd[k] - eprev * qprev - (e - eprev) * c.q[k];
       qprev = qd[k];
@@ -391,8 +520,8 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   // closure
   R F = R(0);
   for (int k = klcl; k >= kel; --k) {
-    R qsp, dqsp;
-    sat_qs_dqs(t.Tp[k], c.p_mid[k], qsp, dqsp);
+    R qsp, dqsp, rD;
+    sat_qs_dqs(t.Tp[k], c.p_mid[k], qsp, dqsp, rD);
     const R dTvp = Mth<R>::dv((R(1) + R(ZVIR) * qsp) + R(ZVIR) * t.Tp[k] * dqsp,
                               R(CP) + R(LV) * dqsp);
     const R dTv = (R(1) + R(ZVIR) * c.q[k]) * dT[k] + R(ZVIR) * c.T[k] * dq[k];
@@ -418,18 +547,21 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   o.prec = (double)(mb * net);
   o.ktop = jt;
   o.kaux = jd;
-  double se = 0.0, sw = 0.0, sc = 0.0;
+  double se = 0.0, sw = 0.0;
+  R sc = R(0);
   for (int k = jt; k <= kb; ++k) {
     const R a = mb * dT[k];
     const R b = mb * dq[k];
     o.dT[k] = a;
     o.dq[k] = b;
-    const double mk = (double)c.m[k];
-    se += mk * CP * (double)a;
-    sw += mk * (double)b;
-    sc += mk * CP * fabs((double)a);
+    const R mk = c.m[k];
+    se += (double)(mk * a);
+    sw += (double)(mk * b);
+    sc += mk * Mth<R>::ab(a);
   }
-  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) / (sc + LV * o.prec + 1e-300);
+  se *= CP;
+  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) /
+           (CP * (double)sc + LV * o.prec + 1e-300);
 }
 
 // Whole deep scheme for one column already loaded into c (T, q, ps, pver).
@@ -466,46 +598,71 @@ struct ShalOut {
   int flags, klcl, ktop, klfc;
 };
 
-// Whole shallow scheme for one column already loaded into c (Alg. 3).
+// Results of the deep trigger the shallow scheme may reuse: when the deep
+// launch layer is the lowest layer of the same (unmodified) column, the
+// shallow source, its LCL and its saturated parcel are the deep ones.
+template <class R>
+struct ShallowSeed {
+  double pL;
+  int klcl;
+  const R* Tp;  // parcel temperature on ktl..klcl
+};
+
+// Whole shallow scheme for one column in c (Alg. 3).  When `prologue_done` the
+// column has been validated and its prologue computed already.
 template <class R>
 __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shallow_params& P,
-                                               Column<R>& c, ShalOut<R>& o) {
+                                               Column<R>& c, ShalOut<R>& o,
+                                               const ShallowSeed<R>* seed = nullptr,
+                                               bool prologue_done = false) {
   const int pver = c.pver;
   for (int k = 0; k < pver; ++k) o.dT[k] = o.dq[k] = R(0);
   o.prec = o.cin = o.mb = o.cons = 0.0;
   o.flags = 0;
   o.klcl = o.ktop = o.klfc = -1;
-  if (!column_valid(c)) {
-    o.flags = CONV_FLAG_BADINPUT;
-    return;
+  if (!prologue_done) {
+    if (!column_valid(c)) {
+      o.flags = CONV_FLAG_BADINPUT;
+      return;
+    }
+    prologue(L, P.p_top_lim, c, false);
   }
-  prologue(L, P.p_top_lim, c, false);
   const int ks = pver - 1, ktl = c.ktl;
   float newton = 0.f;
-  double TL, pL;
-  lcl_fp64((double)c.T[ks], (double)c.q[ks], (double)c.p_mid[ks], P.n_newton_lcl, TL, pL, newton);
-  int klcl = -1;
-  for (int k = ks; k >= 0; --k)
-    if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
+  double pL;
+  int klcl;
+  if (seed) {
+    pL = seed->pL;
+    klcl = seed->klcl;
+  } else {
+    pL = lcl_p(c.T[ks], c.q[ks], c.p_mid[ks], P.n_newton_lcl, newton);
+    klcl = -1;
+    for (int k = ks; k >= 0; --k)
+      if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
+  }
   o.klcl = klcl;
   int exit_code = 0;
   R mb = R(0);
   int klfc = -1, kts = -1;
   R hu[MAXL], qtu[MAXL], qpre[MAXL], rf[MAXL];
+  const R plfc = (R)P.p_lfc_min;
   if (pL < P.p_lcl_min || klcl < ktl) {
     exit_code = 1;
   } else {
     // undilute parcel up to the LFC; CIN in FP64
     const R Ts = c.T[ks], qsrc = c.q[ks], psrc = c.p_mid[ks];
     double cin = 0.0;
-    for (int k = ks; k >= ktl && (double)c.p_mid[k] >= P.p_lfc_min; --k) {
+    MoistSeq<R> seq;
+    seq.have = false;
+    for (int k = ks; k >= ktl && c.p_mid[k] >= plfc; --k) {
       R Tp, qp;
       if (k > klcl) {
         Tp = Ts * Mth<R>::pw(Mth<R>::dv(c.p_mid[k], psrc), R(KAPPA));
         qp = qsrc;
       } else {
-        Tp = moist_invert(c.h[ks], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                          newton);
+        Tp = seed ? seed->Tp[k]
+                  : moist_invert(c.h[ks], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k],
+                                 P.n_newton_h, seq, newton);
         qp = sat_qs(Tp, c.p_mid[k]);
       }
       const R b = virt(Tp, qp) - c.Tv[k];
@@ -534,6 +691,7 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
         R w2 = w2_0;
         const R eps = (R)P.eps_s;
         const double beps = P.b_w * P.eps_s;
+        seq.have = false;
         for (int k = ks - 1; k >= ktl; --k) {
           const R dz = c.z_int[k] - c.z_int[k + 1];
           R qt;
@@ -548,7 +706,7 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
           qpre[k] = qt;
           rf[k] = R(0);
           const R gz = R(GRAV) * c.z_mid[k];
-          const R Tsat = moist_invert(hu[k], gz, c.p_mid[k], c.T[k], P.n_newton_h, newton);
+          const R Tsat = moist_invert(hu[k], gz, c.p_mid[k], c.T[k], P.n_newton_h, seq, newton);
           const R qsu = sat_qs(Tsat, c.p_mid[k]);
           R Tu, qv;
           if (qt >= qsu) {
@@ -605,19 +763,22 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
   o.mb = (double)mb;
   o.prec = (double)(mb * sumr);
   o.ktop = kts;
-  double se = 0.0, sw = 0.0, sc = 0.0;
+  double se = 0.0, sw = 0.0;
+  R sc = R(0);
   for (int k = kts; k <= ks; ++k) {
     const R rm = Mth<R>::dv(R(1), c.m[k]);
     const R dqk = dq[k] * rm;
     const R dTk = (dh[k] * rm - R(LV) * dqk) * R(1.0 / CP);
     o.dT[k] = dTk;
     o.dq[k] = dqk;
-    const double mk = (double)c.m[k];
-    se += mk * CP * (double)dTk;
-    sw += mk * (double)dqk;
-    sc += mk * CP * fabs((double)dTk);
+    const R mk = c.m[k];
+    se += (double)(mk * dTk);
+    sw += (double)(mk * dqk);
+    sc += mk * Mth<R>::ab(dTk);
   }
-  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) / (sc + LV * o.prec + 1e-300);
+  se *= CP;
+  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) /
+           (CP * (double)sc + LV * o.prec + 1e-300);
 }
 
 }  // namespace cvg

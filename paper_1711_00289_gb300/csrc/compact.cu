@@ -1,0 +1,225 @@
+// compact.cu -- the compacted path: the GPU answer to the load imbalance the
+// paper fights with OpenMP dynamic scheduling (Sec. III-A): "at grid points
+// where there is no deep clouding, the corresponding column iterations ... are
+// skipped".  Instead of letting a warp carry idle lanes through the plume code:
+//
+//  k_trigger (all columns, one thread each): prologue, launch level, LCL,
+//    undilute parcel and CAPE.  A column that does not trigger deep convection
+//    is finished here: zero deep outputs, then the shallow scheme on the
+//    unchanged state, reusing the prologue and -- when its launch layer is the
+//    lowest layer -- the deep LCL and saturated parcel.  Triggered columns are
+//    appended to a device queue (warp ballot, one atomic per warp) with their
+//    trigger state (launch/LCL/EL levels, CAPE, parcel temperatures).
+//  k_plume (one thread per queue slot): entraining updraft, downdraft,
+//    closure and deep outputs, then the shallow scheme on the deep-updated
+//    state.  Its grid covers every possible slot and reads the queue length
+//    from device memory, so no host synchronisation is needed (capturable).
+#include "compact.h"
+
+namespace cvg {
+
+template <class R>
+__device__ __forceinline__ void store_deep(const RunArgs& a, int i, const DeepOut<R>& o,
+                                           bool tendencies) {
+  const int ld = a.ld, pver = a.L.pver;
+  if (tendencies) {
+    R* dT = static_cast<R*>(a.od.dTdt);
+    R* dq = static_cast<R*>(a.od.dqdt);
+    for (int k = 0; k < pver; ++k) {
+      dT[(size_t)k * ld + i] = o.dT[k];
+      dq[(size_t)k * ld + i] = o.dq[k];
+    }
+  }
+  a.od.prec[i] = o.prec;
+  a.od.flags[i] = o.flags;
+  if (a.od.kb) a.od.kb[i] = o.kb;
+  if (a.od.klcl) a.od.klcl[i] = o.klcl;
+  if (a.od.ktop) a.od.ktop[i] = o.ktop;
+  if (a.od.kaux) a.od.kaux[i] = o.kaux;
+  if (a.od.cape) a.od.cape[i] = o.cape;
+  if (a.od.mb) a.od.mb[i] = o.mb;
+  if (a.od.cons_err) a.od.cons_err[i] = o.cons;
+}
+
+template <class R>
+__device__ __forceinline__ void store_shallow(const RunArgs& a, int i, const ShalOut<R>& o) {
+  const int ld = a.ld, pver = a.L.pver;
+  R* dT = static_cast<R*>(a.os.dTdt);
+  R* dq = static_cast<R*>(a.os.dqdt);
+  for (int k = 0; k < pver; ++k) {
+    dT[(size_t)k * ld + i] = o.dT[k];
+    dq[(size_t)k * ld + i] = o.dq[k];
+  }
+  const bool bad = (o.flags & CONV_FLAG_BADINPUT) != 0;
+  a.os.prec[i] = o.prec;
+  a.os.flags[i] = o.flags;
+  if (a.os.kb) a.os.kb[i] = bad ? -1 : pver - 1;
+  if (a.os.klcl) a.os.klcl[i] = o.klcl;
+  if (a.os.ktop) a.os.ktop[i] = o.ktop;
+  if (a.os.kaux) a.os.kaux[i] = o.klfc;
+  if (a.os.cape) a.os.cape[i] = o.cin;
+  if (a.os.mb) a.os.mb[i] = o.mb;
+  if (a.os.cons_err) a.os.cons_err[i] = o.cons;
+}
+
+template <class R>
+__device__ __forceinline__ void load_column(const RunArgs& a, int i, Column<R>& c) {
+  const R* __restrict__ T = static_cast<const R*>(a.T);
+  const R* __restrict__ q = static_cast<const R*>(a.q);
+  c.pver = a.L.pver;
+  c.ps = a.ps[i];
+  for (int k = 0; k < c.pver; ++k) {
+    c.T[k] = T[(size_t)k * a.ld + i];
+    c.q[k] = q[(size_t)k * a.ld + i];
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<R> w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = i < a.n;
+  Column<R> c;
+  DeepOut<R> o;
+  DeepTrig<R> t;
+  t.triggered = false;
+  bool valid = false;
+  if (live) {
+    load_column(a, i, c);
+    for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
+    o.prec = o.cape = o.mb = o.cons = 0.0;
+    o.flags = 0;
+    o.kb = o.klcl = o.ktop = o.kaux = -1;
+    valid = column_valid(c);
+    if (!valid) {
+      o.flags = CONV_FLAG_BADINPUT;
+    } else {
+      prologue(a.L, a.dp.p_top_lim, c, true);
+      deep_trigger(c, a.dp, t);
+      o.kb = t.kb;
+      o.klcl = t.klcl;
+      o.cape = t.cape;
+      if (t.triggered) o.flags |= CONV_FLAG_TRIGGERED;
+      if (t.newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+    }
+  }
+  // queue append: one atomic per warp, slots in lane order
+  const unsigned ball = __ballot_sync(0xffffffffu, t.triggered);
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (ball) {
+    const int leader = __ffs(ball) - 1;
+    if (lane == leader) base = atomicAdd(w.count, __popc(ball));
+    base = __shfl_sync(0xffffffffu, base, leader);
+  }
+  if (!live) return;
+  if (t.triggered) {
+    const int slot = base + __popc(ball & ((1u << lane) - 1u));
+    w.queue[slot] = i;
+    w.levels[slot] = t.kb | (t.klcl << 8) | (t.kel << 16);
+    w.cape[slot] = t.cape;
+    for (int k = t.kel; k <= t.klcl; ++k) w.Tp[(size_t)k * a.n + slot] = t.Tp[k];
+    store_deep(a, i, o, false);  // scalars now; tendencies and the rest in k_plume
+    return;
+  }
+  store_deep(a, i, o, true);
+  if (!(a.mode & MODE_SHALLOW)) return;
+  ShalOut<R> s;
+  if (!valid) {
+    shallow_column(a.L, a.sp, c, s);  // flags the column as bad input
+  } else {
+    // same state as the deep scheme saw: reuse prologue, and the LCL/parcel
+    // when the deep launch layer is the shallow source layer
+    const bool same_src = t.kb == c.pver - 1 && a.sp.p_top_lim == a.dp.p_top_lim &&
+                          a.sp.n_newton_lcl == a.dp.n_newton_lcl &&
+                          a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
+    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(a.L, a.sp.p_top_lim, c, false);
+    ShallowSeed<R> seed{t.pL, t.klcl, t.Tp};
+    shallow_column(a.L, a.sp, c, s, same_src ? &seed : nullptr, true);
+  }
+  store_shallow(a, i, s);
+}
+
+template <class R>
+__device__ __forceinline__ R add_mul(R a, double dt, R b);
+template <>
+__device__ __forceinline__ double add_mul<double>(double a, double dt, double b) {
+  return __dadd_rn(a, __dmul_rn(dt, b));
+}
+template <>
+__device__ __forceinline__ float add_mul<float>(float a, double dt, float b) {
+  return a + (float)dt * b;
+}
+
+template <class R>
+__global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R> w) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= *w.count) return;
+  const int i = w.queue[slot];
+  Column<R> c;
+  load_column(a, i, c);
+  prologue(a.L, a.dp.p_top_lim, c, true);
+  DeepTrig<R> t;
+  const int lv = w.levels[slot];
+  t.kb = lv & 0xff;
+  t.klcl = (lv >> 8) & 0xff;
+  t.kel = (lv >> 16) & 0xff;
+  t.cape = w.cape[slot];
+  t.triggered = true;
+  t.newton = 0.f;
+  for (int k = t.kel; k <= t.klcl; ++k) t.Tp[k] = w.Tp[(size_t)k * a.n + slot];
+  DeepOut<R> o;
+  for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
+  o.prec = o.mb = o.cons = 0.0;
+  o.cape = t.cape;
+  o.flags = a.od.flags[i];  // trigger-stage bits written by k_trigger
+  o.kb = t.kb;
+  o.klcl = t.klcl;
+  o.ktop = o.kaux = -1;
+  const R lam = (R)(a.lam ? a.lam[i] : a.dp.lambda_default);
+  const R tau = (R)(a.tau ? a.tau[i] : a.dp.tau_default);
+  deep_plume(c, a.dp, a.dt, lam, tau, t, o);
+  if (t.newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+  store_deep(a, i, o, true);
+  if (!(a.mode & MODE_SHALLOW)) return;
+  for (int k = 0; k < c.pver; ++k) {
+    c.T[k] = add_mul(c.T[k], a.dt, o.dT[k]);
+    const R qn = add_mul(c.q[k], a.dt, o.dq[k]);
+    c.q[k] = qn < R(0) ? R(0) : qn;  // limiter keeps q >= q_min up to rounding
+  }
+  ShalOut<R> s;
+  shallow_column(a.L, a.sp, c, s);
+  store_shallow(a, i, s);
+}
+
+size_t compact_workspace_bytes(int n, int pver, bool fp64) {
+  const size_t rb = fp64 ? 8 : 4;
+  return ws_offsets(n, pver, rb).total;
+}
+
+template <class R>
+static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
+  const WsOffsets off = ws_offsets(a.n, a.L.pver, sizeof(R));
+  if (ws_bytes < off.total) return cudaErrorInvalidValue;
+  char* base = static_cast<char*>(ws);
+  CompactWs<R> w;
+  w.count = reinterpret_cast<int*>(base + off.count);
+  w.queue = reinterpret_cast<int*>(base + off.queue);
+  w.levels = reinterpret_cast<int*>(base + off.levels);
+  w.cape = reinterpret_cast<double*>(base + off.cape);
+  w.Tp = reinterpret_cast<R*>(base + off.Tp);
+  cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
+  if (e != cudaSuccess) return e;
+  const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
+  k_trigger<R><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_plume<R><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const RunArgs& a, bool fp64, void* ws, size_t ws_bytes) {
+  if (a.n == 0) return cudaSuccess;
+  return fp64 ? launch_t<double>(a, ws, ws_bytes) : launch_t<float>(a, ws, ws_bytes);
+}
+
+}  // namespace cvg

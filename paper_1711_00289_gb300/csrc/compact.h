@@ -1,0 +1,46 @@
+// compact.h -- workspace layout of the compacted path (internal).
+#pragma once
+
+#include "launch.h"
+
+namespace cvg {
+
+constexpr int kCompactBlock = 128;
+
+// Device workspace of the compacted path, carved from one caller buffer:
+//   count  int32      queue length (zeroed at the start of every run)
+//   queue  int32[n]   column index of each queued (deep-triggered) column
+//   levels int32[n]   kb | klcl << 8 | kel << 16 of the queued column
+//   cape   double[n]  CAPE of the queued column
+//   Tp     R[pver][n] undilute parcel temperature on kel..klcl, by queue slot
+template <class R>
+struct CompactWs {
+  int* count;
+  int* queue;
+  int* levels;
+  double* cape;
+  R* Tp;
+};
+
+struct WsOffsets {
+  size_t count, queue, levels, cape, Tp, total;
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+inline WsOffsets ws_offsets(int n, int pver, size_t real_bytes) {
+  WsOffsets o;
+  const size_t nn = n < 1 ? 1 : (size_t)n;
+  o.count = 0;
+  o.queue = 256;
+  o.levels = o.queue + align256(4 * nn);
+  o.cape = o.levels + align256(4 * nn);
+  o.Tp = o.cape + align256(8 * nn);
+  o.total = o.Tp + align256(real_bytes * (size_t)pver * nn);
+  return o;
+}
+
+size_t compact_workspace_bytes(int n, int pver, bool fp64);
+cudaError_t launch_compact(const RunArgs& a, bool fp64, void* ws, size_t ws_bytes);
+
+}  // namespace cvg

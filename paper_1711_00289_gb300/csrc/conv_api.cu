@@ -2,9 +2,10 @@
 // validation on the host, packing of kernel parameters, dispatch to a kernel
 // path.  Nothing here allocates or synchronises.
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 
-#include "launch.h"
+#include "compact.h"
 
 namespace {
 
@@ -39,6 +40,8 @@ conv_status fill_grid(const conv_grid* g, RunArgs& a) {
   for (int i = 0; i <= CONV_MAX_LEVELS; ++i) {
     a.L.a[i] = i <= g->pver ? g->hyai[i] : 0.0;
     a.L.b[i] = i <= g->pver ? g->hybi[i] : 0.0;
+    a.L.ap0f[i] = (float)(a.L.a[i] * g->p0);
+    a.L.bf[i] = (float)a.L.b[i];
   }
   for (int i = 0; i < g->pver; ++i) {  // interfaces must be ordered top -> surface
     if (!std::isfinite(g->hyai[i]) || !std::isfinite(g->hybi[i])) return CONV_ERR_ARG;
@@ -70,21 +73,37 @@ cvg::OutP to_outp(const conv_out* o) {
   return p;
 }
 
-int pick_path(const conv_launch* l) { return (l && l->path) ? l->path : CONV_PATH_PLAIN; }
+// AUTO selects the compacted path; a shallow-only run has nothing to compact
+// (no deep trigger) and always uses the plain kernel.
+int pick_path(const conv_launch* l, int mode) {
+  if (!(mode & cvg::MODE_DEEP)) return CONV_PATH_PLAIN;
+  const int p = l ? l->path : CONV_PATH_AUTO;
+  return p == CONV_PATH_AUTO ? CONV_PATH_COMPACT : p;
+}
+
+size_t needed_ws(int n, int pver, conv_precision prec, int path) {
+  return path == CONV_PATH_COMPACT ? cvg::compact_workspace_bytes(n, pver, prec == CONV_FP64)
+                                   : 0;
+}
 
 conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch, void* ws,
                      size_t ws_bytes) {
-  (void)ws;
-  (void)ws_bytes;
   if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
-  const int path = pick_path(launch);
+  if (launch && (launch->path < CONV_PATH_AUTO || launch->path > CONV_PATH_COMPACT))
+    return CONV_ERR_ARG;
   if (launch && (launch->block_threads < 0 || launch->block_threads > 1024)) return CONV_ERR_ARG;
+  const int path = pick_path(launch, a.mode);
   a.block = launch ? launch->block_threads : 0;
+  const size_t need = needed_ws(a.n, a.L.pver, prec, path);
+  if (need > 0) {
+    if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+      return CONV_ERR_WORKSPACE;
+  }
   cudaError_t e;
   if (path == CONV_PATH_PLAIN) {
     e = cvg::launch_plain(a, prec == CONV_FP64);
   } else {
-    return CONV_ERR_UNSUPPORTED;
+    e = cvg::launch_compact(a, prec == CONV_FP64, ws, ws_bytes);
   }
   return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
 }
@@ -153,10 +172,9 @@ const char* conv_status_str(conv_status s) {
 }
 
 size_t conv_workspace_bytes(const conv_grid* grid, conv_precision prec, const conv_launch* launch) {
-  (void)prec;
-  if (!grid || grid->n_cols < 0) return 0;
-  (void)launch;
-  return 0;
+  if (!grid || grid->n_cols < 0 || grid->pver < 1 || grid->pver > CONV_MAX_LEVELS) return 0;
+  if (prec != CONV_FP64 && prec != CONV_MIXED) return 0;
+  return needed_ws(grid->n_cols, grid->pver, prec, pick_path(launch, cvg::MODE_DEEP));
 }
 
 conv_status conv_deep_run(const conv_grid* grid, const conv_in* in, const conv_deep_params* par,

@@ -14,7 +14,7 @@ from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_repor
 
 pytestmark = pytest.mark.gpu
 
-PATHS = ["plain"]
+PATHS = ["plain", "compact"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -149,13 +149,68 @@ def test_mixed_precision_budget(oracle, latlon, path):
 
 
 @pytest.mark.parametrize("frac", [0.1, 0.3, 0.6])
-def test_full_resolution_grid_fp64(oracle, frac):
-    """884,736 columns x 30 levels, the launch the benchmark times: every column
-    against the oracle."""
+def test_full_resolution_grid(oracle, frac):
+    """884,736 columns x 30 levels, the launches the benchmark times: every column
+    of the FP64 paths against the oracle, the mixed compacted path against its
+    error budget."""
     g = S.clustered_grid(frac)
     rd, rs = oracle.deep_shallow(g, threads=THREADS)
-    gd, gs = run_gpu(g, "fp64", "plain")
-    assert_fp64_parity(gd, rd, what=f"deep f={frac}")
-    assert_fp64_parity(gs, rs, what=f"shallow f={frac}")
+    for path in PATHS:
+        gd, gs = run_gpu(g, "fp64", path)
+        assert_fp64_parity(gd, rd, what=f"deep f={frac} {path}")
+        assert_fp64_parity(gs, rs, what=f"shallow f={frac} {path}")
     trig = ((rd["flags"] & 1) > 0).mean()
     assert abs(trig - frac) < 0.02
+    m = layer_mass(g)
+    gd, gs = run_gpu(g, "mixed", "compact")
+    for tag, got, ref in (("deep", gd, rd), ("shallow", gs, rs)):
+        r = mixed_report(got, ref, m)
+        assert r["trigger_flips"] <= 1e-3 * r["n"], (tag, r)
+        assert r["decision_mismatch"] <= 1e-3 * r["n"], (tag, r)
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, (tag, r)
+        assert r["prec_max"] <= 1e-3, (tag, r)
+
+
+def test_compact_fp64_equals_plain_fp64_bitwise():
+    """The compacted FP64 path runs the same arithmetic per column as the plain
+    kernel (the shallow scheme reuses the deep LCL and parcel only when they are
+    the same computation), so every output is bit-identical."""
+    g = S.latlon_grid()
+    a = run_gpu(g, "fp64", "plain")
+    b = run_gpu(g, "fp64", "compact")
+    for x, y in zip(a, b):
+        for k in x:
+            assert np.array_equal(x[k], y[k], equal_nan=True), k
+
+
+def test_workspace_errors():
+    """Missing, short or misaligned workspaces are rejected on the host.  n_cols is
+    0, so even a wrongly accepted call would launch nothing."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1711_00289_gb300 import _lib as L
+    from paper_1711_00289_gb300 import api
+
+    g = S.column_set(64)
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    T, q, ps = (torch.tensor(x, device="cuda") for x in (g.T, g.q, g.ps))
+    out = api.new_outputs(30, 64, "fp64")
+    grid = vg.struct(0, 64)
+    inp = L.In(T.data_ptr(), q.data_ptr(), ps.data_ptr(), None, None)
+    o = api._out_struct(out, 30, 64, "fp64")
+    lc = L.Launch(L.CONV_PATH_COMPACT, 0, 0, 0)
+    dp = L.deep_defaults()
+    need = L.lib().conv_workspace_bytes(C.byref(grid), L.CONV_FP64, C.byref(lc))
+    assert need >= 256
+    buf = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+    base = buf.data_ptr() + ((-buf.data_ptr()) % 256)
+    run = L.lib().conv_deep_run
+    args = (C.byref(grid), C.byref(inp), C.byref(dp), 1800.0, L.CONV_FP64, C.byref(o),
+            C.byref(lc))
+    assert run(*args, None, need, None) == L.CONV_ERR_WORKSPACE
+    assert run(*args, C.c_void_p(base), need - 1, None) == L.CONV_ERR_WORKSPACE
+    assert run(*args, C.c_void_p(base + 8), need, None) == L.CONV_ERR_WORKSPACE
+    assert run(*args, C.c_void_p(base), need, None) == L.CONV_OK
+    torch.cuda.synchronize()
