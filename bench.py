@@ -2,8 +2,10 @@
 
 One step = one call of the fused deep->shallow path over the whole grid (the
 768 x 1152 resolution of the paper's R3 grid, Sec. V-A, with a clustered 30%
-convecting fraction), inputs resident in HBM (425 MB of FP64 profiles, larger
-than the 129 MB L2, so no L2 flush is needed between steps).
+convecting fraction), inputs resident in HBM (202 MB of FP32 / 405 MB of FP64
+profiles, larger than the 129 MB L2, so no L2 flush is needed between steps).
+Default: the mixed-precision compacted path; the plain FP64 kernel is timed
+beside it (the metric's reference point).
 
 Arms:
   default              the CUDA library (libconvgb.so) through the C ABI;
@@ -39,8 +41,10 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    p.add_argument("--path", default="plain", choices=["plain", "compact"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--path", default="compact", choices=["plain", "compact"])
+    p.add_argument("--no-baseline", action="store_true",
+                   help="skip timing the plain FP64 kernel beside the measured path")
     p.add_argument("--frac", type=float, default=0.30)
     p.add_argument("--nlat", type=int, default=768)
     p.add_argument("--nlon", type=int, default=1152)
@@ -107,34 +111,61 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline
 def op_counts(frac: float):
-    """Per-column algorithmic operation counts of the clustered workload with this
-    convecting fraction (per-column counts do not depend on the grid size)."""
+    """Per-column algorithmic operation counts (oracle counting instantiation,
+    oracle/op_counts.json) of the clustered workload with this convecting
+    fraction; per-column counts do not depend on the grid size."""
     path = os.path.join(ROOT, "oracle", "op_counts.json")
     with open(path) as fh:
         w = json.load(fh)["workloads"]
     key = min((k for k in w if k.startswith("clustered")),
               key=lambda k: abs(float(k.rsplit("-f", 1)[1]) - frac))
-    return w[key]["total_per_column"], key
+    return w[key], key
 
 
-def fp64_alu_roofline(counts, kernel_s, n_cols, L):
-    """Arithmetic roofline of an FP64 kernel: the time the algorithmic operation
-    counts need at the device's measured FP64 throughput per operation class
-    (adds and multiplies paired into FMAs), expressed in FMA-equivalent FLOP/s."""
-    r = {op: L.op_rate(op, L.CONV_ARITH_FP64) for op in
-         (L.CONV_OP_FMA, L.CONV_OP_EXP, L.CONV_OP_LOG, L.CONV_OP_DIV, L.CONV_OP_POW)}
-    t_col = (max(counts["add"], counts["mul"]) / r[L.CONV_OP_FMA]
-             + counts["div"] / r[L.CONV_OP_DIV] + counts["exp"] / r[L.CONV_OP_EXP]
-             + counts["log"] / r[L.CONV_OP_LOG] + counts["pow"] / r[L.CONV_OP_POW])
-    t_bound = t_col * n_cols
-    peak = 2.0 * r[L.CONV_OP_FMA]  # FLOP/s, one FMA = 2 FLOP
-    achieved = peak * t_bound / kernel_s
-    rates = {"fma": r[L.CONV_OP_FMA], "exp": r[L.CONV_OP_EXP], "log": r[L.CONV_OP_LOG],
-             "div": r[L.CONV_OP_DIV], "pow": r[L.CONV_OP_POW]}
-    return {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12,
-            "unit": "TFLOP/s (FP64 FMA-equivalent)", "frac": t_bound / kernel_s,
-            "traffic": None, "peak_source": "measured FP64 FMA rate (conv_bench_op_rate)",
-            "op_rates_per_s": rates}
+def device_rates(L):
+    """Measured evaluations/s per operation class on this device."""
+    r = {}
+    for name, arith in (("fp64", L.CONV_ARITH_FP64), ("fp32", L.CONV_ARITH_FP32_FAST)):
+        for op, k in ((L.CONV_OP_FMA, "fma"), (L.CONV_OP_EXP, "exp"), (L.CONV_OP_LOG, "log"),
+                      (L.CONV_OP_DIV, "div"), (L.CONV_OP_POW, "pow")):
+            r[f"{name}_{k}"] = L.op_rate(op, arith)
+    return r
+
+
+def t_ops(c, r, pfx):
+    """Lower-bound time of an operation mix at measured rates (adds and multiplies
+    paired into FMAs, each other class at its own measured throughput)."""
+    return (max(c["add"], c["mul"]) / r[pfx + "fma"] + c["div"] / r[pfx + "div"]
+            + c["exp"] / r[pfx + "exp"] + c["log"] / r[pfx + "log"] + c["pow"] / r[pfx + "pow"])
+
+
+# FP64 work of one LCL solve of the mixed design (the FP64 Newton correction:
+# residual, relative humidity and LCL pressure): 1 log, 1 exp, 4 div, 27 FMA.
+def t_fp64_islands(c, r):
+    lcl = (1 / r["fp64_log"] + 1 / r["fp64_exp"] + 4 / r["fp64_div"] + 27 / r["fp64_fma"])
+    terms = c["fp64_cape_terms"] + c["fp64_cin_terms"] + c["fp64_cons_terms"]
+    return c["fp64_lcl"] * lcl + 2 * terms / r["fp64_fma"]  # add + conversion per term
+
+
+def kernel_roofline(counts, precision, kernel_s, n_cols, r):
+    """Arithmetic roofline of one kernel: the time its algorithmic work needs on
+    the binding pipe at the measured per-operation throughput.  FP64 path: every
+    operation on the FP64 pipe.  Mixed path: the bulk on the FP32 pipes (fast
+    intrinsic rates, the lowest bound) and the FP64 islands on the FP64 pipe; the
+    larger of the two binds."""
+    if precision == "fp64":
+        t64, t32 = t_ops(counts, r, "fp64_") * n_cols, 0.0
+    else:
+        t64, t32 = t_fp64_islands(counts, r) * n_cols, t_ops(counts, r, "fp32_") * n_cols
+    fp64_binds = t64 >= t32
+    t_bound = t64 if fp64_binds else t32
+    peak = 2.0 * (r["fp64_fma"] if fp64_binds else r["fp32_fma"])
+    return {"bound": "alu", "binding_pipe": "fp64" if fp64_binds else "fp32",
+            "achieved": peak * t_bound / kernel_s / 1e12, "peak": peak / 1e12,
+            "unit": "TFLOP/s (FMA-equivalent on the binding pipe)",
+            "frac": t_bound / kernel_s, "t_bound_fp64_ms": t64 * 1e3,
+            "t_bound_fp32_ms": t32 * 1e3, "kernel_ms": kernel_s * 1e3, "traffic": None,
+            "peak_source": "measured FMA rate of the binding pipe (conv_bench_op_rate)"}
 
 
 def hbm_bytes_per_column(pver, real_bytes):
@@ -223,73 +254,98 @@ def ours_arm(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     g = S.clustered_grid(args.frac, args.nlat, args.nlon)
     n, pver = g.n_cols, g.pver
-    prec = args.precision
-    rd = api.real_dtype(prec)
     vg = api.VerticalGrid(g.hyai, g.hybi)
-    T = torch.tensor(g.T, device=dev).to(rd)
-    q = torch.tensor(g.q, device=dev).to(rd)
-    ps = torch.tensor(g.ps, device=dev)
-    od = api.new_outputs(pver, n, prec, dev)
-    os_ = api.new_outputs(pver, n, prec, dev)
-    ws = api.Workspace(dev)
     stream = torch.cuda.current_stream(dev)
+    ws = api.Workspace(dev)
+    bufs = {}
 
-    def step():
-        api.deep_shallow(T, q, ps, vg, dt=g.dt, precision=prec, path=args.path, out_deep=od,
-                         out_shallow=os_, workspace=ws, stream=stream)
+    def setup(prec):
+        if prec not in bufs:
+            rd = api.real_dtype(prec)
+            bufs[prec] = (torch.tensor(g.T, device=dev).to(rd), torch.tensor(g.q, device=dev).to(rd),
+                          torch.tensor(g.ps, device=dev), api.new_outputs(pver, n, prec, dev),
+                          api.new_outputs(pver, n, prec, dev))
+        return bufs[prec]
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    def step(prec, path, events=None):
+        T, q, ps, od, os_ = setup(prec)
+        api.deep_shallow(T, q, ps, vg, dt=g.dt, precision=prec, path=path, out_deep=od,
+                         out_shallow=os_, workspace=ws, stream=stream, stage_events=events)
+
+    def timed(prec, path, steps, warmup, per_kernel):
+        for _ in range(warmup):
+            step(prec, path)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        if per_kernel:
+            for e3 in evs:  # materialise the CUDA events outside the timed region
+                for e in e3:
+                    e.record(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0.record(stream)
+        for s_ in range(steps):
+            step(prec, path, evs[s_] if per_kernel else None)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        kern = None
+        if per_kernel:
+            kern = (statistics.mean(e[0].elapsed_time(e[1]) for e in evs),
+                    statistics.mean(e[1].elapsed_time(e[2]) for e in evs))
+        return ms, kern
+
+    prec, path = args.precision, args.path
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms, kern = timed(prec, path, args.steps, args.warmup, True)
     clk = clocks.stop()
-    launches_per_step = 1 if args.path == "plain" else 3
     if world > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
         ms = float(t.item())
     value = world * n / (ms * 1e-3)
+    od = setup(prec)[3]
+    act = int(((od["flags"] & 2) > 0).sum().item())
+
+    # the plain FP64 kernel, the reference point of the metric
+    base = None
+    if not args.no_baseline and not (prec == "fp64" and path == "plain"):
+        bms, _ = timed("fp64", "plain", max(2, min(args.steps, 5)), 2, False)
+        if world > 1:
+            t = torch.tensor([bms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            bms = float(t.item())
+        base = {"value": world * n / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms,
+                "path": "plain", "precision": "fp64"}
 
     # end to end through the public API from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        hT = torch.tensor(g.T).to(rd).pin_memory()
-        hq = torch.tensor(g.q).to(rd).pin_memory()
-        hps = torch.tensor(g.ps).pin_memory()
-        host_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory()
-                    for o in (od, os_) for k, v in o.items()}
-        names = [(i, k) for i, o in enumerate((od, os_)) for k in o]
+        T, q, ps, od_, os__ = setup(prec)
+        hT, hq, hps = (x.cpu().pin_memory() for x in (T, q, ps))
+        names = [(i, k) for i, o in enumerate((od_, os__)) for k in o]
         hout = {(i, k): torch.empty(o[k].shape, dtype=o[k].dtype).pin_memory()
-                for i, o in enumerate((od, os_)) for k in o}
-        del host_out
+                for i, o in enumerate((od_, os__)) for k in o}
 
         def e2e_step():
             T.copy_(hT, non_blocking=True)
             q.copy_(hq, non_blocking=True)
             ps.copy_(hps, non_blocking=True)
-            step()
+            step(prec, path)
             for (i, k) in names:
-                hout[(i, k)].copy_((od, os_)[i][k], non_blocking=True)
+                hout[(i, k)].copy_((od_, os__)[i][k], non_blocking=True)
 
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
         k2 = max(2, args.steps // 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k2):
             e2e_step()
@@ -303,16 +359,32 @@ def ours_arm(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    roof = None
-    if prec == "fp64":
-        counts, key = op_counts(args.frac)
-        roof = fp64_alu_roofline(counts, ms * 1e-3, n, L)
-        roof["op_counts_workload"] = key
-    roof = roof or {}
-    roof["hbm_algorithmic_bytes_per_column"] = hbm_bytes_per_column(pver, 8 if prec == "fp64"
-                                                                    else 4)
-    roof["hbm_frac_of_measured"] = (roof["hbm_algorithmic_bytes_per_column"] * n / (ms * 1e-3)
-                                    / 1e9 / measured_hbm())
+    counts, key = op_counts(args.frac)
+    r = device_rates(L)
+    kernels = {}
+    if path == "plain":
+        tot = {c: counts["trigger_pass_per_column"][c] + counts["plume_pass_per_column"][c]
+               for c in counts["trigger_pass_per_column"]}
+        if prec == "fp64":
+            tot.update(counts["total_per_column"])
+        kernels["k_plain"] = kernel_roofline(tot, prec, kern[0] * 1e-3, n, r)
+        kernels["k_plain"]["share"] = 1.0
+    else:
+        kt, kp = kern
+        kernels["k_trigger"] = kernel_roofline(counts["trigger_pass_per_column"], prec,
+                                               kt * 1e-3, n, r)
+        kernels["k_plume"] = kernel_roofline(counts["plume_pass_per_column"], prec, kp * 1e-3,
+                                             n, r)
+        kernels["k_trigger"]["share"] = kt / (kt + kp)
+        kernels["k_plume"]["share"] = kp / (kt + kp)
+    dom = max(kernels, key=lambda k: kernels[k]["share"])
+    roof = dict(kernels[dom])
+    roof["kernel"] = dom
+    roof["op_counts_workload"] = key
+    rb = 8 if prec == "fp64" else 4
+    roof["hbm_algorithmic_bytes_per_column"] = hbm_bytes_per_column(pver, rb)
+    roof["hbm_frac_of_measured_path"] = (hbm_bytes_per_column(pver, rb) * n / (ms * 1e-3) / 1e9
+                                         / measured_hbm())
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, ncols, threads, el = cpu_oracle_rate(g, args.cpu_seconds)
@@ -320,7 +392,6 @@ def ours_arm(args, rank, world, local_rank):
                "sample": f"{ncols} column evaluations of this grid (strided sample, repeated) "
                          f"in {el:.1f} s, FP64 oracle, OpenMP dynamic(8) on {threads} threads, "
                          f"{cpu_model()}"}
-    act = int(((od["flags"] & 2) > 0).sum().item())
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -328,13 +399,22 @@ def ours_arm(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": g.name, "columns": n, "levels": pver,
                        "convecting_fraction": args.frac, "deep_active_columns": act,
-                       "precision": prec, "path": args.path, "dt_s": g.dt,
-                       "l2": "inputs (%d MB) larger than L2; no flush" % (
-                           (T.numel() + q.numel()) * T.element_size() // 2**20),
-                       "parallelism": f"replicas x{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches_per_step * args.steps}
+                       "precision": prec, "path": path, "dt_s": g.dt,
+                       "l2": l2_note(prec, n, pver), "parallelism": f"replicas x{world}"},
+            "baseline_fp64_plain": base,
+            "speedup_vs_fp64_plain": (value / base["value"]) if base else None,
+            "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk, "gpu_launches": (1 if path == "plain" else 2) * args.steps,
+            "op_rates_per_s": r}
     print(json.dumps(line), flush=True)
+
+
+def l2_note(prec, n, pver):
+    mb = 2 * pver * n * (8 if prec == "fp64" else 4) / 2**20
+    if mb > 129:
+        return f"profile inputs ({mb:.0f} MB) larger than the 129 MB L2; no flush"
+    return (f"profile inputs ({mb:.0f} MB) fit in L2: timings of this small case are not "
+            f"HBM-representative")
 
 
 def measured_hbm():

@@ -45,6 +45,7 @@
  *   bit 1  CONV_FLAG_ACTIVE     scheme produced non-zero tendencies
  *   bit 2  CONV_FLAG_LIMITED    deep mass flux cut by the q >= q_min limiter
  *   bit 3  CONV_FLAG_NEWTON     a Newton solve's last correction exceeded 1e-4 K
+ *                               (FP64; 1e-3 K in the mixed path, above FP32 noise)
  *   bit 4  CONV_FLAG_BADINPUT   T outside (100, 400) K, q outside [0, 0.1),
  *                               ps outside (5e4, 1.2e5) Pa or not finite;
  *                               all outputs of the column are zero
@@ -165,14 +166,20 @@ typedef struct {
 /* Kernel variant.  CONV_PATH_PLAIN: one thread per column runs the whole scheme
  * (no compaction; the FP64 baseline).  CONV_PATH_COMPACT: a trigger pass over
  * all columns compacts the convecting ones into device queues (warp ballot,
- * one atomic per warp) and plume passes run only over the queues.
- * block_threads 0 = library default. */
+ * one atomic per warp) and plume passes run only over the queues.  AUTO is
+ * COMPACT for runs that include the deep scheme, PLAIN for shallow-only runs.
+ * block_threads 0 = library default.
+ * stage_events (optional, may be NULL): three caller-created cudaEvent_t the
+ * library records on `stream` -- [0] before its first kernel, [1] after the
+ * trigger pass (plain path: after its only kernel), [2] after its last kernel
+ * -- so a caller can time each pass; recording changes no work. */
 typedef enum { CONV_PATH_AUTO = 0, CONV_PATH_PLAIN = 1, CONV_PATH_COMPACT = 2 } conv_path;
 typedef struct {
   int32_t path;
   int32_t block_threads;
   int32_t reserved0;
   int32_t reserved1;
+  void* const* stage_events;
 } conv_launch;
 
 /* Fill parameter structs with the defaults listed above. */

@@ -155,6 +155,25 @@ inline Cnt log(const Cnt& a) { g_count[C_LOG] += 1; return Cnt(std::log(a.v)); }
 inline Cnt sqrt(const Cnt& a) { g_count[C_SQRT] += 1; return Cnt(std::sqrt(a.v)); }
 inline Cnt pow(const Cnt& a, double e) { g_count[C_POW] += 1; return Cnt(std::pow(a.v, e)); }
 
+// FP64-island work of the mixed-precision design, tallied by the counting
+// instantiation only: LCL solves (each ends with one FP64 Newton correction),
+// CAPE terms and CIN terms accumulated in FP64, conservation-sum terms.
+enum { I_LCL = 0, I_CAPE, I_CIN, I_CONS, I_NCAT };
+thread_local double g_island[I_NCAT];
+// Snapshot of g_count when the deep trigger stage ends (launch level through
+// the CAPE trigger): splits the deep work between the trigger and plume passes.
+thread_local double g_mark[C_NCAT];
+template <class R>
+inline void island(int, double) {}
+template <>
+inline void island<Cnt>(int cat, double n) { g_island[cat] += n; }
+template <class R>
+inline void mark_trigger_end() {}
+template <>
+inline void mark_trigger_end<Cnt>() {
+  for (int c = 0; c < C_NCAT; ++c) g_mark[c] = g_count[c];
+}
+
 // ---------------------------------------------------------------- parameters
 struct DeepP {
   double capelmt, lambda_default, tau_default, c0, alpha_dd, p_launch_min, p_top_lim, q_min,
@@ -384,8 +403,10 @@ void deep_column(int pver, const double* hyai, const double* hybi, double p0, co
 
   const R Tb = T[kb], qb = q[kb], pb = s.p_mid[kb];
   s.newton_max = std::max(s.newton_max, lcl(Tb, qb, pb, P.n_lcl, s.TL, s.pL));
+  island<R>(I_LCL, 1);
   const int klcl = lcl_level(s.p_mid, kb, s.pL);
   s.klcl = klcl;
+  mark_trigger_end<R>();
   if (klcl < ktl) return;  // LCL missing or above the top limit: no convection
 
   // Undilute parcel on levels ktl..klcl (saturated branch) and buoyancy.
@@ -406,11 +427,14 @@ void deep_column(int pver, const double* hyai, const double* hybi, double p0, co
   for (int k = ktl; k <= klcl; ++k)
     if (val(s.b[k]) > 0.0) { kel = k; break; }
   s.kel = kel;
+  mark_trigger_end<R>();
   if (kel < 0) return;
   R cape(0.0);
   for (int k = klcl; k >= kel; --k) cape = cape + RD * s.b[k] * s.dlnp[k];
+  island<R>(I_CAPE, klcl - kel + 1);
   if (val(cape) < 0.0) cape = R(0.0);
   s.cape = cape;
+  mark_trigger_end<R>();
   if (!(val(cape) > P.capelmt)) return;
   s.triggered = true;
 
@@ -529,6 +553,7 @@ void deep_column(int pver, const double* hyai, const double* hybi, double p0, co
   }
   s.active = true;
   s.mb = mb;
+  island<R>(I_CONS, 2.0 * (kb - jt + 1));
   for (int k = 0; k < pver; ++k) {
     s.dTdt[k] = mb * s.dT[k];
     s.dqdt[k] = mb * s.dq[k];
@@ -605,6 +630,7 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
   const int ks = pver - 1;
   const R Ts = T[ks], qsrc = q[ks], psrc = s.p_mid[ks];
   s.newton_max = std::max(s.newton_max, lcl(Ts, qsrc, psrc, P.n_lcl, s.TL, s.pL));
+  island<R>(I_LCL, 1);
   const int klcl = lcl_level(s.p_mid, ks, s.pL);
   s.klcl = klcl;
   if (val(s.pL) < P.p_lcl_min || klcl < ktl) { s.exit_code = 1; return; }
@@ -631,6 +657,7 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
   for (int k = ks; k > klfc; --k) {
     R neg = -s.b[k];
     if (val(neg) < 0.0) neg = R(0.0);
+    if (val(neg) > 0.0) island<R>(I_CIN, 1);
     cin = cin + RD * neg * s.dlnp[k];
   }
   s.cin = cin;
@@ -702,6 +729,7 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
   }
   s.active = true;
   s.mb = mb;
+  island<R>(I_CONS, 2.0 * (ks - kts + 1));
 
   // Tendencies: m_k dphi_k = [U_k+1 phi_u,k+1 - U_k phi~_k] + [U_k phi_k-1 - U_k+1 phi_k],
   // U = M_b through the interfaces kts+1..ks, phi~ the pre-rain plume value.
@@ -992,6 +1020,60 @@ int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const dou
     for (int c = 0; c < C_NCAT; ++c) counts_deep[c] = deep[c];
   if (counts_total)
     for (int c = 0; c < C_NCAT; ++c) counts_total[c] = tot[c];
+  return 0;
+}
+
+int oracle_count_ops_by_pass(int n_cols, int pver, int ld, const double* hyai,
+                             const double* hybi, double p0, const double* T, const double* q,
+                             const double* ps, const oracle_deep_params* dpar,
+                             const oracle_shallow_params* spar, double dt, double* trigger_pass,
+                             double* plume_pass, double* n_triggered) {
+  if (!grid_ok(n_cols, pver, ld) || !dpar || !spar || !trigger_pass || !plume_pass) return 1;
+  const DeepP DP = to_deep(dpar);
+  const ShalP SP = to_shal(spar);
+  const int W = C_NCAT + I_NCAT;
+  for (int c = 0; c < W; ++c) trigger_pass[c] = plume_pass[c] = 0.0;
+  double ntrig = 0.0;
+  std::unique_ptr<DeepState<Cnt>> sp(new DeepState<Cnt>());
+  std::unique_ptr<ShalState<Cnt>> tp(new ShalState<Cnt>());
+  for (int i = 0; i < n_cols; ++i) {
+    Cnt Tc[MAXLEV], qc[MAXLEV], T2[MAXLEV], q2[MAXLEV];
+    for (int k = 0; k < pver; ++k) { Tc[k] = Cnt(T[k * ld + i]); qc[k] = Cnt(q[k * ld + i]); }
+    for (int c = 0; c < C_NCAT; ++c) g_count[c] = g_mark[c] = 0.0;
+    for (int c = 0; c < I_NCAT; ++c) g_island[c] = 0.0;
+    *sp = DeepState<Cnt>();  // the column routines expect freshly constructed states
+    *tp = ShalState<Cnt>();
+    DeepState<Cnt>& s = *sp;
+    deep_column<Cnt>(pver, hyai, hybi, p0, Tc, qc, Cnt(ps[i]), Cnt(DP.lambda_default),
+                     Cnt(DP.tau_default), DP, dt, s);
+    double deep_ops[C_NCAT], deep_isl[I_NCAT];
+    for (int c = 0; c < C_NCAT; ++c) deep_ops[c] = g_count[c];
+    for (int c = 0; c < I_NCAT; ++c) deep_isl[c] = g_island[c];
+    const bool trig = s.triggered;
+    // trigger stage (all columns); the rest of the deep scheme runs in the plume pass
+    for (int c = 0; c < C_NCAT; ++c) {
+      const double mark = s.bad ? 0.0 : (trig ? g_mark[c] : deep_ops[c]);
+      trigger_pass[c] += mark;
+      plume_pass[c] += deep_ops[c] - mark;
+    }
+    for (int c = 0; c < I_NCAT; ++c) {
+      if (c == I_CONS) plume_pass[C_NCAT + c] += deep_isl[c];
+      else trigger_pass[C_NCAT + c] += deep_isl[c];
+    }
+    for (int k = 0; k < pver; ++k) {
+      T2[k] = Tc[k] + dt * s.dTdt[k].v;
+      q2[k] = qc[k] + dt * s.dqdt[k].v;
+      if (!s.bad && q2[k].v < 0.0) q2[k] = Cnt(0.0);
+    }
+    for (int c = 0; c < C_NCAT; ++c) g_count[c] = 0.0;
+    for (int c = 0; c < I_NCAT; ++c) g_island[c] = 0.0;
+    shallow_column<Cnt>(pver, hyai, hybi, p0, T2, q2, Cnt(ps[i]), SP, *tp);
+    double* dst = trig ? plume_pass : trigger_pass;
+    for (int c = 0; c < C_NCAT; ++c) dst[c] += g_count[c];
+    for (int c = 0; c < I_NCAT; ++c) dst[C_NCAT + c] += g_island[c];
+    ntrig += trig ? 1.0 : 0.0;
+  }
+  if (n_triggered) *n_triggered = ntrig;
   return 0;
 }
 

@@ -122,6 +122,18 @@ int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const dou
                      const oracle_deep_params* dpar, const oracle_shallow_params* spar,
                      double dt, double* counts_deep, double* counts_total);
 
+/* The same counts split by the two passes of a compacted GPU implementation:
+ * trigger_pass = deep trigger stage of every column + the shallow scheme of the
+ * columns that do not trigger; plume_pass = the rest of the deep scheme and the
+ * shallow scheme of the triggered columns.  Each array has 12 entries: the 8
+ * operation categories, then FP64-island tallies of the mixed-precision design:
+ * [8] LCL solves, [9] CAPE terms, [10] CIN terms, [11] conservation-sum terms. */
+int oracle_count_ops_by_pass(int n_cols, int pver, int ld, const double* hyai,
+                             const double* hybi, double p0, const double* T, const double* q,
+                             const double* ps, const oracle_deep_params* dpar,
+                             const oracle_shallow_params* spar, double dt, double* trigger_pass,
+                             double* plume_pass, double* n_triggered);
+
 #ifdef __cplusplus
 }
 #endif

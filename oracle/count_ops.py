@@ -14,16 +14,24 @@ from oracle import oracle as O  # noqa: E402
 from paper_1711_00289_gb300 import soundings as S  # noqa: E402
 
 CATS = ["add", "mul", "div", "exp", "log", "pow", "sqrt"]
+PASS_CATS = CATS + ["unused", "fp64_lcl", "fp64_cape_terms", "fp64_cin_terms",
+                    "fp64_cons_terms"]
 
 
 def counts(g, stride=1):
     sub = S.Columns(g.name, g.pver, g.T[:, ::stride].copy(), g.q[:, ::stride].copy(),
                     g.ps[::stride].copy(), g.hyai, g.hybi)
     cd, ct = O.count_ops(sub)
+    a, b, nt = O.count_ops_by_pass(sub)
     n = sub.n_cols
-    return {"columns_counted": n,
+    return {"columns_counted": n, "triggered_fraction": nt / n,
             "deep_per_column": {c: cd[i] / n for i, c in enumerate(CATS)},
-            "total_per_column": {c: ct[i] / n for i, c in enumerate(CATS)}}
+            "total_per_column": {c: ct[i] / n for i, c in enumerate(CATS)},
+            # per column of the whole grid, split by pass of the compacted path
+            "trigger_pass_per_column": {c: a[i] / n for i, c in enumerate(PASS_CATS)
+                                        if c != "unused"},
+            "plume_pass_per_column": {c: b[i] / n for i, c in enumerate(PASS_CATS)
+                                      if c != "unused"}}
 
 
 def main():

@@ -140,8 +140,10 @@ def lib():
                                           d, p, p, p, p, p, p, p, i]
         L.oracle_count_ops.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                        C.POINTER(ShallowParams), d, p, p]
+        L.oracle_count_ops_by_pass.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
+                                               C.POINTER(ShallowParams), d, p, p, p]
         for fn in ("oracle_deep", "oracle_shallow", "oracle_deep_shallow", "oracle_deep_adjoint",
-                   "oracle_count_ops"):
+                   "oracle_count_ops", "oracle_count_ops_by_pass"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -256,6 +258,21 @@ def count_ops(g, dpar=None, spar=None, dt=None):
                                 _ptr(ct))
     assert rc == 0
     return cd, ct
+
+
+def count_ops_by_pass(g, dpar=None, spar=None, dt=None):
+    """(trigger_pass[12], plume_pass[12], n_triggered) summed over g's columns."""
+    dpar = dpar or deep_params()
+    spar = spar or shallow_params()
+    dt = g.dt if dt is None else dt
+    T, q, ps = _c64(g.T), _c64(g.q), _c64(g.ps)
+    a, b, nt = np.zeros(12), np.zeros(12), np.zeros(1)
+    hyai, hybi = _c64(g.hyai), _c64(g.hybi)
+    rc = lib().oracle_count_ops_by_pass(g.n_cols, g.pver, g.n_cols, _ptr(hyai), _ptr(hybi), 1e5,
+                                        _ptr(T), _ptr(q), _ptr(ps), C.byref(dpar), C.byref(spar),
+                                        dt, _ptr(a), _ptr(b), _ptr(nt))
+    assert rc == 0
+    return a, b, float(nt[0])
 
 
 def deep_column_diag(pver, hyai, hybi, T, q, ps, lam=1e-3, tau=3600.0, par=None, dt=1800.0):

@@ -62,7 +62,7 @@ class Out(C.Structure):
 
 class Launch(C.Structure):
     _fields_ = [("path", C.c_int32), ("block_threads", C.c_int32), ("reserved0", C.c_int32),
-                ("reserved1", C.c_int32)]
+                ("reserved1", C.c_int32), ("stage_events", C.POINTER(C.c_void_p))]
 
 
 _lib = None

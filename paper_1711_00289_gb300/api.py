@@ -86,8 +86,20 @@ class VerticalGrid:
                       self.hybi.ctypes.data_as(dp), self.p0)
 
 
-def _launch(path: str, block_threads: int = 0) -> L.Launch:
-    return L.Launch(_PATH[path], int(block_threads), 0, 0)
+def _launch(path: str, block_threads: int = 0, stage_events=None) -> L.Launch:
+    lc = L.Launch(_PATH[path], int(block_threads), 0, 0, None)
+    if stage_events is not None:
+        if len(stage_events) != 3:
+            raise ValueError("stage_events needs three torch.cuda.Event")
+        handles = []
+        for ev in stage_events:
+            if ev.cuda_event == 0:  # torch creates the CUDA event lazily
+                ev.record()
+            handles.append(ev.cuda_event)
+        arr = (C.c_void_p * 3)(*handles)
+        lc._keep = arr
+        lc.stage_events = C.cast(arr, C.POINTER(C.c_void_p))
+    return lc
 
 
 def workspace_bytes(vgrid: VerticalGrid, n_cols: int, ld: int, precision="fp64",
@@ -155,17 +167,18 @@ def _stream(stream):
 def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64",
                  lam=None, tau=None, deep_params=None, shallow_params=None, path="auto",
                  block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
-                 workspace: Workspace | None = None, stream=None):
+                 workspace: Workspace | None = None, stream=None, stage_events=None):
     """Deep then shallow convection (Alg. 1 order) in one fused call.
 
-    Returns ``(deep_out, shallow_out)`` dicts of output tensors."""
+    Returns ``(deep_out, shallow_out)`` dicts of output tensors.  stage_events:
+    optional three torch.cuda.Event the library records around its passes."""
     pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
     od = out_deep if out_deep is not None else new_outputs(pver, ld, precision, T.device)
     os_ = out_shallow if out_shallow is not None else new_outputs(pver, ld, precision, T.device)
     dp = deep_params or L.deep_defaults()
     sp = shallow_params or L.shallow_defaults()
     g = vgrid.struct(n, ld)
-    lc = _launch(path, block_threads)
+    lc = _launch(path, block_threads, stage_events)
     nb = int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
     wp, wn = _ws_for(T.device, workspace).get(nb)
     st = L.lib().conv_deep_shallow_run(

@@ -59,8 +59,7 @@ constexpr double ESA = 17.67;
 constexpr double EST0 = 273.15;
 constexpr double EST1 = 29.65;
 constexpr double ESC = 243.5;
-constexpr double LN_ES0 = 6.415424628734003;  // ln(611.2)
-constexpr double NEWTON_TOL = 1e-4;           // K
+constexpr double LN_ES0 = 6.415424237852311;  // ln(611.2), correctly rounded
 constexpr int MAXL = CONV_MAX_LEVELS;
 constexpr int kWarmSteps = 3;  // Newton steps after the tangent predictor (mixed path)
 
@@ -82,9 +81,14 @@ struct Levels {
 // exp(-CIN) closure, so they use the accurate FP32 library functions.
 template <class R>
 struct Mth;
+// newton_tol: a Newton solve whose last correction exceeds it sets
+// CONV_FLAG_NEWTON (K); in FP32 the residual cp T + gz + Lv qs - h of a
+// converged solve still carries ~0.05 J/kg of rounding, i.e. ~5e-5 K.
 template <>
 struct Mth<double> {
   static constexpr bool warm = false;
+  static constexpr bool anomaly = false;
+  static constexpr float newton_tol = 1e-4f;
   static __device__ __forceinline__ double es(double x) { return exp(x); }
   static __device__ __forceinline__ double ex(double x) { return exp(x); }
   static __device__ __forceinline__ double lg(double x) { return log(x); }
@@ -95,10 +99,15 @@ struct Mth<double> {
 template <>
 struct Mth<float> {
   static constexpr bool warm = true;
+  static constexpr bool anomaly = true;
+  static constexpr float newton_tol = 1e-3f;
   static __device__ __forceinline__ float es(float x) { return expf(x); }
   static __device__ __forceinline__ float ex(float x) { return __expf(x); }
   static __device__ __forceinline__ float lg(float x) { return logf(x); }
-  static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+  // IEEE division: with the approximate __fdividef the moist-inversion Newton
+  // iteration on this device converged only linearly (final corrections of
+  // 1e-3 K after three steps, against 3e-5 K with IEEE division).
+  static __device__ __forceinline__ float dv(float a, float b) { return a / b; }
   static __device__ __forceinline__ float pw(float a, float b) { return powf(a, b); }
   static __device__ __forceinline__ float ab(float a) { return fabsf(a); }
 };
@@ -112,6 +121,8 @@ __device__ __forceinline__ double virt(double T, double q) {
 __device__ __forceinline__ float virt(float T, float q) {
   return __fmul_rn(T, __fadd_rn(1.0f, __fmul_rn((float)ZVIR, q)));
 }
+
+__device__ __forceinline__ float fdiv_ieee(float a, float b) { return a / b; }
 
 // ---------------------------------------------------------------- thermodynamics
 // Saturation specific humidity, its T derivative (branch-consistent clamp) and
@@ -154,9 +165,10 @@ struct MoistSeq {
   R T, qs, dqs, rD, p, gz, h;
 };
 
+// h is relative to the column reference cp Tref + Lv qref (see Column).
 template <class R>
 __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, MoistSeq<R>& s,
-                                          float& newton) {
+                                          float& newton, R Tref, R qref) {
   R T;
   int steps;
   if (Mth<R>::warm && s.have) {
@@ -170,7 +182,7 @@ __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, Mois
   R step = R(0), qs = R(0), dqs = R(0), rD = R(0);
   for (int it = 0; it < steps; ++it) {
     sat_qs_dqs(T, p, qs, dqs, rD);
-    const R f = R(CP) * T + gz + R(LV) * qs - h;
+    const R f = R(CP) * (T - Tref) + gz + R(LV) * (qs - qref) - h;
     const R fp = R(CP) + R(LV) * dqs;
     step = Mth<R>::dv(f, fp);
     T -= step;
@@ -236,22 +248,22 @@ __device__ __forceinline__ double ln_ratio(double x, double y) {
 __device__ __forceinline__ double lcl_p(float Tb, float qb, float pb, int n_newton,
                                         float& newton) {
   const float esb =
-      (float)ES0 * expf(__fdividef((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
+      (float)ES0 * expf(fdiv_ieee((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
   float Db = pb - (float)ONE_M_EPS * esb;
   if (Db < 1e-3f * pb) Db = 1e-3f * pb;
-  if (qb >= __fdividef((float)EPSV * esb, Db)) return (double)pb;
+  if (qb >= fdiv_ieee((float)EPSV * esb, Db)) return (double)pb;
   const double Tbd = Tb, qbd = qb, pbd = pb;
   const double eb = qbd * pbd / (EPSV + ONE_M_EPS * qbd);
   const double lnrh = log(eb) - (LN_ES0 + ESA * (Tbd - EST0) / (Tbd - EST1));
   const float lnrhf = (float)lnrh;
-  const float c1 = __fdividef((float)(ESA * ESC), Tb - (float)EST1);
-  float T = __fdividef(1.f, __fdividef(1.f, Tb - 55.f) - lnrhf * (1.f / 2840.f)) + 55.f;
+  const float c1 = fdiv_ieee((float)(ESA * ESC), Tb - (float)EST1);
+  float T = fdiv_ieee(1.f, fdiv_ieee(1.f, Tb - 55.f) - lnrhf * (1.f / 2840.f)) + 55.f;
   float rGp = 0.f;
   for (int it = 0; it < n_newton; ++it) {
-    const float r = __fdividef(1.f, T - (float)EST1);
-    const float G = c1 * (T - Tb) * r - lnrhf - (float)INV_KAPPA * logf(__fdividef(T, Tb));
-    const float Gp = (float)(ESA * ESC) * r * r - __fdividef((float)INV_KAPPA, T);
-    rGp = __fdividef(1.f, Gp);
+    const float r = fdiv_ieee(1.f, T - (float)EST1);
+    const float G = c1 * (T - Tb) * r - lnrhf - (float)INV_KAPPA * logf(fdiv_ieee(T, Tb));
+    const float Gp = (float)(ESA * ESC) * r * r - fdiv_ieee((float)INV_KAPPA, T);
+    rGp = fdiv_ieee(1.f, Gp);
     T -= G * rGp;
   }
   const double Td = T;
@@ -260,7 +272,7 @@ __device__ __forceinline__ double lcl_p(float Tb, float qb, float pb, int n_newt
   const double step = G * (double)rGp;
   newton = fmaxf(newton, (float)fabs(step));
   // ln(TL/Tb) = ln(T/Tb) - step/T to second order in the (tiny) step
-  return pbd * exp(INV_KAPPA * (lr - step * (double)__fdividef(1.f, T)));
+  return pbd * exp(INV_KAPPA * (lr - step * (double)fdiv_ieee(1.f, T)));
 }
 
 // Entraining mass-flux profile (1 + dz/z_e)^(lambda z_e).
@@ -270,11 +282,18 @@ __device__ __forceinline__ R entrain_growth(R lam, R ze, R dz) {
 }
 
 // ---------------------------------------------------------------- column state
+// Column state.  Moist static energies h, hs (and every plume MSE derived from
+// them) are stored relative to cp Tref + Lv qref: in the mixed path (Tref,
+// qref) is the lowest layer's (T, q), so FP32 resolves MSE differences to
+// ~1e-3 J/kg instead of the 0.03 J/kg ulp of 3.4e5 J/kg; in the FP64 path the
+// reference is zero.  The reference cancels in every mixing rule, difference
+// and Newton residual.
 template <class R>
 struct Column {
   R T[MAXL], q[MAXL];
   R p_mid[MAXL], dlnp[MAXL], m[MAXL];
   R z_mid[MAXL], z_int[MAXL + 1], Tv[MAXL], h[MAXL], hs[MAXL];
+  R Tref, qref;
   int pver, ktl;
   double ps;
 };
@@ -332,6 +351,8 @@ __device__ __forceinline__ void prologue(const Levels& L, double p_top_lim, Colu
   R pi_lo = P.pi(pver);
   R zi = R(0);
   c.z_int[pver] = R(0);
+  c.Tref = Mth<R>::anomaly ? c.T[pver - 1] : R(0);
+  c.qref = Mth<R>::anomaly ? c.q[pver - 1] : R(0);
   int ktl = pver - 1;
   for (int k = pver - 1; k >= 0; --k) {
     const R pi_hi = P.pi(k);
@@ -347,9 +368,9 @@ __device__ __forceinline__ void prologue(const Levels& L, double p_top_lim, Colu
     zi = zi + scale * dl;
     c.z_int[k] = zi;
     c.z_mid[k] = zm;
-    const R sdry = R(CP) * c.T[k] + R(GRAV) * zm;
-    c.h[k] = sdry + R(LV) * c.q[k];
-    if (need_hs) c.hs[k] = sdry + R(LV) * sat_qs(c.T[k], pm);
+    const R sdry = R(CP) * (c.T[k] - c.Tref) + R(GRAV) * zm;
+    c.h[k] = sdry + R(LV) * (c.q[k] - c.qref);
+    if (need_hs) c.hs[k] = sdry + R(LV) * (sat_qs(c.T[k], pm) - c.qref);
     if (pm >= ptl) ktl = k;
     pi_lo = pi_hi;
   }
@@ -405,7 +426,7 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   double cape = 0.0;
   for (int k = klcl; k >= ktl; --k) {
     const R Tp = moist_invert(hb, R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h, seq,
-                              t.newton);
+                              t.newton, c.Tref, c.qref);
     t.Tp[k] = Tp;
     const R b = virt(Tp, sat_qs(Tp, c.p_mid[k])) - c.Tv[k];
     run += (double)(R(RD) * b * c.dlnp[k]);
@@ -455,7 +476,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
     }
     const R qt = (eta[k + 1] * qtu[k + 1] + de * c.q[k]) * re;
     const R Ts = moist_invert(hu[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                              seq, t.newton);
+                              seq, t.newton, c.Tref, c.qref);
     R l = qt - sat_qs(Ts, c.p_mid[k]);
     if (l < R(0)) l = R(0);
     const R dz = c.z_int[k] - c.z_int[k + 1];
@@ -480,7 +501,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
       etad[k] = e;
       hd[k] = (k == jd) ? c.h[jd] : Mth<R>::dv(eprev * hd[k - 1] + (e - eprev) * c.h[k], e);
       const R Td = moist_invert(hd[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                                seq, t.newton);
+                                seq, t.newton, c.Tref, c.qref);
       qd[k] = sat_qs(Td, c.p_mid[k]);
       sumE += e * qd[k] - eprev * qprev - (e - eprev) * c.q[k];
       qprev = qd[k];
@@ -587,7 +608,7 @@ __device__ __forceinline__ void deep_column(const Levels& L, const conv_deep_par
     o.flags |= CONV_FLAG_TRIGGERED;
     deep_plume(c, P, dt, lam, tau, t, o);
   }
-  if (t.newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+  if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
 }
 
 // ---------------------------------------------------------------- shallow scheme
@@ -662,7 +683,7 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
       } else {
         Tp = seed ? seed->Tp[k]
                   : moist_invert(c.h[ks], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k],
-                                 P.n_newton_h, seq, newton);
+                                 P.n_newton_h, seq, newton, c.Tref, c.qref);
         qp = sat_qs(Tp, c.p_mid[k]);
       }
       const R b = virt(Tp, qp) - c.Tv[k];
@@ -706,14 +727,15 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
           qpre[k] = qt;
           rf[k] = R(0);
           const R gz = R(GRAV) * c.z_mid[k];
-          const R Tsat = moist_invert(hu[k], gz, c.p_mid[k], c.T[k], P.n_newton_h, seq, newton);
+          const R Tsat =
+              moist_invert(hu[k], gz, c.p_mid[k], c.T[k], P.n_newton_h, seq, newton, c.Tref, c.qref);
           const R qsu = sat_qs(Tsat, c.p_mid[k]);
           R Tu, qv;
           if (qt >= qsu) {
             Tu = Tsat;
             qv = qsu;
           } else {
-            Tu = (hu[k] - gz - R(LV) * qt) * R(1.0 / CP);
+            Tu = c.Tref + (hu[k] - gz - R(LV) * (qt - c.qref)) * R(1.0 / CP);
             qv = qt;
           }
           if (k < klfc) {
@@ -744,7 +766,7 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
   }
   if (exit_code == 0 || exit_code == 4) o.flags |= CONV_FLAG_TRIGGERED;
   o.flags |= exit_code << CONV_EXIT_SHIFT;
-  if (newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+  if (newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   if (exit_code != 0) return;
 
   // tendencies of the constant-mass-flux plume

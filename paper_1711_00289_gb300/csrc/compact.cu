@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<
       o.klcl = t.klcl;
       o.cape = t.cape;
       if (t.triggered) o.flags |= CONV_FLAG_TRIGGERED;
-      if (t.newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+      if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
     }
   }
   // queue append: one atomic per warp, slots in lane order
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R>
   const R lam = (R)(a.lam ? a.lam[i] : a.dp.lambda_default);
   const R tau = (R)(a.tau ? a.tau[i] : a.dp.tau_default);
   deep_plume(c, a.dp, a.dt, lam, tau, t, o);
-  if (t.newton > NEWTON_TOL) o.flags |= CONV_FLAG_NEWTON;
+  if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   store_deep(a, i, o, true);
   if (!(a.mode & MODE_SHALLOW)) return;
   for (int k = 0; k < c.pver; ++k) {
@@ -207,14 +207,18 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   w.levels = reinterpret_cast<int*>(base + off.levels);
   w.cape = reinterpret_cast<double*>(base + off.cape);
   w.Tp = reinterpret_cast<R*>(base + off.Tp);
+  record_stage(a, 0);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
   if (e != cudaSuccess) return e;
   const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
   k_trigger<R><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  record_stage(a, 1);
   k_plume<R><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  record_stage(a, 2);
+  return e;
 }
 
 cudaError_t launch_compact(const RunArgs& a, bool fp64, void* ws, size_t ws_bytes) {

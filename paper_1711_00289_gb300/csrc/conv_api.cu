@@ -94,6 +94,10 @@ conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch,
   if (launch && (launch->block_threads < 0 || launch->block_threads > 1024)) return CONV_ERR_ARG;
   const int path = pick_path(launch, a.mode);
   a.block = launch ? launch->block_threads : 0;
+  for (int i = 0; i < 3; ++i)
+    a.ev[i] = (launch && launch->stage_events)
+                  ? static_cast<cudaEvent_t>(launch->stage_events[i])
+                  : nullptr;
   const size_t need = needed_ws(a.n, a.L.pver, prec, path);
   if (need > 0) {
     if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)

@@ -41,7 +41,12 @@ struct RunArgs {
   int mode;
   int block;
   cudaStream_t stream;
+  cudaEvent_t ev[3];  // optional stage events (nullptr = none)
 };
+
+inline void record_stage(const RunArgs& a, int i) {
+  if (a.ev[i]) cudaEventRecord(a.ev[i], a.stream);
+}
 
 // Plain path: one thread per column, whole scheme, no compaction.
 cudaError_t launch_plain(const RunArgs& a, bool fp64);

@@ -88,11 +88,15 @@ cudaError_t launch_plain(const RunArgs& a, bool fp64) {
   if (a.n == 0) return cudaSuccess;
   const int block = 128;
   const int grid = (a.n + block - 1) / block;
+  record_stage(a, 0);
   if (fp64)
     k_plain<double><<<grid, block, 0, a.stream>>>(a);
   else
     k_plain<float><<<grid, block, 0, a.stream>>>(a);
-  return cudaGetLastError();
+  const cudaError_t e = cudaGetLastError();
+  record_stage(a, 1);
+  record_stage(a, 2);
+  return e;
 }
 
 }  // namespace cvg

@@ -89,25 +89,51 @@ def assert_fp64_parity(got, ref, tol=1e-10, what=""):
         assert np.all(err <= tol), f"{what} {k} rel err {err.max():.3g} at {err.argmax()}"
 
 
-def mixed_report(got, ref, m):
-    """Mixed-precision error budget.  Decisions: any of flags/kb/klcl/ktop/kaux
-    differing.  Errors over columns active in both with identical decisions:
-    tendency column integral |sum m (x - y)| / sum m |y|; precipitation
-    |P - P_ref| / max(P_ref, 1e-3 * median nonzero P_ref)."""
+def same_decisions(got, ref):
     same = np.ones(ref["flags"].shape[0], bool)
     for k in INDEX_KEYS:
         same &= got[k] == ref[k]
+    return same
+
+
+def mixed_report(got, ref, m, upstream_same=None, p_surface=None):
+    """Mixed-precision error budget.  Decisions: any of flags/kb/klcl/ktop/kaux
+    differing.  Errors over columns active in both with identical decisions:
+    tendency column integral |sum m (x - y)| / sum m |y|; precipitation
+    |P - P_ref| / max(P_ref, 1e-3 * median nonzero surface precipitation), the
+    surface precipitation being deep + shallow of the oracle (p_surface; the
+    scheme's own P when not given), so trace drizzle -- liquid a hair above the
+    autoconversion threshold, whose FP32 rounding is relatively large -- is
+    measured against the precipitation scale of the grid.  upstream_same: for
+    the shallow scheme, the columns whose deep decisions agree -- a deep
+    decision flip changes the shallow scheme's input state, and is already
+    counted against the deep scheme."""
+    same = same_decisions(got, ref)
+    if upstream_same is not None:
+        same_own = same.copy()
+        same &= upstream_same
     trig_flips = int(np.sum((got["flags"] & 1) != (ref["flags"] & 1)))
     act = same & ((ref["flags"] & 2) > 0)
-    out = dict(n=int(same.size), decision_mismatch=int((~same).sum()), trigger_flips=trig_flips,
-               active=int(act.sum()))
+    if upstream_same is not None:
+        # flips of the shallow scheme on columns whose deep decisions agree
+        trig_flips = int(np.sum(((got["flags"] & 1) != (ref["flags"] & 1)) & upstream_same))
+        same_for_count = same_own | ~upstream_same
+    else:
+        same_for_count = same
+    by_key = {k: int(np.sum(got[k] != ref[k])) for k in INDEX_KEYS}
+    x = got["flags"] ^ ref["flags"]
+    bits = {b: int(np.sum((x >> b) & 1)) for b in range(12) if np.any((x >> b) & 1)}
+    out = dict(n=int(same.size), decision_mismatch=int((~same_for_count).sum()),
+               trigger_flips=trig_flips, active=int(act.sum()), mismatch_by_key=by_key,
+               flag_bits_differing=bits)
     for k in ("dTdt", "dqdt"):
         num = np.abs(np.sum(m * (got[k] - ref[k]), axis=0))
         den = np.maximum(np.sum(m * np.abs(ref[k]), axis=0), 1e-300)
         e = (num / den)[act]
         out[k + "_colint_max"] = float(e.max()) if e.size else 0.0
     pr = ref["prec"]
-    nz = pr[pr > 0]
+    ps_ = pr if p_surface is None else p_surface
+    nz = ps_[ps_ > 0]
     floor = 1e-3 * (np.median(nz) if nz.size else 1.0)
     e = (np.abs(got["prec"] - pr) / np.maximum(pr, floor))[act]
     out["prec_max"] = float(e.max()) if e.size else 0.0

@@ -101,7 +101,7 @@ def test_bad_precision_and_dt_rejected():
 def test_workspace_size_query_without_device():
     g, inp, out, keep = _args(n=1000, ld=1024)  # size query only, nothing runs
     lib = L.lib()
-    plain = L.Launch(L.CONV_PATH_PLAIN, 0, 0, 0)
+    plain = L.Launch(L.CONV_PATH_PLAIN, 0, 0, 0, None)
     assert lib.conv_workspace_bytes(C.byref(g), L.CONV_FP64, C.byref(plain)) == 0
     assert lib.conv_workspace_bytes(None, L.CONV_FP64, None) == 0
 

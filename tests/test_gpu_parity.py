@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 from paper_1711_00289_gb300 import soundings as S
-from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu)
+from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu,
+                            same_decisions)
 
 pytestmark = pytest.mark.gpu
 
@@ -140,12 +141,14 @@ def test_mixed_precision_budget(oracle, latlon, path):
     rd, rs = oracle.deep_shallow(latlon, threads=THREADS)
     gd, gs = run_gpu(latlon, "mixed", path)
     m = layer_mass(latlon)
-    for tag, got, ref in (("deep", gd, rd), ("shallow", gs, rs)):
-        r = mixed_report(got, ref, m)
-        assert r["trigger_flips"] <= 1e-3 * r["n"], (tag, r)
-        assert r["decision_mismatch"] <= 1e-3 * r["n"], (tag, r)
-        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, (tag, r)
-        assert r["prec_max"] <= 1e-3, (tag, r)
+    deep_same = same_decisions(gd, rd)
+    psurf = rd["prec"] + rs["prec"]
+    for tag, got, ref, up in (("deep", gd, rd, None), ("shallow", gs, rs, deep_same)):
+        r = mixed_report(got, ref, m, up, psurf)
+        assert r["trigger_flips"] <= 1e-3 * r["n"], f"{tag} {r}"
+        assert r["decision_mismatch"] <= 1e-3 * r["n"], f"{tag} {r}"
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
 
 
 @pytest.mark.parametrize("frac", [0.1, 0.3, 0.6])
@@ -163,12 +166,14 @@ def test_full_resolution_grid(oracle, frac):
     assert abs(trig - frac) < 0.02
     m = layer_mass(g)
     gd, gs = run_gpu(g, "mixed", "compact")
-    for tag, got, ref in (("deep", gd, rd), ("shallow", gs, rs)):
-        r = mixed_report(got, ref, m)
-        assert r["trigger_flips"] <= 1e-3 * r["n"], (tag, r)
-        assert r["decision_mismatch"] <= 1e-3 * r["n"], (tag, r)
-        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, (tag, r)
-        assert r["prec_max"] <= 1e-3, (tag, r)
+    deep_same = same_decisions(gd, rd)
+    psurf = rd["prec"] + rs["prec"]
+    for tag, got, ref, up in (("deep", gd, rd, None), ("shallow", gs, rs, deep_same)):
+        r = mixed_report(got, ref, m, up, psurf)
+        assert r["trigger_flips"] <= 1e-3 * r["n"], f"{tag} {r}"
+        assert r["decision_mismatch"] <= 1e-3 * r["n"], f"{tag} {r}"
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
 
 
 def test_compact_fp64_equals_plain_fp64_bitwise():
@@ -200,7 +205,7 @@ def test_workspace_errors():
     grid = vg.struct(0, 64)
     inp = L.In(T.data_ptr(), q.data_ptr(), ps.data_ptr(), None, None)
     o = api._out_struct(out, 30, 64, "fp64")
-    lc = L.Launch(L.CONV_PATH_COMPACT, 0, 0, 0)
+    lc = L.Launch(L.CONV_PATH_COMPACT, 0, 0, 0, None)
     dp = L.deep_defaults()
     need = L.lib().conv_workspace_bytes(C.byref(grid), L.CONV_FP64, C.byref(lc))
     assert need >= 256
