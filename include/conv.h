@@ -216,6 +216,35 @@ conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
                                   const conv_out* shallow_out, const conv_launch* launch,
                                   void* ws, size_t ws_bytes, conv_stream stream);
 
+/* Largest n_cols accepted by conv_deep_shallow_run_noalloc. */
+#define CONV_NOALLOC_MAX_COLS 65536
+
+/* conv_deep_shallow_run without a caller workspace.  No counterpart in the paper:
+ * it exists for callers that cannot allocate device memory where they call --
+ * a host model whose memory manager owns the whole device pool, or code that
+ * must not call cudaMalloc because it may synchronise the device or is not
+ * allowed while a stream is being captured.  The caller still owns and passes
+ * every input and output; the compacted path's scratch (queue and per-slot
+ * trigger state) lives in a library-owned static device array sized for
+ * CONV_NOALLOC_MAX_COLS columns of up to CONV_MAX_LEVELS levels in FP64
+ * (about 17 MB), held on every GPU that loads the library until the process
+ * exits.  Nothing here calls cudaMalloc, cudaFree or any allocating routine.
+ *   - n_cols > CONV_NOALLOC_MAX_COLS returns CONV_ERR_ARG before anything runs;
+ *     all other arguments are validated as for conv_deep_shallow_run.
+ *   - The first call on a device looks up that device's address of the array
+ *     (once per device, for the device current at the call); make that first
+ *     call before any stream capture.  The stream must belong to the current
+ *     device.
+ *   - Every call shares the one array, which keeps the last call's contents;
+ *     the queue length is reset at the start of each call.  Calls that overlap
+ *     on the GPU (other streams, other host threads) race on it: serialise them.
+ * Outputs are those of conv_deep_shallow_run on the compacted path. */
+conv_status conv_deep_shallow_run_noalloc(const conv_grid* grid, const conv_in* in,
+                                          const conv_deep_params* dpar,
+                                          const conv_shallow_params* spar, double dt,
+                                          conv_precision prec, const conv_out* deep_out,
+                                          const conv_out* shallow_out, conv_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,7 @@ CONV_PATH_AUTO, CONV_PATH_PLAIN, CONV_PATH_COMPACT = 0, 1, 2
 FLAG_TRIGGERED, FLAG_ACTIVE, FLAG_LIMITED, FLAG_NEWTON, FLAG_BADINPUT = 1, 2, 4, 8, 16
 EXIT_SHIFT = 8
 MAX_LEVELS = 32
+NOALLOC_MAX_COLS = 65536
 
 
 class ConvError(RuntimeError):
@@ -98,6 +99,9 @@ def lib(build: bool = True):
     L.conv_deep_shallow_run.restype = st
     L.conv_bench_op_rate.argtypes = [st, st, st, P(C.c_double)]
     L.conv_bench_op_rate.restype = st
+    L.conv_deep_shallow_run_noalloc.argtypes = [P(Grid), P(In), P(DeepParams),
+                                                P(ShallowParams), d, st, P(Out), P(Out), vp]
+    L.conv_deep_shallow_run_noalloc.restype = st
     _bind_optional(L)
     _lib = L
     return L
