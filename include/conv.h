@@ -216,6 +216,60 @@ conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
                                   const conv_out* shallow_out, const conv_launch* launch,
                                   void* ws, size_t ws_bytes, conv_stream stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many grids / ensemble members of uneven column counts and level counts in one
+ * trigger launch over all their columns and one persistent launch over a common
+ * device queue of convecting columns (the GPU answer to the load imbalance the
+ * paper meets with OpenMP dynamic scheduling, Sec. III-A).  Each member is a
+ * complete fused deep->shallow problem with its own grid, parameters and
+ * buffers; results equal those of conv_deep_shallow_run on the compacted path
+ * for that member alone. */
+typedef struct {
+  conv_grid grid; /* hyai/hybi: host arrays, copied at plan time */
+  conv_in in;
+  conv_out deep_out;
+  conv_out shallow_out;
+  conv_deep_params deep;
+  conv_shallow_params shallow;
+  double dt;
+} conv_member;
+
+typedef struct conv_batch conv_batch; /* opaque plan */
+
+/* Validate every member as conv_deep_shallow_run would (CONV_ERR_ARG names no
+ * member; check them singly to find it), copy the descriptors to the device and
+ * choose a launch shape (from the autotuner's process-wide cache when it holds
+ * one for this precision, level count and active-fraction bucket).  Plan time
+ * allocates: host memory for the plan and a device descriptor table
+ * (cudaMalloc + synchronous copy); runs allocate nothing.  n_members >= 1,
+ * total columns < 2^31. */
+conv_status conv_batch_plan(const conv_member* members, int n_members, conv_precision prec,
+                            conv_batch** out);
+
+/* Device workspace a run of this plan needs (256-byte aligned). */
+size_t conv_batch_workspace_bytes(const conv_batch* b);
+
+/* Enqueue the batched run on `stream`: queue reset, trigger pass, persistent
+ * plume pass.  No host synchronisation and no allocation, so it may be captured
+ * into a CUDA graph and replayed (the member buffers must stay valid).
+ * stage_events: optional three cudaEvent_t recorded as for conv_launch. */
+conv_status conv_batch_run(const conv_batch* b, void* ws, size_t ws_bytes, conv_stream stream,
+                           void* const* stage_events);
+
+/* Time candidate launch shapes (trigger block 64/128/256, then plume block
+ * 64/128/256 with its persistent grid) on this plan's own data, `reps` runs each
+ * after one warm-up, keep the fastest in the plan and in the process-wide cache.
+ * Synchronises `stream`; not capturable.  Outputs hold the last run's results. */
+conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_stream stream,
+                                int reps);
+
+/* Launch shape currently chosen (any pointer may be NULL). */
+conv_status conv_batch_config(const conv_batch* b, int32_t* trigger_block, int32_t* plume_block,
+                              int32_t* plume_grid);
+
+/* Release the plan and its device descriptor table (NULL is a no-op). */
+void conv_batch_free(conv_batch* b);
+
 /* Largest n_cols accepted by conv_deep_shallow_run_noalloc. */
 #define CONV_NOALLOC_MAX_COLS 65536
 

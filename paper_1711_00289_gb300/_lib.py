@@ -66,6 +66,11 @@ class Launch(C.Structure):
                 ("reserved1", C.c_int32), ("stage_events", C.POINTER(C.c_void_p))]
 
 
+class Member(C.Structure):
+    _fields_ = [("grid", Grid), ("in_", In), ("deep_out", Out), ("shallow_out", Out),
+                ("deep", DeepParams), ("shallow", ShallowParams), ("dt", C.c_double)]
+
+
 _lib = None
 
 
@@ -102,6 +107,18 @@ def lib(build: bool = True):
     L.conv_deep_shallow_run_noalloc.argtypes = [P(Grid), P(In), P(DeepParams),
                                                 P(ShallowParams), d, st, P(Out), P(Out), vp]
     L.conv_deep_shallow_run_noalloc.restype = st
+    L.conv_batch_plan.argtypes = [P(Member), st, st, P(vp)]
+    L.conv_batch_plan.restype = st
+    L.conv_batch_workspace_bytes.argtypes = [vp]
+    L.conv_batch_workspace_bytes.restype = C.c_size_t
+    L.conv_batch_run.argtypes = [vp, vp, C.c_size_t, vp, P(vp)]
+    L.conv_batch_run.restype = st
+    L.conv_batch_autotune.argtypes = [vp, vp, C.c_size_t, vp, st]
+    L.conv_batch_autotune.restype = st
+    L.conv_batch_config.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.conv_batch_config.restype = st
+    L.conv_batch_free.argtypes = [vp]
+    L.conv_batch_free.restype = None
     _bind_optional(L)
     _lib = L
     return L

@@ -223,3 +223,75 @@ def shallow(T, q, ps, vgrid: VerticalGrid, *, precision="fp64", params=None, pat
                                   wp, wn, _stream(stream))
     L.check(st, "conv_shallow_run")
     return o
+
+
+class Batch:
+    """A batched ensemble: many fused deep->shallow problems (uneven column and
+    level counts) run as one trigger launch and one persistent plume launch.
+
+    members: list of dicts with keys T, q, ps (device tensors, [pver, ld] /
+    [ld]), vgrid (VerticalGrid), optional lam, tau, n_cols, dt, deep_params,
+    shallow_params; outputs are allocated here (``self.outputs[m] = (deep,
+    shallow)``) unless given as ``out_deep`` / ``out_shallow``."""
+
+    def __init__(self, members, precision="fp64", device="cuda"):
+        self.precision = precision
+        self.outputs = []
+        self._keep = []
+        arr = (L.Member * len(members))()
+        for m, mb in enumerate(members):
+            T, q, ps, vg = mb["T"], mb["q"], mb["ps"], mb["vgrid"]
+            lam, tau = mb.get("lam"), mb.get("tau")
+            pver, ld, n, inp = _common(T, q, ps, vg, mb.get("n_cols"), precision, lam, tau)
+            od = mb.get("out_deep") or new_outputs(pver, ld, precision, T.device)
+            os_ = mb.get("out_shallow") or new_outputs(pver, ld, precision, T.device)
+            self.outputs.append((od, os_))
+            self._keep.append((T, q, ps, lam, tau, vg))
+            arr[m].grid = vg.struct(n, ld)
+            arr[m].in_ = inp
+            arr[m].deep_out = _out_struct(od, pver, ld, precision)
+            arr[m].shallow_out = _out_struct(os_, pver, ld, precision)
+            arr[m].deep = mb.get("deep_params") or L.deep_defaults()
+            arr[m].shallow = mb.get("shallow_params") or L.shallow_defaults()
+            arr[m].dt = float(mb.get("dt", 1800.0))
+        h = C.c_void_p()
+        L.check(L.lib().conv_batch_plan(arr, len(members), _PREC[precision], C.byref(h)),
+                "conv_batch_plan")
+        self._h = h
+        self.ws = Workspace(device)
+
+    def workspace_bytes(self) -> int:
+        return int(L.lib().conv_batch_workspace_bytes(self._h))
+
+    def run(self, stream=None, stage_events=None):
+        wp, wn = self.ws.get(self.workspace_bytes())
+        ev = None
+        if stage_events is not None:
+            lc = _launch("auto", 0, stage_events)
+            ev = lc.stage_events
+            self._ev_keep = lc
+        L.check(L.lib().conv_batch_run(self._h, wp, wn, _stream(stream), ev), "conv_batch_run")
+        return self.outputs
+
+    def autotune(self, reps: int = 3, stream=None):
+        wp, wn = self.ws.get(self.workspace_bytes())
+        L.check(L.lib().conv_batch_autotune(self._h, wp, wn, _stream(stream), int(reps)),
+                "conv_batch_autotune")
+        return self.config()
+
+    def config(self):
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        L.check(L.lib().conv_batch_config(self._h, C.byref(a), C.byref(b), C.byref(c)),
+                "conv_batch_config")
+        return {"trigger_block": a.value, "plume_block": b.value, "plume_grid": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().conv_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -275,6 +275,20 @@ __device__ __forceinline__ double lcl_p(float Tb, float qb, float pb, int n_newt
   return pbd * exp(INV_KAPPA * (lr - step * (double)fdiv_ieee(1.f, T)));
 }
 
+// Largest k <= kstart with p_mid[k] <= pL, or -1.  In FP32 the comparison runs
+// against pL rounded towards -inf to float: for a float x and a double y,
+// x <= y exactly when x <= round_down(y), so the decision is the FP64 one
+// without a conversion per level on the FP64 pipe.
+__device__ __forceinline__ float cmp_bound(double pL, float) { return __double2float_rd(pL); }
+__device__ __forceinline__ double cmp_bound(double pL, double) { return pL; }
+template <class R>
+__device__ __forceinline__ int lcl_level(const R* p_mid, int kstart, double pL) {
+  const R b = cmp_bound(pL, R(0));
+  for (int k = kstart; k >= 0; --k)
+    if (p_mid[k] <= b) return k;
+  return -1;
+}
+
 // Entraining mass-flux profile (1 + dz/z_e)^(lambda z_e).
 template <class R>
 __device__ __forceinline__ R entrain_growth(R lam, R ze, R dz) {
@@ -411,9 +425,7 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   t.newton = 0.f;
   const double pL = lcl_p(c.T[kb], c.q[kb], c.p_mid[kb], P.n_newton_lcl, t.newton);
   t.pL = pL;
-  int klcl = -1;
-  for (int k = kb; k >= 0; --k)
-    if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
+  const int klcl = lcl_level(c.p_mid, kb, pL);
   t.klcl = klcl;
   if (klcl < ktl) return;
   const R hb = c.h[kb];
@@ -657,9 +669,7 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
     klcl = seed->klcl;
   } else {
     pL = lcl_p(c.T[ks], c.q[ks], c.p_mid[ks], P.n_newton_lcl, newton);
-    klcl = -1;
-    for (int k = ks; k >= 0; --k)
-      if ((double)c.p_mid[k] <= pL) { klcl = k; break; }
+    klcl = lcl_level(c.p_mid, ks, pL);
   }
   o.klcl = klcl;
   int exit_code = 0;

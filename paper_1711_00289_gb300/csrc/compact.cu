@@ -74,10 +74,12 @@ __device__ __forceinline__ void load_column(const RunArgs& a, int i, Column<R>& 
   }
 }
 
+// Trigger pass of one column (all lanes of the warp must call it: the queue
+// append is a warp ballot).  `tag` is what the queue records for the column
+// (the column index, or a batch-wide index), `live` false for padding lanes.
 template <class R>
-__global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<R> w) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool live = i < a.n;
+__device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R>& w, int i,
+                                             bool live, int tag) {
   Column<R> c;
   DeepOut<R> o;
   DeepTrig<R> t;
@@ -93,7 +95,7 @@ __global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<
     if (!valid) {
       o.flags = CONV_FLAG_BADINPUT;
     } else {
-      prologue(a.L, a.dp.p_top_lim, c, true);
+      prologue(a.L, a.dp.p_top_lim, c, false);  // h* is needed only by the plume pass
       deep_trigger(c, a.dp, t);
       o.kb = t.kb;
       o.klcl = t.klcl;
@@ -114,11 +116,11 @@ __global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<
   if (!live) return;
   if (t.triggered) {
     const int slot = base + __popc(ball & ((1u << lane) - 1u));
-    w.queue[slot] = i;
+    w.queue[slot] = tag;
     w.levels[slot] = t.kb | (t.klcl << 8) | (t.kel << 16);
     w.cape[slot] = t.cape;
-    for (int k = t.kel; k <= t.klcl; ++k) w.Tp[(size_t)k * a.n + slot] = t.Tp[k];
-    store_deep(a, i, o, false);  // scalars now; tendencies and the rest in k_plume
+    for (int k = t.kel; k <= t.klcl; ++k) w.Tp[(size_t)k * w.cap + slot] = t.Tp[k];
+    store_deep(a, i, o, false);  // scalars now; tendencies and the rest in the plume pass
     return;
   }
   store_deep(a, i, o, true);
@@ -140,6 +142,12 @@ __global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<
 }
 
 template <class R>
+__global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<R> w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  trigger_body(a, w, i, i < a.n, i);
+}
+
+template <class R>
 __device__ __forceinline__ R add_mul(R a, double dt, R b);
 template <>
 __device__ __forceinline__ double add_mul<double>(double a, double dt, double b) {
@@ -150,11 +158,10 @@ __device__ __forceinline__ float add_mul<float>(float a, double dt, float b) {
   return a + (float)dt * b;
 }
 
+// Plume pass of the column in queue slot `slot` (column i of member a).
 template <class R>
-__global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R> w) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= *w.count) return;
-  const int i = w.queue[slot];
+__device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>& w, int slot,
+                                           int i) {
   Column<R> c;
   load_column(a, i, c);
   prologue(a.L, a.dp.p_top_lim, c, true);
@@ -166,12 +173,12 @@ __global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R>
   t.cape = w.cape[slot];
   t.triggered = true;
   t.newton = 0.f;
-  for (int k = t.kel; k <= t.klcl; ++k) t.Tp[k] = w.Tp[(size_t)k * a.n + slot];
+  for (int k = t.kel; k <= t.klcl; ++k) t.Tp[k] = w.Tp[(size_t)k * w.cap + slot];
   DeepOut<R> o;
   for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
   o.prec = o.mb = o.cons = 0.0;
   o.cape = t.cape;
-  o.flags = a.od.flags[i];  // trigger-stage bits written by k_trigger
+  o.flags = a.od.flags[i];  // trigger-stage bits written by the trigger pass
   o.kb = t.kb;
   o.klcl = t.klcl;
   o.ktop = o.kaux = -1;
@@ -191,6 +198,13 @@ __global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R>
   store_shallow(a, i, s);
 }
 
+template <class R>
+__global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R> w) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= *w.count) return;
+  plume_body(a, w, slot, w.queue[slot]);
+}
+
 size_t compact_workspace_bytes(int n, int pver, bool fp64) {
   const size_t rb = fp64 ? 8 : 4;
   return ws_offsets(n, pver, rb).total;
@@ -207,6 +221,7 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   w.levels = reinterpret_cast<int*>(base + off.levels);
   w.cape = reinterpret_cast<double*>(base + off.cape);
   w.Tp = reinterpret_cast<R*>(base + off.Tp);
+  w.cap = a.n;
   record_stage(a, 0);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
   if (e != cudaSuccess) return e;
@@ -224,6 +239,113 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
 cudaError_t launch_compact(const RunArgs& a, bool fp64, void* ws, size_t ws_bytes) {
   if (a.n == 0) return cudaSuccess;
   return fp64 ? launch_t<double>(a, ws, ws_bytes) : launch_t<float>(a, ws, ws_bytes);
+}
+
+// ---------------------------------------------------------------- batched ensemble
+// Members of uneven column and level counts share one trigger launch over the
+// concatenation of their columns (column g belongs to the member m with
+// offsets[m] <= g < offsets[m+1]) and one persistent plume launch that walks the
+// common queue of triggered columns with a grid-stride loop until the queue
+// length read from device memory is exhausted -- no host synchronisation, no
+// waiting on other blocks.
+
+__device__ __forceinline__ int find_member(const int* off, int M, int g) {
+  int lo = 0, hi = M;  // invariant: off[lo] <= g < off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_batch_trigger(BatchDev b, CompactWs<R> w) {
+  const int g = blockIdx.x * BLOCK + threadIdx.x;
+  const bool live = g < b.total;
+  int m = 0, i = 0;
+  if (live) {
+    m = find_member(b.offsets, b.n_members, g);
+    i = g - b.offsets[m];
+  }
+  trigger_body(b.members[m], w, i, live, g);
+}
+
+template <class R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_batch_plume(BatchDev b, CompactWs<R> w) {
+  const int count = *w.count;
+  for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
+    const int g = w.queue[slot];
+    const int m = find_member(b.offsets, b.n_members, g);
+    plume_body(b.members[m], w, slot, g - b.offsets[m]);
+  }
+}
+
+template <class R, int BLOCK>
+static int plume_occupancy() {
+  int blocks = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_plume<R, BLOCK>, BLOCK, 0) !=
+      cudaSuccess)
+    return 1;
+  return blocks < 1 ? 1 : blocks;
+}
+
+int batch_plume_occupancy(bool fp64, int block) {
+  switch (block) {
+    case 64: return fp64 ? plume_occupancy<double, 64>() : plume_occupancy<float, 64>();
+    case 256: return fp64 ? plume_occupancy<double, 256>() : plume_occupancy<float, 256>();
+    default: return fp64 ? plume_occupancy<double, 128>() : plume_occupancy<float, 128>();
+  }
+}
+
+template <class R, int BLOCK>
+static void launch_trig(const BatchDev& b, const CompactWs<R>& w, cudaStream_t s) {
+  k_batch_trigger<R, BLOCK><<<(b.total + BLOCK - 1) / BLOCK, BLOCK, 0, s>>>(b, w);
+}
+template <class R, int BLOCK>
+static void launch_plume(const BatchDev& b, const CompactWs<R>& w, int grid, cudaStream_t s) {
+  k_batch_plume<R, BLOCK><<<grid, BLOCK, 0, s>>>(b, w);
+}
+
+template <class R>
+static cudaError_t batch_t(const BatchDev& b, const BatchShape& sh, void* ws, size_t ws_bytes,
+                           cudaStream_t s, cudaEvent_t* ev) {
+  const WsOffsets off = ws_offsets(b.total, sh.max_pver, sizeof(R));
+  if (ws_bytes < off.total) return cudaErrorInvalidValue;
+  char* base = static_cast<char*>(ws);
+  CompactWs<R> w;
+  w.count = reinterpret_cast<int*>(base + off.count);
+  w.queue = reinterpret_cast<int*>(base + off.queue);
+  w.levels = reinterpret_cast<int*>(base + off.levels);
+  w.cape = reinterpret_cast<double*>(base + off.cape);
+  w.Tp = reinterpret_cast<R*>(base + off.Tp);
+  w.cap = b.total;
+  if (ev && ev[0]) cudaEventRecord(ev[0], s);
+  cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  switch (sh.trigger_block) {
+    case 64: launch_trig<R, 64>(b, w, s); break;
+    case 256: launch_trig<R, 256>(b, w, s); break;
+    default: launch_trig<R, 128>(b, w, s); break;
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev && ev[1]) cudaEventRecord(ev[1], s);
+  switch (sh.plume_block) {
+    case 64: launch_plume<R, 64>(b, w, sh.plume_grid, s); break;
+    case 256: launch_plume<R, 256>(b, w, sh.plume_grid, s); break;
+    default: launch_plume<R, 128>(b, w, sh.plume_grid, s); break;
+  }
+  e = cudaGetLastError();
+  if (ev && ev[2]) cudaEventRecord(ev[2], s);
+  return e;
+}
+
+cudaError_t launch_batch(const BatchDev& b, const BatchShape& sh, bool fp64, void* ws,
+                         size_t ws_bytes, cudaStream_t s, cudaEvent_t* ev) {
+  if (b.total == 0) return cudaSuccess;
+  return fp64 ? batch_t<double>(b, sh, ws, ws_bytes, s, ev)
+              : batch_t<float>(b, sh, ws, ws_bytes, s, ev);
 }
 
 }  // namespace cvg

@@ -13,6 +13,7 @@ constexpr int kCompactBlock = 128;
 //   levels int32[n]   kb | klcl << 8 | kel << 16 of the queued column
 //   cape   double[n]  CAPE of the queued column
 //   Tp     R[pver][n] undilute parcel temperature on kel..klcl, by queue slot
+// (n = queue capacity: the columns of the run, or of all members of a batch)
 template <class R>
 struct CompactWs {
   int* count;
@@ -20,6 +21,7 @@ struct CompactWs {
   int* levels;
   double* cape;
   R* Tp;
+  int cap;  // queue capacity (columns); row stride of Tp
 };
 
 struct WsOffsets {
@@ -42,5 +44,24 @@ inline WsOffsets ws_offsets(int n, int pver, size_t real_bytes) {
 
 size_t compact_workspace_bytes(int n, int pver, bool fp64);
 cudaError_t launch_compact(const RunArgs& a, bool fp64, void* ws, size_t ws_bytes);
+
+// Batched ensemble: device copies of the members' run descriptors and the
+// prefix sums of their column counts (offsets[n_members] = total).
+struct BatchDev {
+  const RunArgs* members;
+  const int* offsets;
+  int n_members;
+  int total;
+};
+// Launch shape chosen by the plan (and the autotuner).
+struct BatchShape {
+  int max_pver;
+  int trigger_block;  // 64, 128 or 256
+  int plume_block;    // 64, 128 or 256
+  int plume_grid;     // persistent grid: SMs x resident blocks per SM
+};
+int batch_plume_occupancy(bool fp64, int block);
+cudaError_t launch_batch(const BatchDev& b, const BatchShape& sh, bool fp64, void* ws,
+                         size_t ws_bytes, cudaStream_t s, cudaEvent_t* ev);
 
 }  // namespace cvg

@@ -4,6 +4,10 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "compact.h"
 
@@ -232,6 +236,202 @@ conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
   a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
   a.stream = reinterpret_cast<cudaStream_t>(stream);
   return dispatch(a, prec, launch, ws, ws_bytes);
+}
+
+}  // extern "C"
+
+// ================================================================ batches
+struct conv_batch {
+  conv_precision prec;
+  int n_members;
+  int total;
+  int sms;
+  cvg::BatchShape shape;
+  cvg::RunArgs* d_members;
+  int* d_offsets;
+  std::vector<int> h_offsets;
+};
+
+namespace {
+
+// Autotuner cache: (precision, largest level count, active-fraction decile).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, cvg::BatchShape> g_tune_cache;
+std::map<std::pair<int, int>, int> g_last_bucket;  // (prec, pver) -> last measured decile
+
+cvg::BatchShape default_shape(bool fp64, int max_pver, int sms) {
+  cvg::BatchShape sh;
+  sh.max_pver = max_pver;
+  sh.trigger_block = 128;
+  sh.plume_block = 128;
+  sh.plume_grid = sms * cvg::batch_plume_occupancy(fp64, 128);
+  return sh;
+}
+
+}  // namespace
+
+extern "C" {
+
+conv_status conv_batch_plan(const conv_member* members, int n_members, conv_precision prec,
+                            conv_batch** out) {
+  if (!out) return CONV_ERR_ARG;
+  *out = nullptr;
+  if (!members || n_members < 1 || (prec != CONV_FP64 && prec != CONV_MIXED)) return CONV_ERR_ARG;
+  std::vector<RunArgs> h(n_members);
+  std::vector<int> off(n_members + 1, 0);
+  long long total = 0;
+  int max_pver = 0;
+  for (int m = 0; m < n_members; ++m) {
+    const conv_member& mb = members[m];
+    RunArgs& a = h[m];
+    conv_status st = common_in(&mb.grid, &mb.in, mb.dt, a);
+    if (st != CONV_OK) return st;
+    if (!deep_params_ok(&mb.deep) || !shallow_params_ok(&mb.shallow) || !out_ok(&mb.deep_out) ||
+        !out_ok(&mb.shallow_out))
+      return CONV_ERR_ARG;
+    a.dp = mb.deep;
+    a.sp = mb.shallow;
+    a.od = to_outp(&mb.deep_out);
+    a.os = to_outp(&mb.shallow_out);
+    a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
+    a.stream = nullptr;
+    off[m] = (int)total;
+    total += a.n;
+    if (a.L.pver > max_pver) max_pver = a.L.pver;
+  }
+  if (total >= (1ll << 31)) return CONV_ERR_ARG;
+  off[n_members] = (int)total;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CONV_ERR_CUDA;
+  conv_batch* b = new conv_batch();
+  b->prec = prec;
+  b->n_members = n_members;
+  b->total = (int)total;
+  b->sms = sms;
+  b->h_offsets = off;
+  b->d_members = nullptr;
+  b->d_offsets = nullptr;
+  if (cudaMalloc(&b->d_members, sizeof(RunArgs) * n_members) != cudaSuccess ||
+      cudaMalloc(&b->d_offsets, sizeof(int) * (n_members + 1)) != cudaSuccess ||
+      cudaMemcpy(b->d_members, h.data(), sizeof(RunArgs) * n_members, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(b->d_offsets, off.data(), sizeof(int) * (n_members + 1),
+                 cudaMemcpyHostToDevice) != cudaSuccess) {
+    conv_batch_free(b);
+    return CONV_ERR_CUDA;
+  }
+  const bool fp64 = prec == CONV_FP64;
+  b->shape = default_shape(fp64, max_pver, sms);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto lb = g_last_bucket.find({(int)prec, max_pver});
+    if (lb != g_last_bucket.end()) {
+      auto it = g_tune_cache.find(std::make_tuple((int)prec, max_pver, lb->second));
+      if (it != g_tune_cache.end()) b->shape = it->second;
+    }
+  }
+  *out = b;
+  return CONV_OK;
+}
+
+size_t conv_batch_workspace_bytes(const conv_batch* b) {
+  if (!b) return 0;
+  return cvg::ws_offsets(b->total, b->shape.max_pver, b->prec == CONV_FP64 ? 8 : 4).total;
+}
+
+conv_status conv_batch_run(const conv_batch* b, void* ws, size_t ws_bytes, conv_stream stream,
+                           void* const* stage_events) {
+  if (!b) return CONV_ERR_ARG;
+  const size_t need = conv_batch_workspace_bytes(b);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+    return CONV_ERR_WORKSPACE;
+  cvg::BatchDev d{b->d_members, b->d_offsets, b->n_members, b->total};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (stage_events)
+    for (int i = 0; i < 3; ++i) ev[i] = static_cast<cudaEvent_t>(stage_events[i]);
+  const cudaError_t e = cvg::launch_batch(d, b->shape, b->prec == CONV_FP64, ws, ws_bytes,
+                                          reinterpret_cast<cudaStream_t>(stream), ev);
+  return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
+
+conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_stream stream,
+                                int reps) {
+  if (!b || reps < 1) return CONV_ERR_ARG;
+  const size_t need = conv_batch_workspace_bytes(b);
+  if (!ws || ws_bytes < need || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0)
+    return CONV_ERR_WORKSPACE;
+  const bool fp64 = b->prec == CONV_FP64;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return CONV_ERR_CUDA;
+  cvg::BatchDev d{b->d_members, b->d_offsets, b->n_members, b->total};
+  auto time_shape = [&](const cvg::BatchShape& sh, float* ms) -> cudaError_t {
+    cudaError_t err = cvg::launch_batch(d, sh, fp64, ws, ws_bytes, s, nullptr);  // warm-up
+    if (err != cudaSuccess) return err;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && err == cudaSuccess; ++r)
+      err = cvg::launch_batch(d, sh, fp64, ws, ws_bytes, s, nullptr);
+    cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+    return err;
+  };
+  static const int kBlocks[3] = {64, 128, 256};
+  cvg::BatchShape best = b->shape;
+  float best_ms = 1e30f;
+  cudaError_t err = cudaSuccess;
+  for (int tb : kBlocks) {
+    cvg::BatchShape sh = best;
+    sh.trigger_block = tb;
+    float ms = 0.f;
+    err = time_shape(sh, &ms);
+    if (err != cudaSuccess) break;
+    if (ms < best_ms) { best_ms = ms; best = sh; }
+  }
+  for (int pb : kBlocks) {
+    if (err != cudaSuccess) break;
+    cvg::BatchShape sh = best;
+    sh.plume_block = pb;
+    sh.plume_grid = b->sms * cvg::batch_plume_occupancy(fp64, pb);
+    float ms = 0.f;
+    err = time_shape(sh, &ms);
+    if (err != cudaSuccess) break;
+    if (ms < best_ms) { best_ms = ms; best = sh; }
+  }
+  int count = 0;
+  if (err == cudaSuccess) {  // active fraction of this batch: the queue length
+    const cvg::WsOffsets off = cvg::ws_offsets(b->total, b->shape.max_pver, fp64 ? 8 : 4);
+    err = cudaMemcpy(&count, static_cast<char*>(ws) + off.count, sizeof(int),
+                     cudaMemcpyDeviceToHost);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return CONV_ERR_CUDA;
+  b->shape = best;
+  const int bucket = b->total > 0 ? (int)(10.0 * count / b->total) : 0;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_cache[std::make_tuple((int)b->prec, best.max_pver, bucket)] = best;
+  g_last_bucket[{(int)b->prec, best.max_pver}] = bucket;
+  return CONV_OK;
+}
+
+conv_status conv_batch_config(const conv_batch* b, int32_t* trigger_block, int32_t* plume_block,
+                              int32_t* plume_grid) {
+  if (!b) return CONV_ERR_ARG;
+  if (trigger_block) *trigger_block = b->shape.trigger_block;
+  if (plume_block) *plume_block = b->shape.plume_block;
+  if (plume_grid) *plume_grid = b->shape.plume_grid;
+  return CONV_OK;
+}
+
+void conv_batch_free(conv_batch* b) {
+  if (!b) return;
+  if (b->d_members) cudaFree(b->d_members);
+  if (b->d_offsets) cudaFree(b->d_offsets);
+  delete b;
 }
 
 }  // extern "C"

@@ -114,3 +114,19 @@ def test_package_has_no_cpu_fallback():
     for f in glob.glob(os.path.join(pkg, "**", "*.*"), recursive=True):
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             assert not bad.search(open(f).read()), f
+
+
+def test_batch_plan_validates_members_before_touching_a_device():
+    lib = L.lib()
+    g, inp, out, keep = _args()
+    m = (L.Member * 2)()
+    for k in range(2):
+        m[k].grid, m[k].in_, m[k].deep_out, m[k].shallow_out = g, inp, out, out
+        m[k].deep, m[k].shallow, m[k].dt = L.deep_defaults(), L.shallow_defaults(), 1800.0
+    m[1].deep.tau_default = -1.0
+    h = C.c_void_p()
+    assert lib.conv_batch_plan(m, 2, L.CONV_FP64, C.byref(h)) == L.CONV_ERR_ARG
+    assert not h.value
+    assert lib.conv_batch_plan(m, 0, L.CONV_FP64, C.byref(h)) == L.CONV_ERR_ARG
+    assert lib.conv_batch_workspace_bytes(None) == 0
+    lib.conv_batch_free(None)
