@@ -216,6 +216,39 @@ conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
                                   const conv_out* shallow_out, const conv_launch* launch,
                                   void* ws, size_t ws_bytes, conv_stream stream);
 
+/* ------------------------------------------------------------------ adjoint
+ * Reverse-mode gradient of the deep scheme, for tuning lambda and tau or for
+ * sensitivity studies.  No counterpart in the paper (it gives the forward
+ * scheme only); the forward scheme it differentiates is the one conv_deep_run
+ * computes (Alg. 2: launch level, LCL, undilute parcel and CAPE, entraining
+ * updraft with rain, saturated downdraft, flux-form tendencies, CAPE closure
+ * and moisture limiter).  Per column i it evaluates
+ *   P_i  surface precipitation (kg m-2 s-1, = prec of conv_deep_run)
+ *   H_i  = sum_k w_k * m_k * cp * dTdt_k,i   (W m-2 for w = 1)
+ * (m_k = dp_k / g: layer mass per unit area; w_k = w_heat[k], or p_mid_k / ps_i
+ * when w_heat is NULL) and the gradient of J_i = gP[i] * P_i + gH[i] * H_i:
+ *   gT, gq  [pver][ld] doubles: dJ/dT (per K), dJ/dq (per kg/kg)
+ *   glambda, gtau  [ld] doubles: dJ/dlambda, dJ/dtau
+ * gT, gq, glambda, gtau: all four DEVICE buffers (gradient wanted) or all NULL
+ * (P_out / H_out only).  P_out, H_out: DEVICE [ld] doubles or NULL; at least one
+ * output must be requested.  gP, gH: DEVICE [ld] doubles, either may be NULL
+ * (zero).  w_heat: HOST [pver] doubles or NULL, copied into the launch.  FP64
+ * only (CONV_MIXED -> CONV_ERR_UNSUPPORTED); in->T, in->q are doubles;
+ * in->lambda / in->tau may be NULL (defaults).  Outputs are owned by the caller
+ * and written for every column: zeros where the scheme is not active (not
+ * triggered, no cloud, closure off, bad input).  Discrete choices (levels,
+ * saturation, the downdraft cap and the moisture limiter) are held at their
+ * forward values: the result is the derivative of the smooth piece the inputs
+ * lie on.  One thread per column recomputes the forward scheme (nothing is
+ * kept between calls), then runs the reverse sweep; Newton solves are
+ * differentiated by the implicit function theorem.  Asynchronous on `stream`;
+ * allocates nothing; no workspace. */
+conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
+                              const conv_deep_params* par, double dt, conv_precision prec,
+                              const double* gP, const double* gH, const double* w_heat,
+                              double* gT, double* gq, double* glambda, double* gtau,
+                              double* P_out, double* H_out, conv_stream stream);
+
 /* ------------------------------------------------------------------ batches
  * Many grids / ensemble members of uneven column counts and level counts in one
  * trigger launch over all their columns and one persistent launch over a common

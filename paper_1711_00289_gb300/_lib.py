@@ -119,18 +119,11 @@ def lib(build: bool = True):
     L.conv_batch_config.restype = st
     L.conv_batch_free.argtypes = [vp]
     L.conv_batch_free.restype = None
-    _bind_optional(L)
+    L.conv_deep_adjoint.argtypes = [P(Grid), P(In), P(DeepParams), d, st, vp, vp,
+                                    P(C.c_double), vp, vp, vp, vp, vp, vp, vp]
+    L.conv_deep_adjoint.restype = st
     _lib = L
     return L
-
-
-def _bind_optional(L):
-    """Entry points added by later modules of the library bind here when present."""
-    for hook in _HOOKS:
-        hook(L)
-
-
-_HOOKS = []
 
 
 CONV_OP_FMA, CONV_OP_EXP, CONV_OP_LOG, CONV_OP_DIV, CONV_OP_POW, CONV_OP_SQRT = range(6)

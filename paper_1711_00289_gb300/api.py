@@ -295,3 +295,81 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def deep_adjoint(T, q, ps, vgrid: VerticalGrid, *, gP=None, gH=None, w_heat=None,
+                 dt: float = 1800.0, lam=None, tau=None, params=None, n_cols=None,
+                 gradient=True, objective=False, stream=None):
+    """Deep-scheme objective and/or adjoint (FP64, conv_deep_adjoint).
+
+    Per column: P (precipitation) and H = sum_k w_k m_k cp dTdt_k, and the
+    gradient of J = gP P + gH H w.r.t. T, q ([pver, ld]), lambda and tau ([ld]).
+    w_heat: host sequence of pver weights, None for p_mid/ps.  Returns a dict
+    with gT, gq, glambda, gtau (if ``gradient``) and P, H (if ``objective``)."""
+    if not (gradient or objective):
+        raise ValueError("nothing requested")
+    pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, "fp64", lam, tau)
+    f64 = torch.float64
+    for name, t in (("gP", gP), ("gH", gH)):
+        if t is not None:
+            _require_cuda(t, name, f64, (ld,))
+    w = None
+    if w_heat is not None:
+        wa = np.ascontiguousarray(w_heat, dtype=np.float64)
+        if wa.shape != (pver,):
+            raise ValueError(f"w_heat must have {pver} entries")
+        w = wa.ctypes.data_as(C.POINTER(C.c_double))
+    res = {}
+    if gradient:
+        res = dict(gT=torch.empty((pver, ld), dtype=f64, device=T.device),
+                   gq=torch.empty((pver, ld), dtype=f64, device=T.device),
+                   glambda=torch.empty(ld, dtype=f64, device=T.device),
+                   gtau=torch.empty(ld, dtype=f64, device=T.device))
+    if objective:
+        res["P"] = torch.empty(ld, dtype=f64, device=T.device)
+        res["H"] = torch.empty(ld, dtype=f64, device=T.device)
+    dp = params or L.deep_defaults()
+    g = vgrid.struct(n, ld)
+    st = L.lib().conv_deep_adjoint(
+        C.byref(g), C.byref(inp), C.byref(dp), float(dt), L.CONV_FP64, _ptr(gP), _ptr(gH), w,
+        _ptr(res.get("gT")), _ptr(res.get("gq")), _ptr(res.get("glambda")),
+        _ptr(res.get("gtau")), _ptr(res.get("P")), _ptr(res.get("H")), _stream(stream))
+    L.check(st, "conv_deep_adjoint")
+    return res
+
+
+class DeepConvection(torch.autograd.Function):
+    """Differentiable deep scheme: (T, q, lam, tau) -> (P, H) per column, with
+    P the precipitation and H = sum_k w_k m_k cp dTdt_k.  Both directions run in
+    the library: forward and backward call conv_deep_adjoint (the backward
+    recomputes the forward scheme in its kernel; nothing is saved but inputs).
+    lam / tau may be None (parameter defaults, no gradient)."""
+
+    @staticmethod
+    def forward(ctx, T, q, lam, tau, ps, vgrid, dt, params, w_heat):
+        ctx.save_for_backward(T, q, lam, tau, ps)
+        ctx.cfg = (vgrid, dt, params, w_heat)
+        r = deep_adjoint(T.detach(), q.detach(), ps, vgrid, w_heat=w_heat, dt=dt,
+                         lam=None if lam is None else lam.detach(),
+                         tau=None if tau is None else tau.detach(), params=params,
+                         gradient=False, objective=True)
+        return r["P"], r["H"]
+
+    @staticmethod
+    def backward(ctx, gP, gH):
+        T, q, lam, tau, ps = ctx.saved_tensors
+        vgrid, dt, params, w_heat = ctx.cfg
+        r = deep_adjoint(T.detach(), q.detach(), ps, vgrid, gP=gP.contiguous(),
+                         gH=gH.contiguous(), w_heat=w_heat, dt=dt,
+                         lam=None if lam is None else lam.detach(),
+                         tau=None if tau is None else tau.detach(), params=params)
+        need = ctx.needs_input_grad
+        return (r["gT"] if need[0] else None, r["gq"] if need[1] else None,
+                r["glambda"] if need[2] else None, r["gtau"] if need[3] else None,
+                None, None, None, None, None)
+
+
+def deep_precip_heating(T, q, ps, vgrid: VerticalGrid, *, lam=None, tau=None,
+                        dt: float = 1800.0, params=None, w_heat=None):
+    """(P, H) of the deep scheme per column, differentiable w.r.t. T, q, lam, tau."""
+    return DeepConvection.apply(T, q, lam, tau, ps, vgrid, dt, params, w_heat)

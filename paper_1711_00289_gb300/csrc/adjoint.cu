@@ -1,0 +1,65 @@
+// adjoint.cu -- kernel and launch of the deep-scheme adjoint (FP64): one
+// thread per column loads its profiles, runs deep_adjoint_column (adjoint.cuh)
+// and stores dJ/dT, dJ/dq, dJ/dlambda, dJ/dtau and/or the objective pieces P, H.
+#include "adjoint.cuh"
+#include "launch.h"
+
+namespace cvg {
+
+struct AdjArgs {
+  RunArgs a;
+  const double* gP;
+  const double* gH;
+  AdjW w;
+  double* gT;
+  double* gq;
+  double* glam;
+  double* gtau;
+  double* Pout;
+  double* Hout;
+};
+
+__global__ void __launch_bounds__(64) k_deep_adjoint(AdjArgs A) {
+  const RunArgs& a = A.a;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  const int pver = a.L.pver, ld = a.ld;
+  Column<double> c;
+  c.pver = pver;
+  c.ps = a.ps[i];
+  const double* T = static_cast<const double*>(a.T);
+  const double* q = static_cast<const double*>(a.q);
+  for (int k = 0; k < pver; ++k) {
+    c.T[k] = T[(size_t)k * ld + i];
+    c.q[k] = q[(size_t)k * ld + i];
+  }
+  const double lam = a.lam ? a.lam[i] : a.dp.lambda_default;
+  const double tau = a.tau ? a.tau[i] : a.dp.tau_default;
+  const double gP = A.gP ? A.gP[i] : 0.0, gH = A.gH ? A.gH[i] : 0.0;
+  const bool rev = A.gT != nullptr;
+  double bT[MAXL], bq[MAXL], blam, btau, Pv, Hv;
+  deep_adjoint_column(a.L, a.dp, a.dt, lam, tau, c, gP, gH, A.w.given ? A.w.w : nullptr, rev, bT,
+                      bq, blam, btau, Pv, Hv);
+  if (rev) {
+    for (int k = 0; k < pver; ++k) {
+      A.gT[(size_t)k * ld + i] = bT[k];
+      A.gq[(size_t)k * ld + i] = bq[k];
+    }
+    A.glam[i] = blam;
+    A.gtau[i] = btau;
+  }
+  if (A.Pout) A.Pout[i] = Pv;
+  if (A.Hout) A.Hout[i] = Hv;
+}
+
+cudaError_t launch_deep_adjoint(const RunArgs& a, const double* gP, const double* gH,
+                                const AdjW& w, double* gT, double* gq, double* glam,
+                                double* gtau, double* Pout, double* Hout) {
+  if (a.n == 0) return cudaSuccess;
+  AdjArgs A{a, gP, gH, w, gT, gq, glam, gtau, Pout, Hout};
+  const int block = 64;
+  k_deep_adjoint<<<(a.n + block - 1) / block, block, 0, a.stream>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace cvg

@@ -1,0 +1,291 @@
+// adjoint.cuh -- reverse-mode adjoint of the deep scheme (FP64), one thread per
+// column.  For J = gP P + gH H, H = sum_k w_k m_k cp dT/dt_k, it returns
+// dJ/dT_k, dJ/dq_k, dJ/dlambda and dJ/dtau.  The column is first recomputed
+// forward in the thread (the plume state is recomputed, never stored between
+// kernels) with deep_plume recording its intermediates; then the reverse sweep
+// runs through closure, tendencies, downdraft, updraft, parcel, moist static
+// energy and heights.  Newton solves are differentiated by the implicit
+// function theorem, dT = (dh - g dz) / (cp + Lv dqs/dT); level choices, the
+// saturation, alpha and limiter branches are held at their forward values
+// (the scheme is piecewise smooth).
+#pragma once
+
+#include "column.cuh"
+
+namespace cvg {
+
+// qs, dqs/dT and d2qs/dT2 at (T, p), same branch as sat_qs_dqs.
+__device__ __forceinline__ void qs_derivs(double T, double p, double& qs, double& dqs,
+                                          double& d2qs) {
+  const double r = 1.0 / (T - EST1);
+  const double es = ES0 * exp(ESA * (T - EST0) * r);
+  const double a = ESA * ESC * r * r;  // d ln es / dT
+  const double ap = -2.0 * a * r;      // d a / dT
+  const double D = p - ONE_M_EPS * es;
+  if (D < 1e-3 * p) {
+    qs = EPSV * es / (1e-3 * p);
+    dqs = qs * a;
+    d2qs = qs * (a * a + ap);
+  } else {
+    qs = EPSV * es / D;
+    dqs = qs * p * a / D;
+    d2qs = EPSV * p * es / (D * D) * (ap + a * a + 2.0 * a * a * ONE_M_EPS * es / D);
+  }
+}
+
+// Adjoint of T = hinv(h, g z, p): dT = (dh - g dz) / (cp + Lv dqs(T)).
+__device__ __forceinline__ void inv_adj(double T, double p, double bT, double& bh, double& bz) {
+  double qs, dqs, d2;
+  qs_derivs(T, p, qs, dqs, d2);
+  const double B = CP + LV * dqs;
+  bh += bT / B;
+  bz -= GRAV * bT / B;
+}
+
+// For the column loaded in c (T, q, ps, pver): P (surface precipitation) and
+// H = sum_k w_k m_k cp dTdt_k into Pv, Hv, and -- when `reverse` -- the gradient
+// of J = gP P + gH H into bT, bq [pver], blam, btau (all zeroed first).
+// w_heat: [pver] weights, or nullptr for w_k = p_mid_k / ps.
+__device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_deep_params& P,
+                                                    double dt, double lam, double tau,
+                                                    Column<double>& c, double gP, double gH,
+                                                    const double* w_heat, bool reverse,
+                                                    double* bT, double* bq, double& blam,
+                                                    double& btau, double& Pv, double& Hv) {
+  const int pver = c.pver;
+  for (int k = 0; k < pver; ++k) bT[k] = bq[k] = 0.0;
+  blam = btau = Pv = Hv = 0.0;
+  DeepTape<double> tp;
+  tp.active = false;
+  DeepTrig<double> t;
+  if (column_valid(c)) {
+    prologue(L, P.p_top_lim, c, true);
+    deep_trigger(c, P, t);
+    if (t.triggered) {
+      DeepOut<double> o;
+      o.flags = 0;
+      deep_plume<double, DeepTape<double>>(c, P, dt, lam, tau, t, o, &tp);
+    }
+  }
+  if (!tp.active) return;
+  const int kb = t.kb, klcl = t.klcl, kel = t.kel, jt = tp.jt, jd = tp.jd;
+  const double mb = tp.mb, ze = P.ent_zscale;
+  // objective pieces: P = mb max(0, sumR - alpha sumE), H = cp mb sum w m dT
+  double Hs = 0.0;
+  for (int k = jt; k <= kb; ++k)
+    Hs += (w_heat ? w_heat[k] : c.p_mid[k] / c.ps) * c.m[k] * tp.dT[k];
+  Pv = mb * tp.net;
+  Hv = CP * mb * Hs;
+  if (reverse) {
+    double bTv[MAXL], bzm[MAXL], bzi[MAXL + 1], bh[MAXL], beta[MAXL], bhu[MAXL], bqtu[MAXL];
+    double betad[MAXL], bhd[MAXL], bqd[MAXL], bdh[MAXL], bdq[MAXL], bdT[MAXL], bTp[MAXL];
+    for (int k = 0; k < pver; ++k) {
+      bTv[k] = bzm[k] = bzi[k] = bh[k] = beta[k] = bhu[k] = bqtu[k] = 0.0;
+      betad[k] = bhd[k] = bqd[k] = bdh[k] = bdq[k] = bdT[k] = bTp[k] = 0.0;
+    }
+    bzi[pver] = 0.0;
+    double bMb = 0.0, bCAPE = 0.0, bF = 0.0, bsumR = 0.0, bsumE = 0.0, balpha = 0.0;
+
+    // seeds from the objective
+    for (int k = jt; k <= kb; ++k)
+      bdT[k] += gH * CP * mb * (w_heat ? w_heat[k] : c.p_mid[k] / c.ps) * c.m[k];
+    bMb += gH * CP * Hs;
+    if (tp.net_pos) {
+      bMb += gP * tp.net;
+      const double bnet = gP * mb;
+      bsumR += bnet;
+      balpha -= bnet * tp.sumE;
+      bsumE -= bnet * tp.alpha;
+    }
+
+    // closure or limiter
+    if (tp.limited) {
+      const int ks = tp.kstar;
+      const double N = c.q[ks] - P.q_min, Dn = -dt * tp.dq[ks];
+      bq[ks] += bMb / Dn;
+      bdq[ks] += bMb * N * dt / (Dn * Dn);
+    } else {
+      const double F = tp.F, cape = t.cape;
+      bCAPE += -bMb / (tau * F);
+      btau += bMb * cape / (tau * tau * F);
+      bF += bMb * cape / (tau * F * F);
+      const double dhkb = tp.dh[kb];
+      for (int k = kel; k <= klcl; ++k) {
+        const double Tp = t.Tp[k];
+        double qsp, dqsp, d2qsp;
+        qs_derivs(Tp, c.p_mid[k], qsp, dqsp, d2qsp);
+        const double Av = (1.0 + ZVIR * qsp) + ZVIR * Tp * dqsp, Bv = CP + LV * dqsp;
+        const double w1 = bF * RD * c.dlnp[k];
+        bdh[kb] += w1 * Av / Bv;
+        const double bdTvp = w1 * dhkb;
+        const double bdTv = -w1;
+        const bool in_plume = k >= jt && k <= kb;  // dT, dq are constant zero elsewhere
+        const double dTk = in_plume ? tp.dT[k] : 0.0, dqk = in_plume ? tp.dq[k] : 0.0;
+        bq[k] += bdTv * ZVIR * dTk;
+        bT[k] += bdTv * ZVIR * dqk;
+        if (in_plume) {
+          bdT[k] += bdTv * (1.0 + ZVIR * c.q[k]);
+          bdq[k] += bdTv * ZVIR * c.T[k];
+        }
+        const double bA = bdTvp / Bv, bB = -bdTvp * Av / (Bv * Bv);
+        const double bqsp = bA * ZVIR, bdqsp = bA * ZVIR * Tp + bB * LV;
+        bTp[k] += bA * ZVIR * dqsp + bqsp * dqsp + bdqsp * d2qsp;
+      }
+    }
+
+    // tendencies: dT = (dh - Lv dq)/cp, dh = dh_raw/m
+    double bhr[MAXL], bqr[MAXL];
+    for (int k = 0; k < pver; ++k) bhr[k] = bqr[k] = 0.0;
+    for (int k = jt; k <= kb; ++k) {
+      bdh[k] += bdT[k] / CP;
+      bdq[k] -= LV * bdT[k] / CP;
+      bhr[k] = bdh[k] / c.m[k];
+      bqr[k] = bdq[k] / c.m[k];
+    }
+    if (jd >= 0) {
+      const double al = tp.alpha;
+      for (int k = jd; k <= kb - 1; ++k) {
+        const double D = al * tp.etad[k];
+        const double bD = bhr[k] * (c.h[k + 1] - c.h[k]) + bqr[k] * (c.q[k + 1] - c.q[k]);
+        bh[k + 1] += bhr[k] * D;
+        bh[k] -= bhr[k] * D;
+        bq[k + 1] += bqr[k] * D;
+        bq[k] -= bqr[k] * D;
+        balpha += bD * tp.etad[k];
+        betad[k] += bD * al;
+      }
+      const double D = al * tp.etad[kb - 1];
+      const double bD = bhr[kb] * (tp.hd[kb - 1] - c.h[kb]) + bqr[kb] * (tp.qd[kb - 1] - c.q[kb]);
+      bhd[kb - 1] += bhr[kb] * D;
+      bh[kb] -= bhr[kb] * D;
+      bqd[kb - 1] += bqr[kb] * D;
+      bq[kb] -= bqr[kb] * D;
+      balpha += bD * tp.etad[kb - 1];
+      betad[kb - 1] += bD * al;
+    }
+    for (int k = jt + 1; k <= kb; ++k) {
+      const double e = tp.eta[k];
+      bh[k - 1] += bhr[k] * e;
+      bh[k] -= bhr[k] * e;
+      bq[k - 1] += bqr[k] * e;
+      bq[k] -= bqr[k] * e;
+      beta[k] += bhr[k] * (c.h[k - 1] - c.h[k]) + bqr[k] * (c.q[k - 1] - c.q[k]);
+    }
+    beta[jt + 1] += bhr[jt] * (tp.hu[jt + 1] - c.h[jt]) + bqr[jt] * (tp.qtu[jt + 1] - c.q[jt]);
+    bhu[jt + 1] += bhr[jt] * tp.eta[jt + 1];
+    bh[jt] -= bhr[jt] * tp.eta[jt + 1];
+    bqtu[jt + 1] += bqr[jt] * tp.eta[jt + 1];
+    bq[jt] -= bqr[jt] * tp.eta[jt + 1];
+
+    // downdraft: alpha, evaporation sum (telescoped), saturation, mixing, mass flux
+    if (jd >= 0) {
+      const double sR = tp.sumR, sE = tp.sumE;
+      if (tp.capped) {
+        bsumR += balpha / sE;
+        bsumE -= balpha * sR / (sE * sE);
+      }
+      betad[kb - 1] += bsumE * tp.qd[kb - 1];
+      bqd[kb - 1] += bsumE * tp.etad[kb - 1];
+      for (int k = jd; k <= kb - 1; ++k) {
+        const double eprev = k > jd ? tp.etad[k - 1] : 0.0;
+        bq[k] -= bsumE * (tp.etad[k] - eprev);
+        betad[k] -= bsumE * c.q[k];
+        if (k > jd) betad[k - 1] += bsumE * c.q[k];
+      }
+      for (int k = kb - 1; k >= jd; --k) {
+        if (bqd[k] != 0.0) {
+          double qs, dqs, d2;
+          qs_derivs(tp.Td[k], c.p_mid[k], qs, dqs, d2);
+          inv_adj(tp.Td[k], c.p_mid[k], bqd[k] * dqs, bhd[k], bzm[k]);
+        }
+        if (k > jd) {
+          const double e = tp.etad[k], ep = tp.etad[k - 1];
+          betad[k - 1] += bhd[k] * (tp.hd[k - 1] - c.h[k]) / e;
+          bhd[k - 1] += bhd[k] * ep / e;
+          bh[k] += bhd[k] * (e - ep) / e;
+          betad[k] += bhd[k] * (c.h[k] - tp.hd[k]) / e;
+        } else {
+          bh[jd] += bhd[jd];
+        }
+      }
+      for (int k = jd; k <= kb - 1; ++k) {
+        const double u = 1.0 + (c.z_mid[jd] - c.z_mid[k]) / ze;
+        blam += betad[k] * tp.etad[k] * ze * log(u);
+        const double bu = betad[k] * tp.etad[k] * lam * ze / u;
+        bzm[jd] += bu / ze;
+        bzm[k] -= bu / ze;
+      }
+    }
+
+    // updraft, reverse of its upward recurrence
+    const double c0 = P.c0;
+    for (int k = jt + 1; k <= kb - 1; ++k) {
+      const double e = tp.eta[k], e1 = tp.eta[k + 1];
+      double bqt = bqtu[k];
+      const double bR = bsumR - bqtu[k] / e;
+      beta[k] += bqtu[k] * tp.rain[k] / (e * e);
+      const double dz = tp.dz[k];
+      const double g = c0 * dz / (1.0 + c0 * dz), gp = c0 / ((1.0 + c0 * dz) * (1.0 + c0 * dz));
+      const double l = (e * g) != 0.0 ? tp.rain[k] / (e * g) : 0.0;
+      beta[k] += bR * l * g;
+      const double bl = bR * e * g;
+      const double bdz = bR * e * l * gp;
+      bzi[k] += bdz;
+      bzi[k + 1] -= bdz;
+      if (tp.lpos[k]) {
+        bqt += bl;
+        double qs, dqs, d2;
+        qs_derivs(tp.Ts[k], c.p_mid[k], qs, dqs, d2);
+        inv_adj(tp.Ts[k], c.p_mid[k], -bl * dqs, bhu[k], bzm[k]);
+      }
+      beta[k + 1] += bqt * (tp.qtu[k + 1] - c.q[k]) / e;
+      bqtu[k + 1] += bqt * e1 / e;
+      bq[k] += bqt * (e - e1) / e;
+      beta[k] += bqt * (c.q[k] - tp.qt[k]) / e;
+      beta[k + 1] += bhu[k] * (tp.hu[k + 1] - c.h[k]) / e;
+      bhu[k + 1] += bhu[k] * e1 / e;
+      bh[k] += bhu[k] * (e - e1) / e;
+      beta[k] += bhu[k] * (c.h[k] - tp.hu[k]) / e;
+    }
+    bh[kb] += bhu[kb];
+    bq[kb] += bqtu[kb];
+    for (int k = jt + 1; k <= kb - 1; ++k) {
+      const double u = 1.0 + (c.z_mid[k] - c.z_mid[kb]) / ze;
+      blam += beta[k] * tp.eta[k] * ze * log(u);
+      const double bu = beta[k] * tp.eta[k] * lam * ze / u;
+      bzm[k] += bu / ze;
+      bzm[kb] -= bu / ze;
+    }
+
+    // undilute parcel and CAPE (closure branch only)
+    for (int k = kel; k <= klcl; ++k) {
+      const double Tp = t.Tp[k];
+      double qp, dqp, d2;
+      qs_derivs(Tp, c.p_mid[k], qp, dqp, d2);
+      const double bb = bCAPE * RD * c.dlnp[k];
+      bTp[k] += bb * ((1.0 + ZVIR * qp) + Tp * ZVIR * dqp);
+      bTv[k] -= bb;
+      inv_adj(Tp, c.p_mid[k], bTp[k], bh[kb], bzm[k]);
+    }
+
+    // moist static energy, heights, virtual temperature
+    for (int k = 0; k < pver; ++k) {
+      bT[k] += CP * bh[k];
+      bzm[k] += GRAV * bh[k];
+      bq[k] += LV * bh[k];
+    }
+    const PressFP64 Pr{L, c.ps};
+    for (int k = 0; k < pver; ++k) {
+      bzi[k + 1] += bzi[k] + bzm[k];
+      const double L2 = log(Pr.pi(k + 1) / c.p_mid[k]);
+      const double bs = bzi[k] * c.dlnp[k] + bzm[k] * L2;
+      bTv[k] += bs * (RD / GRAV);
+    }
+    for (int k = 0; k < pver; ++k) {
+      bT[k] += bTv[k] * (1.0 + ZVIR * c.q[k]);
+      bq[k] += bTv[k] * c.T[k] * ZVIR;
+    }
+  }
+}
+
+}  // namespace cvg

@@ -454,12 +454,30 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   t.triggered = cape > P.capelmt;
 }
 
+// Intermediate state of deep_plume, recorded only for the adjoint kernel (the
+// forward kernels instantiate NoTape and record nothing).
+struct NoTape {
+  static constexpr bool kOn = false;
+};
+template <class R>
+struct DeepTape {
+  static constexpr bool kOn = true;
+  R eta[MAXL], hu[MAXL], qt[MAXL], Ts[MAXL], rain[MAXL], dz[MAXL], qtu[MAXL];
+  R etad[MAXL], hd[MAXL], Td[MAXL], qd[MAXL];
+  R dh[MAXL], dq[MAXL], dT[MAXL];
+  bool lpos[MAXL];
+  R sumR, sumE, alpha, F, mb, net;
+  int jt, jd, kstar;
+  bool capped, limited, active, net_pos;
+};
+
 // Updraft, downdraft, tendencies, closure and limiter of a triggered column
 // (deep "stage B": the entrainment and precipitation loops of Alg. 2).
-template <class R>
+template <class R, class TP = NoTape>
 __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_params& P,
                                            double dt, R lam, R tau, DeepTrig<R>& t,
-                                           DeepOut<R>& o) {
+                                           DeepOut<R>& o, TP* tape = nullptr) {
+  if constexpr (TP::kOn) tape->active = false;
   const int pver = c.pver, ktl = c.ktl, kb = t.kb, klcl = t.klcl, kel = t.kel;
   const R ze = (R)P.ent_zscale;
   // minimum h* layer above the LCL (ties: lowest)
@@ -490,11 +508,19 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
     const R Ts = moist_invert(hu[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
                               seq, t.newton, c.Tref, c.qref);
     R l = qt - sat_qs(Ts, c.p_mid[k]);
+    const bool lpos = l > R(0);
     if (l < R(0)) l = R(0);
     const R dz = c.z_int[k] - c.z_int[k + 1];
     const R rain = Mth<R>::dv(e * c0 * dz * l, R(1) + c0 * dz);
     qtu[k] = qt - rain * re;
     sumR += rain;
+    if constexpr (TP::kOn) {
+      tape->qt[k] = qt;
+      tape->Ts[k] = Ts;
+      tape->lpos[k] = lpos;
+      tape->rain[k] = rain;
+      tape->dz[k] = dz;
+    }
   }
   if (jt < 0 || jt >= klcl) return;
 
@@ -515,12 +541,15 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
       const R Td = moist_invert(hd[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
                                 seq, t.newton, c.Tref, c.qref);
       qd[k] = sat_qs(Td, c.p_mid[k]);
+      if constexpr (TP::kOn) tape->Td[k] = Td;
       sumE += e * qd[k] - eprev * qprev - (e - eprev) * c.q[k];
       qprev = qd[k];
       eprev = e;
     }
     alpha = (R)P.alpha_dd;
-    if (alpha * sumE > sumR) alpha = Mth<R>::dv(sumR, sumE);
+    const bool capped = alpha * sumE > sumR;
+    if (capped) alpha = Mth<R>::dv(sumR, sumE);
+    if constexpr (TP::kOn) tape->capped = capped;
   }
 
   // unit tendencies (per M_b) in flux form
@@ -563,18 +592,49 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   if (!(F < R(0))) return;
   R mb = Mth<R>::dv((R)(-t.cape), tau * F);
   bool limited = false;
+  int kstar = -1;
   for (int k = jt; k <= kb; ++k) {
     if (dq[k] < R(0)) {
       const R ml = Mth<R>::dv(c.q[k] - (R)P.q_min, -(R)dt * dq[k]);
       if (ml < mb) {
         mb = ml;
         limited = true;
+        kstar = k;
       }
     }
   }
   if (!(mb > R(0))) return;
   R net = sumR - alpha * sumE;
+  const bool net_pos = net >= R(0);
   if (net < R(0)) net = R(0);
+  if constexpr (TP::kOn) {
+    tape->active = true;
+    tape->jt = jt;
+    tape->jd = jd;
+    tape->kstar = kstar;
+    tape->limited = limited;
+    tape->net_pos = net_pos;
+    tape->sumR = sumR;
+    tape->sumE = sumE;
+    tape->alpha = alpha;
+    tape->F = F;
+    tape->mb = mb;
+    tape->net = net;
+    if (jd < 0) tape->capped = false;
+    for (int k = 0; k < pver; ++k) {
+      tape->eta[k] = eta[k];
+      tape->hu[k] = hu[k];
+      tape->qtu[k] = qtu[k];
+      tape->dh[k] = dh[k];
+      tape->dq[k] = dq[k];
+      tape->dT[k] = dT[k];
+      if (jd >= 0) {
+        tape->etad[k] = etad[k];
+        tape->hd[k] = hd[k];
+        tape->qd[k] = qd[k];
+      }
+    }
+  }
   o.flags |= CONV_FLAG_ACTIVE | (limited ? CONV_FLAG_LIMITED : 0);
   o.mb = (double)mb;
   o.prec = (double)(mb * net);

@@ -238,6 +238,33 @@ conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
   return dispatch(a, prec, launch, ws, ws_bytes);
 }
 
+conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
+                              const conv_deep_params* par, double dt, conv_precision prec,
+                              const double* gP, const double* gH, const double* w_heat,
+                              double* gT, double* gq, double* glambda, double* gtau,
+                              double* P_out, double* H_out, conv_stream stream) {
+  if (prec != CONV_FP64) return prec == CONV_MIXED ? CONV_ERR_UNSUPPORTED : CONV_ERR_ARG;
+  RunArgs a;
+  conv_status s = common_in(grid, in, dt, a);
+  if (s != CONV_OK) return s;
+  if (!deep_params_ok(par)) return CONV_ERR_ARG;
+  const int n_grad = (gT != nullptr) + (gq != nullptr) + (glambda != nullptr) + (gtau != nullptr);
+  if (n_grad != 0 && n_grad != 4) return CONV_ERR_ARG;
+  if (n_grad == 0 && !P_out && !H_out) return CONV_ERR_ARG;
+  cvg::AdjW w;
+  w.given = w_heat != nullptr;
+  for (int k = 0; k < CONV_MAX_LEVELS; ++k) {
+    w.w[k] = (w_heat && k < grid->pver) ? w_heat[k] : 0.0;
+    if (!std::isfinite(w.w[k])) return CONV_ERR_ARG;
+  }
+  a.dp = *par;
+  a.mode = cvg::MODE_DEEP;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e =
+      cvg::launch_deep_adjoint(a, gP, gH, w, gT, gq, glambda, gtau, P_out, H_out);
+  return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
+
 }  // extern "C"
 
 // ================================================================ batches

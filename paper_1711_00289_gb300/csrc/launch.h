@@ -51,4 +51,15 @@ inline void record_stage(const RunArgs& a, int i) {
 // Plain path: one thread per column, whole scheme, no compaction.
 cudaError_t launch_plain(const RunArgs& a, bool fp64);
 
+// Heating weights of the adjoint's objective, passed by value in the launch.
+struct AdjW {
+  double w[MAXL];
+  bool given;  // false: w_k = p_mid_k / ps
+};
+// Deep-scheme adjoint (FP64): one thread per column.  gT == nullptr: no
+// reverse sweep (gq, glam, gtau unused); Pout, Hout may be nullptr.
+cudaError_t launch_deep_adjoint(const RunArgs& a, const double* gP, const double* gH,
+                                const AdjW& w, double* gT, double* gq, double* glam,
+                                double* gtau, double* Pout, double* Hout);
+
 }  // namespace cvg

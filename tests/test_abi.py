@@ -130,3 +130,29 @@ def test_batch_plan_validates_members_before_touching_a_device():
     assert lib.conv_batch_plan(m, 0, L.CONV_FP64, C.byref(h)) == L.CONV_ERR_ARG
     assert lib.conv_batch_workspace_bytes(None) == 0
     lib.conv_batch_free(None)
+
+
+def test_adjoint_arguments_checked_on_host():
+    g, inp, out, keep = _args()
+    dp = L.deep_defaults()
+    lib = L.lib()
+    fake = C.c_void_p(0x1000)
+    w = (C.c_double * 30)(*([1.0] * 30))
+
+    def call(prec=L.CONV_FP64, grads=(fake,) * 4, P=None, H=None, wh=None, dt=1800.0):
+        return lib.conv_deep_adjoint(C.byref(g), C.byref(inp), C.byref(dp), dt, prec, None,
+                                     None, wh, *grads, P, H, None)
+
+    # n_cols = 0: a valid request enqueues nothing and succeeds without a device
+    assert call() == L.CONV_OK
+    assert call(grads=(None,) * 4, P=fake) == L.CONV_OK
+    assert call(wh=w) == L.CONV_OK
+    assert call(prec=L.CONV_MIXED) == L.CONV_ERR_UNSUPPORTED
+    assert call(prec=7) == L.CONV_ERR_ARG
+    assert call(grads=(fake, fake, None, fake)) == L.CONV_ERR_ARG
+    assert call(grads=(None,) * 4) == L.CONV_ERR_ARG  # nothing requested
+    assert call(dt=0.0) == L.CONV_ERR_ARG
+    w[3] = float("nan")
+    assert call(wh=w) == L.CONV_ERR_ARG
+    dp.tau_default = 0.0
+    assert call() == L.CONV_ERR_ARG
