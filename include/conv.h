@@ -35,7 +35,9 @@
  * read during the call.  Run calls are asynchronous on the given stream: they
  * validate arguments on the host, enqueue kernels and return.  The library
  * never allocates on a run path and never synchronises the stream.  Calls on
- * different streams with disjoint buffers may run concurrently.
+ * different streams with disjoint buffers may run concurrently.  Output arrays
+ * must not overlap the inputs (the kernels re-read T and q through the
+ * read-only cache while they write tendencies).
  *
  * Errors.  Argument errors are detected on the host before anything is
  * enqueued (CONV_ERR_ARG / CONV_ERR_WORKSPACE / CONV_ERR_UNSUPPORTED); a launch

@@ -19,26 +19,19 @@ struct AdjArgs {
   double* Hout;
 };
 
-__global__ void __launch_bounds__(64) k_deep_adjoint(AdjArgs A) {
+__global__ void __launch_bounds__(64) k_deep_adjoint(const __grid_constant__ AdjArgs A) {
   const RunArgs& a = A.a;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   const int pver = a.L.pver, ld = a.ld;
   Column<double> c;
-  c.pver = pver;
-  c.ps = a.ps[i];
-  const double* T = static_cast<const double*>(a.T);
-  const double* q = static_cast<const double*>(a.q);
-  for (int k = 0; k < pver; ++k) {
-    c.T[k] = T[(size_t)k * ld + i];
-    c.q[k] = q[(size_t)k * ld + i];
-  }
+  init_column(c, a.L, input_src<double>(a, i), a.ps[i]);
   const double lam = a.lam ? a.lam[i] : a.dp.lambda_default;
   const double tau = a.tau ? a.tau[i] : a.dp.tau_default;
   const double gP = A.gP ? A.gP[i] : 0.0, gH = A.gH ? A.gH[i] : 0.0;
   const bool rev = A.gT != nullptr;
   double bT[MAXL], bq[MAXL], blam, btau, Pv, Hv;
-  deep_adjoint_column(a.L, a.dp, a.dt, lam, tau, c, gP, gH, A.w.given ? A.w.w : nullptr, rev, bT,
+  deep_adjoint_column(a.dp, a.dt, lam, tau, c, gP, gH, A.w.given ? A.w.w : nullptr, rev, bT,
                       bq, blam, btau, Pv, Hv);
   if (rev) {
     for (int k = 0; k < pver; ++k) {

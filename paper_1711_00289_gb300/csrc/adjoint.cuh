@@ -46,8 +46,8 @@ __device__ __forceinline__ void inv_adj(double T, double p, double bT, double& b
 // H = sum_k w_k m_k cp dTdt_k into Pv, Hv, and -- when `reverse` -- the gradient
 // of J = gP P + gH H into bT, bq [pver], blam, btau (all zeroed first).
 // w_heat: [pver] weights, or nullptr for w_k = p_mid_k / ps.
-__device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_deep_params& P,
-                                                    double dt, double lam, double tau,
+__device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P, double dt,
+                                                    double lam, double tau,
                                                     Column<double>& c, double gP, double gH,
                                                     const double* w_heat, bool reverse,
                                                     double* bT, double* bq, double& blam,
@@ -59,12 +59,13 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
   tp.active = false;
   DeepTrig<double> t;
   if (column_valid(c)) {
-    prologue(L, P.p_top_lim, c, true);
+    double hs[MAXL];
+    prologue(P.p_top_lim, c, hs);
     deep_trigger(c, P, t);
     if (t.triggered) {
-      DeepOut<double> o;
+      DeepOut o;
       o.flags = 0;
-      deep_plume<double, DeepTape<double>>(c, P, dt, lam, tau, t, o, &tp);
+      deep_plume<double, DeepTape<double>>(c, hs, P, dt, lam, tau, t, o, NoOut<double>(), &tp);
     }
   }
   if (!tp.active) return;
@@ -73,7 +74,7 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
   // objective pieces: P = mb max(0, sumR - alpha sumE), H = cp mb sum w m dT
   double Hs = 0.0;
   for (int k = jt; k <= kb; ++k)
-    Hs += (w_heat ? w_heat[k] : c.p_mid[k] / c.ps) * c.m[k] * tp.dT[k];
+    Hs += (w_heat ? w_heat[k] : c.pm(k) / c.ps) * c.m(k) * tp.dT[k];
   Pv = mb * tp.net;
   Hv = CP * mb * Hs;
   if (reverse) {
@@ -88,7 +89,7 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
 
     // seeds from the objective
     for (int k = jt; k <= kb; ++k)
-      bdT[k] += gH * CP * mb * (w_heat ? w_heat[k] : c.p_mid[k] / c.ps) * c.m[k];
+      bdT[k] += gH * CP * mb * (w_heat ? w_heat[k] : c.pm(k) / c.ps) * c.m(k);
     bMb += gH * CP * Hs;
     if (tp.net_pos) {
       bMb += gP * tp.net;
@@ -101,7 +102,7 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
     // closure or limiter
     if (tp.limited) {
       const int ks = tp.kstar;
-      const double N = c.q[ks] - P.q_min, Dn = -dt * tp.dq[ks];
+      const double N = c.q(ks) - P.q_min, Dn = -dt * tp.dq[ks];
       bq[ks] += bMb / Dn;
       bdq[ks] += bMb * N * dt / (Dn * Dn);
     } else {
@@ -113,9 +114,9 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
       for (int k = kel; k <= klcl; ++k) {
         const double Tp = t.Tp[k];
         double qsp, dqsp, d2qsp;
-        qs_derivs(Tp, c.p_mid[k], qsp, dqsp, d2qsp);
+        qs_derivs(Tp, c.pm(k), qsp, dqsp, d2qsp);
         const double Av = (1.0 + ZVIR * qsp) + ZVIR * Tp * dqsp, Bv = CP + LV * dqsp;
-        const double w1 = bF * RD * c.dlnp[k];
+        const double w1 = bF * RD * c.dl[k];
         bdh[kb] += w1 * Av / Bv;
         const double bdTvp = w1 * dhkb;
         const double bdTv = -w1;
@@ -124,8 +125,8 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
         bq[k] += bdTv * ZVIR * dTk;
         bT[k] += bdTv * ZVIR * dqk;
         if (in_plume) {
-          bdT[k] += bdTv * (1.0 + ZVIR * c.q[k]);
-          bdq[k] += bdTv * ZVIR * c.T[k];
+          bdT[k] += bdTv * (1.0 + ZVIR * c.q(k));
+          bdq[k] += bdTv * ZVIR * c.T(k);
         }
         const double bA = bdTvp / Bv, bB = -bdTvp * Av / (Bv * Bv);
         const double bqsp = bA * ZVIR, bdqsp = bA * ZVIR * Tp + bB * LV;
@@ -139,14 +140,14 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
     for (int k = jt; k <= kb; ++k) {
       bdh[k] += bdT[k] / CP;
       bdq[k] -= LV * bdT[k] / CP;
-      bhr[k] = bdh[k] / c.m[k];
-      bqr[k] = bdq[k] / c.m[k];
+      bhr[k] = bdh[k] / c.m(k);
+      bqr[k] = bdq[k] / c.m(k);
     }
     if (jd >= 0) {
       const double al = tp.alpha;
       for (int k = jd; k <= kb - 1; ++k) {
         const double D = al * tp.etad[k];
-        const double bD = bhr[k] * (c.h[k + 1] - c.h[k]) + bqr[k] * (c.q[k + 1] - c.q[k]);
+        const double bD = bhr[k] * (c.h(k + 1) - c.h(k)) + bqr[k] * (c.q(k + 1) - c.q(k));
         bh[k + 1] += bhr[k] * D;
         bh[k] -= bhr[k] * D;
         bq[k + 1] += bqr[k] * D;
@@ -155,7 +156,7 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
         betad[k] += bD * al;
       }
       const double D = al * tp.etad[kb - 1];
-      const double bD = bhr[kb] * (tp.hd[kb - 1] - c.h[kb]) + bqr[kb] * (tp.qd[kb - 1] - c.q[kb]);
+      const double bD = bhr[kb] * (tp.hd[kb - 1] - c.h(kb)) + bqr[kb] * (tp.qd[kb - 1] - c.q(kb));
       bhd[kb - 1] += bhr[kb] * D;
       bh[kb] -= bhr[kb] * D;
       bqd[kb - 1] += bqr[kb] * D;
@@ -169,9 +170,9 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
       bh[k] -= bhr[k] * e;
       bq[k - 1] += bqr[k] * e;
       bq[k] -= bqr[k] * e;
-      beta[k] += bhr[k] * (c.h[k - 1] - c.h[k]) + bqr[k] * (c.q[k - 1] - c.q[k]);
+      beta[k] += bhr[k] * (c.h(k - 1) - c.h(k)) + bqr[k] * (c.q(k - 1) - c.q(k));
     }
-    beta[jt + 1] += bhr[jt] * (tp.hu[jt + 1] - c.h[jt]) + bqr[jt] * (tp.qtu[jt + 1] - c.q[jt]);
+    beta[jt + 1] += bhr[jt] * (tp.hu[jt + 1] - c.h(jt)) + bqr[jt] * (tp.qtu[jt + 1] - c.q(jt));
     bhu[jt + 1] += bhr[jt] * tp.eta[jt + 1];
     bh[jt] -= bhr[jt] * tp.eta[jt + 1];
     bqtu[jt + 1] += bqr[jt] * tp.eta[jt + 1];
@@ -189,27 +190,27 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
       for (int k = jd; k <= kb - 1; ++k) {
         const double eprev = k > jd ? tp.etad[k - 1] : 0.0;
         bq[k] -= bsumE * (tp.etad[k] - eprev);
-        betad[k] -= bsumE * c.q[k];
-        if (k > jd) betad[k - 1] += bsumE * c.q[k];
+        betad[k] -= bsumE * c.q(k);
+        if (k > jd) betad[k - 1] += bsumE * c.q(k);
       }
       for (int k = kb - 1; k >= jd; --k) {
         if (bqd[k] != 0.0) {
           double qs, dqs, d2;
-          qs_derivs(tp.Td[k], c.p_mid[k], qs, dqs, d2);
-          inv_adj(tp.Td[k], c.p_mid[k], bqd[k] * dqs, bhd[k], bzm[k]);
+          qs_derivs(tp.Td[k], c.pm(k), qs, dqs, d2);
+          inv_adj(tp.Td[k], c.pm(k), bqd[k] * dqs, bhd[k], bzm[k]);
         }
         if (k > jd) {
           const double e = tp.etad[k], ep = tp.etad[k - 1];
-          betad[k - 1] += bhd[k] * (tp.hd[k - 1] - c.h[k]) / e;
+          betad[k - 1] += bhd[k] * (tp.hd[k - 1] - c.h(k)) / e;
           bhd[k - 1] += bhd[k] * ep / e;
           bh[k] += bhd[k] * (e - ep) / e;
-          betad[k] += bhd[k] * (c.h[k] - tp.hd[k]) / e;
+          betad[k] += bhd[k] * (c.h(k) - tp.hd[k]) / e;
         } else {
           bh[jd] += bhd[jd];
         }
       }
       for (int k = jd; k <= kb - 1; ++k) {
-        const double u = 1.0 + (c.z_mid[jd] - c.z_mid[k]) / ze;
+        const double u = 1.0 + (c.zm[jd] - c.zm[k]) / ze;
         blam += betad[k] * tp.etad[k] * ze * log(u);
         const double bu = betad[k] * tp.etad[k] * lam * ze / u;
         bzm[jd] += bu / ze;
@@ -230,27 +231,26 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
       beta[k] += bR * l * g;
       const double bl = bR * e * g;
       const double bdz = bR * e * l * gp;
-      bzi[k] += bdz;
-      bzi[k + 1] -= bdz;
+      bTv[k] += bdz * (RD / GRAV) * c.dl[k];  // dz = (Rd Tv / g) ln(p_k+1/p_k)
       if (tp.lpos[k]) {
         bqt += bl;
         double qs, dqs, d2;
-        qs_derivs(tp.Ts[k], c.p_mid[k], qs, dqs, d2);
-        inv_adj(tp.Ts[k], c.p_mid[k], -bl * dqs, bhu[k], bzm[k]);
+        qs_derivs(tp.Ts[k], c.pm(k), qs, dqs, d2);
+        inv_adj(tp.Ts[k], c.pm(k), -bl * dqs, bhu[k], bzm[k]);
       }
-      beta[k + 1] += bqt * (tp.qtu[k + 1] - c.q[k]) / e;
+      beta[k + 1] += bqt * (tp.qtu[k + 1] - c.q(k)) / e;
       bqtu[k + 1] += bqt * e1 / e;
       bq[k] += bqt * (e - e1) / e;
-      beta[k] += bqt * (c.q[k] - tp.qt[k]) / e;
-      beta[k + 1] += bhu[k] * (tp.hu[k + 1] - c.h[k]) / e;
+      beta[k] += bqt * (c.q(k) - tp.qt[k]) / e;
+      beta[k + 1] += bhu[k] * (tp.hu[k + 1] - c.h(k)) / e;
       bhu[k + 1] += bhu[k] * e1 / e;
       bh[k] += bhu[k] * (e - e1) / e;
-      beta[k] += bhu[k] * (c.h[k] - tp.hu[k]) / e;
+      beta[k] += bhu[k] * (c.h(k) - tp.hu[k]) / e;
     }
     bh[kb] += bhu[kb];
     bq[kb] += bqtu[kb];
     for (int k = jt + 1; k <= kb - 1; ++k) {
-      const double u = 1.0 + (c.z_mid[k] - c.z_mid[kb]) / ze;
+      const double u = 1.0 + (c.zm[k] - c.zm[kb]) / ze;
       blam += beta[k] * tp.eta[k] * ze * log(u);
       const double bu = beta[k] * tp.eta[k] * lam * ze / u;
       bzm[k] += bu / ze;
@@ -261,11 +261,11 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
     for (int k = kel; k <= klcl; ++k) {
       const double Tp = t.Tp[k];
       double qp, dqp, d2;
-      qs_derivs(Tp, c.p_mid[k], qp, dqp, d2);
-      const double bb = bCAPE * RD * c.dlnp[k];
+      qs_derivs(Tp, c.pm(k), qp, dqp, d2);
+      const double bb = bCAPE * RD * c.dl[k];
       bTp[k] += bb * ((1.0 + ZVIR * qp) + Tp * ZVIR * dqp);
       bTv[k] -= bb;
-      inv_adj(Tp, c.p_mid[k], bTp[k], bh[kb], bzm[k]);
+      inv_adj(Tp, c.pm(k), bTp[k], bh[kb], bzm[k]);
     }
 
     // moist static energy, heights, virtual temperature
@@ -274,16 +274,16 @@ __device__ __forceinline__ void deep_adjoint_column(const Levels& L, const conv_
       bzm[k] += GRAV * bh[k];
       bq[k] += LV * bh[k];
     }
-    const PressFP64 Pr{L, c.ps};
+    const PressFP64 Pr = c.press();
     for (int k = 0; k < pver; ++k) {
       bzi[k + 1] += bzi[k] + bzm[k];
-      const double L2 = log(Pr.pi(k + 1) / c.p_mid[k]);
-      const double bs = bzi[k] * c.dlnp[k] + bzm[k] * L2;
+      const double L2 = log(Pr.pi(k + 1) / c.pm(k));
+      const double bs = bzi[k] * c.dl[k] + bzm[k] * L2;
       bTv[k] += bs * (RD / GRAV);
     }
     for (int k = 0; k < pver; ++k) {
-      bT[k] += bTv[k] * (1.0 + ZVIR * c.q[k]);
-      bq[k] += bTv[k] * c.T[k] * ZVIR;
+      bT[k] += bTv[k] * (1.0 + ZVIR * c.q(k));
+      bq[k] += bTv[k] * c.T(k) * ZVIR;
     }
   }
 }

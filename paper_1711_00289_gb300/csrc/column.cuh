@@ -275,19 +275,12 @@ __device__ __forceinline__ double lcl_p(float Tb, float qb, float pb, int n_newt
   return pbd * exp(INV_KAPPA * (lr - step * (double)fdiv_ieee(1.f, T)));
 }
 
-// Largest k <= kstart with p_mid[k] <= pL, or -1.  In FP32 the comparison runs
-// against pL rounded towards -inf to float: for a float x and a double y,
-// x <= y exactly when x <= round_down(y), so the decision is the FP64 one
-// without a conversion per level on the FP64 pipe.
+// LCL layer comparisons p_mid[k] <= pL.  In FP32 the comparison runs against pL
+// rounded towards -inf to float: for a float x and a double y, x <= y exactly
+// when x <= round_down(y), so the decision is the FP64 one without a conversion
+// per level on the FP64 pipe.
 __device__ __forceinline__ float cmp_bound(double pL, float) { return __double2float_rd(pL); }
 __device__ __forceinline__ double cmp_bound(double pL, double) { return pL; }
-template <class R>
-__device__ __forceinline__ int lcl_level(const R* p_mid, int kstart, double pL) {
-  const R b = cmp_bound(pL, R(0));
-  for (int k = kstart; k >= 0; --k)
-    if (p_mid[k] <= b) return k;
-  return -1;
-}
 
 // Entraining mass-flux profile (1 + dz/z_e)^(lambda z_e).
 template <class R>
@@ -295,37 +288,83 @@ __device__ __forceinline__ R entrain_growth(R lam, R ze, R dz) {
   return Mth<R>::ex(lam * ze * Mth<R>::lg(R(1) + Mth<R>::dv(dz, ze)));
 }
 
-// ---------------------------------------------------------------- column state
-// Column state.  Moist static energies h, hs (and every plume MSE derived from
-// them) are stored relative to cp Tref + Lv qref: in the mixed path (Tref,
-// qref) is the lowest layer's (T, q), so FP32 resolves MSE differences to
-// ~1e-3 J/kg instead of the 0.03 J/kg ulp of 3.4e5 J/kg; in the FP64 path the
-// reference is zero.  The reference cancels in every mixing rule, difference
-// and Newton residual.
+// ---------------------------------------------------------------- column sums
+// Running sum of working-precision terms (CAPE, CIN, the conservation sums),
+// accurate to FP64.  FP64 path: a plain FP64 sum.  Mixed path: a compensated
+// FP32 pair -- Knuth's TwoSum carries the rounding error of every addition into
+// a second FP32 word -- which keeps the sum of the FP32 terms to ~2^-48
+// relative without occupying the FP64 pipe (on this device 1/64 of the FP32
+// rate, and the pipe that bounds the trigger pass).
 template <class R>
-struct Column {
-  R T[MAXL], q[MAXL];
-  R p_mid[MAXL], dlnp[MAXL], m[MAXL];
-  R z_mid[MAXL], z_int[MAXL + 1], Tv[MAXL], h[MAXL], hs[MAXL];
-  R Tref, qref;
-  int pver, ktl;
-  double ps;
+struct Acc;
+template <>
+struct Acc<double> {
+  double s;
+  __device__ __forceinline__ Acc() : s(0.0) {}
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float hi, lo;
+  __device__ __forceinline__ Acc() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(x, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
-__device__ __forceinline__ bool in_range(double T, double q) {
-  return (T > 100.0 && T < 400.0) && (q >= 0.0 && q < 0.1);
+// ---------------------------------------------------------------- column state
+// T + dt*dT/dt as the schemes chain it (Alg. 1): FP64 without contraction.
+// (dt already in the working precision: the mixed path converts it once.)
+__device__ __forceinline__ double add_mul(double a, double dt, double b) {
+  return __dadd_rn(a, __dmul_rn(dt, b));
 }
-__device__ __forceinline__ bool in_range(float T, float q) {
-  return (T > 100.f && T < 400.f) && (q >= 0.f && q < 0.1f);
+__device__ __forceinline__ float add_mul(float a, float dt, float b) {
+  return __fmaf_rn(dt, b, a);
 }
 
-template <class R>
-__device__ __forceinline__ bool column_valid(const Column<R>& c) {
-  if (!(c.ps > 5.0e4 && c.ps < 1.2e5)) return false;
-  bool ok = true;
-  for (int k = 0; k < c.pver; ++k) ok = ok && in_range(c.T[k], c.q[k]);
-  return ok;
+// Moist static energy cp (T - Tref) + g z + Lv (q - qref), every operation rounded
+// explicitly so that each re-evaluation of a level's h is bit-identical.
+__device__ __forceinline__ double mse(double T, double q, double z, double Tref, double qref) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(CP, T - Tref), __dmul_rn(GRAV, z)),
+                   __dmul_rn(LV, q - qref));
 }
+__device__ __forceinline__ float mse(float T, float q, float z, float Tref, float qref) {
+  return __fmaf_rn((float)LV, __fsub_rn(q, qref),
+                   __fmaf_rn((float)CP, __fsub_rn(T, Tref), __fmul_rn((float)GRAV, z)));
+}
+
+// Where a column's T and q come from: the caller's input arrays, optionally
+// advanced by dt times the tendencies an earlier scheme has just written
+// (read back from its output arrays), with q floored at zero.
+template <class R>
+struct Src {
+  const R* T;
+  const R* q;
+  const R* dT;  // nullptr: no update
+  const R* dq;
+  R dt;
+  size_t ld;
+  int i;
+  bool floor_q;
+  __device__ __forceinline__ R Tk(int k) const {
+    const size_t o = (size_t)k * ld + i;
+    const R t = __ldg(T + o);
+    return dT ? add_mul(t, dt, dT[o]) : t;
+  }
+  __device__ __forceinline__ R qk(int k) const {
+    const size_t o = (size_t)k * ld + i;
+    const R v = __ldg(q + o);
+    if (!dq) return v;
+    const R u = add_mul(v, dt, dq[o]);
+    return (floor_q && u < R(0)) ? R(0) : u;
+  }
+};
 
 // Interface pressures: FP64 path rounds each operation as the definition reads
 // (no contraction); mixed path in FP32.
@@ -343,7 +382,9 @@ struct PressFP32 {
   const Levels& L;
   float ps;
   __device__ __forceinline__ float pi(int i) const { return fmaf(L.bf[i], ps, L.ap0f[i]); }
-  __device__ __forceinline__ float mid(float lo, float hi) const { return 0.5f * (hi + lo); }
+  __device__ __forceinline__ float mid(float lo, float hi) const {
+    return __fmul_rn(0.5f, __fadd_rn(hi, lo));
+  }
 };
 template <class R>
 struct PressOf {
@@ -354,47 +395,182 @@ struct PressOf<float> {
   using type = PressFP32;
 };
 
-// Levels, heights, moist static energies, top limit (shared by both schemes).
+// Column state.  The profile T, q stays where it is (Src: global memory, read
+// again where needed, L2-resident while the column is worked on); the thread
+// keeps only what costs a logarithm to rebuild: mid-layer heights z_mid and layer
+// log-thicknesses ln(p_k+1/p_k).  Pressures, layer masses, virtual temperatures,
+// moist static energies and layer depths are re-evaluated from those.
+// Moist static energies h, hs (and every plume MSE derived from them) are
+// relative to cp Tref + Lv qref: in the mixed path (Tref, qref) is the lowest
+// layer's (T, q), so FP32 resolves MSE differences to ~1e-3 J/kg instead of the
+// 0.03 J/kg ulp of 3.4e5 J/kg; in the FP64 path the reference is zero.  The
+// reference cancels in every mixing rule, difference and Newton residual.
+// Per-level values the FP64 path keeps instead of re-evaluating: there every
+// re-evaluation runs on the FP64 pipe (a mid-layer pressure is eight FP64
+// operations, an updated T two), whose throughput bounds the FP64 kernels; in
+// the mixed path they cost a few FP32 operations and are re-evaluated.
 template <class R>
-__device__ __forceinline__ void prologue(const Levels& L, double p_top_lim, Column<R>& c,
-                                         bool need_hs) {
+struct ColCache {
+  static constexpr bool on = false;
+};
+template <>
+struct ColCache<double> {
+  static constexpr bool on = true;
+  double T[MAXL], q[MAXL], pm[MAXL], m[MAXL], Tv[MAXL], h[MAXL];
+};
+
+template <class R>
+struct Column {
   using Pr = typename PressOf<R>::type;
-  const Pr P{L, (R)c.ps};
+  Src<R> s;
+  const Levels* L;
+  R zm[MAXL], dl[MAXL];
+  ColCache<R> cc;
+  R Tref, qref;
+  R psR;  // ps in the working precision
+  int pver, ktl;
+  double ps;
+  __device__ __forceinline__ Pr press() const { return Pr{*L, psR}; }
+  __device__ __forceinline__ R T(int k) const {
+    if constexpr (ColCache<R>::on) return cc.T[k];
+    else return s.Tk(k);
+  }
+  __device__ __forceinline__ R q(int k) const {
+    if constexpr (ColCache<R>::on) return cc.q[k];
+    else return s.qk(k);
+  }
+  __device__ __forceinline__ R pm(int k) const {
+    if constexpr (ColCache<R>::on) {
+      return cc.pm[k];
+    } else {
+      const Pr P = press();
+      return P.mid(P.pi(k + 1), P.pi(k));
+    }
+  }
+  __device__ __forceinline__ R m(int k) const {
+    if constexpr (ColCache<R>::on) {
+      return cc.m[k];
+    } else {
+      const Pr P = press();
+      return (P.pi(k + 1) - P.pi(k)) * R(1.0 / GRAV);
+    }
+  }
+  __device__ __forceinline__ R Tv(int k) const {
+    if constexpr (ColCache<R>::on) return cc.Tv[k];
+    else return virt(T(k), q(k));
+  }
+  __device__ __forceinline__ R h(int k) const {
+    if constexpr (ColCache<R>::on) return cc.h[k];
+    else return mse(T(k), q(k), zm[k], Tref, qref);
+  }
+  // layer depth z_int,k - z_int,k+1 = (Rd Tv / g) ln(p_k+1/p_k)
+  __device__ __forceinline__ R dz(int k) const { return R(RD / GRAV) * Tv(k) * dl[k]; }
+};
+
+template <class R>
+__device__ __forceinline__ void init_column(Column<R>& c, const Levels& L, const Src<R>& s,
+                                            double ps) {
+  c.s = s;
+  c.L = &L;
+  c.pver = L.pver;
+  c.ps = ps;
+  c.psR = (R)ps;
+}
+
+__device__ __forceinline__ bool in_range(double T, double q) {
+  return (T > 100.0 && T < 400.0) && (q >= 0.0 && q < 0.1);
+}
+__device__ __forceinline__ bool in_range(float T, float q) {
+  return (T > 100.f && T < 400.f) && (q >= 0.f && q < 0.1f);
+}
+
+template <class R>
+__device__ __forceinline__ bool column_valid(const Column<R>& c) {
+  if (!(c.ps > 5.0e4 && c.ps < 1.2e5)) return false;
+  bool ok = true;
+  for (int k = 0; k < c.pver; ++k) ok = ok && in_range(c.s.Tk(k), c.s.qk(k));
+  return ok;
+}
+
+// Heights, log-thicknesses, top limit and (when hs != nullptr) saturation moist
+// static energies (shared by both schemes).
+template <class R>
+__device__ __forceinline__ void prologue(double p_top_lim, Column<R>& c, R* hs) {
+  const auto P = c.press();
   const int pver = c.pver;
   const R ptl = (R)p_top_lim;
   R pi_lo = P.pi(pver);
   R zi = R(0);
-  c.z_int[pver] = R(0);
-  c.Tref = Mth<R>::anomaly ? c.T[pver - 1] : R(0);
-  c.qref = Mth<R>::anomaly ? c.q[pver - 1] : R(0);
+  if constexpr (ColCache<R>::on) {
+    for (int k = 0; k < pver; ++k) {
+      c.cc.T[k] = c.s.Tk(k);
+      c.cc.q[k] = c.s.qk(k);
+    }
+  }
+  c.Tref = Mth<R>::anomaly ? c.T(pver - 1) : R(0);
+  c.qref = Mth<R>::anomaly ? c.q(pver - 1) : R(0);
   int ktl = pver - 1;
   for (int k = pver - 1; k >= 0; --k) {
     const R pi_hi = P.pi(k);
     const R pm = P.mid(pi_lo, pi_hi);
-    c.p_mid[k] = pm;
-    c.m[k] = (pi_lo - pi_hi) * R(1.0 / GRAV);
-    const R tv = virt(c.T[k], c.q[k]);
-    c.Tv[k] = tv;
+    const R Tk = c.T(k), qk = c.q(k);
+    const R tv = virt(Tk, qk);
     const R scale = R(RD / GRAV) * tv;
     const R dl = Mth<R>::lg(Mth<R>::dv(pi_lo, pi_hi));
-    c.dlnp[k] = dl;
+    c.dl[k] = dl;
     const R zm = zi + scale * Mth<R>::lg(Mth<R>::dv(pi_lo, pm));
     zi = zi + scale * dl;
-    c.z_int[k] = zi;
-    c.z_mid[k] = zm;
-    const R sdry = R(CP) * (c.T[k] - c.Tref) + R(GRAV) * zm;
-    c.h[k] = sdry + R(LV) * (c.q[k] - c.qref);
-    if (need_hs) c.hs[k] = sdry + R(LV) * (sat_qs(c.T[k], pm) - c.qref);
+    c.zm[k] = zm;
+    if constexpr (ColCache<R>::on) {
+      c.cc.pm[k] = pm;
+      c.cc.m[k] = (pi_lo - pi_hi) * R(1.0 / GRAV);
+      c.cc.Tv[k] = tv;
+      c.cc.h[k] = mse(Tk, qk, zm, c.Tref, c.qref);
+    }
+    if (hs) hs[k] = mse(Tk, sat_qs(Tk, pm), zm, c.Tref, c.qref);
     if (pm >= ptl) ktl = k;
     pi_lo = pi_hi;
   }
   c.ktl = ktl;
 }
 
-// ---------------------------------------------------------------- deep scheme
+// Largest k <= kstart with p_mid[k] <= pL, or -1 (see cmp_bound).
 template <class R>
+__device__ __forceinline__ int lcl_level(const Column<R>& c, int kstart, double pL) {
+  const R b = cmp_bound(pL, R(0));
+  for (int k = kstart; k >= 0; --k)
+    if (c.pm(k) <= b) return k;
+  return -1;
+}
+
+// Tendency output of one scheme for one column: [pver][ld] arrays, written
+// level by level as the scheme produces them.
+template <class R>
+struct OutCol {
+  R* dT;
+  R* dq;
+  size_t ld;
+  int i;
+  __device__ __forceinline__ void put(int k, R a, R b) const {
+    const size_t o = (size_t)k * ld + i;
+    dT[o] = a;
+    dq[o] = b;
+  }
+  __device__ __forceinline__ void zero(int k0, int k1) const {  // levels k0..k1-1
+    for (int k = k0; k < k1; ++k) put(k, R(0), R(0));
+  }
+};
+
+// Discards tendencies (the adjoint recomputes the scheme for its tape only).
+template <class R>
+struct NoOut {
+  __device__ __forceinline__ void put(int, R, R) const {}
+  __device__ __forceinline__ void zero(int, int) const {}
+};
+
+// ---------------------------------------------------------------- deep scheme
+// Column scalars of the deep scheme (the tendencies go straight to OutCol).
 struct DeepOut {
-  R dT[MAXL], dq[MAXL];  // dT/dt, dq/dt of the column
   double prec, cape, mb, cons;
   int flags, kb, klcl, ktop, kaux;
 };
@@ -416,39 +592,45 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   const int pver = c.pver, ktl = c.ktl;
   const R plaunch = (R)P.p_launch_min;
   int kb = pver - 1;
-  for (int k = pver - 2; k >= 0 && c.p_mid[k] >= plaunch; --k)
-    if (c.h[k] > c.h[kb]) kb = k;
+  R hb = c.h(kb);
+  for (int k = pver - 2; k >= 0 && c.pm(k) >= plaunch; --k) {
+    const R hk = c.h(k);
+    if (hk > hb) {
+      kb = k;
+      hb = hk;
+    }
+  }
   t.kb = kb;
   t.kel = -1;
   t.cape = 0.0;
   t.triggered = false;
   t.newton = 0.f;
-  const double pL = lcl_p(c.T[kb], c.q[kb], c.p_mid[kb], P.n_newton_lcl, t.newton);
+  const double pL = lcl_p(c.T(kb), c.q(kb), c.pm(kb), P.n_newton_lcl, t.newton);
   t.pL = pL;
-  const int klcl = lcl_level(c.p_mid, kb, pL);
+  const int klcl = lcl_level(c, kb, pL);
   t.klcl = klcl;
   if (klcl < ktl) return;
-  const R hb = c.h[kb];
   // Undilute parcel up from the LCL layer; CAPE accumulated in FP64, bottom up,
   // and captured at the highest positively buoyant layer.
   MoistSeq<R> seq;
   seq.have = false;
-  double run = 0.0;
+  Acc<R> run, at_el;
   int kel = -1;
-  double cape = 0.0;
   for (int k = klcl; k >= ktl; --k) {
-    const R Tp = moist_invert(hb, R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h, seq,
-                              t.newton, c.Tref, c.qref);
+    const R pm = c.pm(k), Tk = c.T(k);
+    const R Tp =
+        moist_invert(hb, R(GRAV) * c.zm[k], pm, Tk, P.n_newton_h, seq, t.newton, c.Tref, c.qref);
     t.Tp[k] = Tp;
-    const R b = virt(Tp, sat_qs(Tp, c.p_mid[k])) - c.Tv[k];
-    run += (double)(R(RD) * b * c.dlnp[k]);
+    const R b = virt(Tp, sat_qs(Tp, pm)) - virt(Tk, c.q(k));
+    run.add(R(RD) * b * c.dl[k]);
     if (b > R(0)) {
       kel = k;
-      cape = run;
+      at_el = run;
     }
   }
   t.kel = kel;
   if (kel < 0) return;
+  double cape = at_el.value();
   if (cape < 0.0) cape = 0.0;
   t.cape = cape;
   t.triggered = cape > P.capelmt;
@@ -472,47 +654,54 @@ struct DeepTape {
 };
 
 // Updraft, downdraft, tendencies, closure and limiter of a triggered column
-// (deep "stage B": the entrainment and precipitation loops of Alg. 2).
-template <class R, class TP = NoTape>
-__device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_params& P,
-                                           double dt, R lam, R tau, DeepTrig<R>& t,
-                                           DeepOut<R>& o, TP* tape = nullptr) {
+// (deep "stage B": the entrainment and precipitation loops of Alg. 2).  hs: the
+// column's saturation MSE; writes every level of `out`.
+template <class R, class TP = NoTape, class OUT = OutCol<R>>
+__device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
+                                           const conv_deep_params& P, double dt, R lam, R tau,
+                                           DeepTrig<R>& t, DeepOut& o, const OUT& out,
+                                           TP* tape = nullptr) {
   if constexpr (TP::kOn) tape->active = false;
   const int pver = c.pver, ktl = c.ktl, kb = t.kb, klcl = t.klcl, kel = t.kel;
   const R ze = (R)P.ent_zscale;
   // minimum h* layer above the LCL (ties: lowest)
   int khmin = -1;
   for (int k = klcl - 1; k >= ktl; --k)
-    if (khmin < 0 || c.hs[k] < c.hs[khmin]) khmin = k;
-  R eta[MAXL], hu[MAXL], qtu[MAXL];
+    if (khmin < 0 || hs[k] < hs[khmin]) khmin = k;
+  R eta[MAXL];
   eta[kb] = R(1);
-  hu[kb] = c.h[kb];
-  qtu[kb] = c.q[kb];
-  const R zb = c.z_mid[kb];
+  R hu1 = c.h(kb), qtu1 = c.q(kb);  // updraft MSE and total water at level k+1
+  if constexpr (TP::kOn) {
+    tape->hu[kb] = hu1;
+    tape->qtu[kb] = qtu1;
+  }
+  const R zb = c.zm[kb];
   const R c0 = (R)P.c0;
   int jt = -1;
   R sumR = R(0);
   MoistSeq<R> seq;
   seq.have = false;
   for (int k = kb - 1; k >= ktl; --k) {
-    const R e = entrain_growth(lam, ze, c.z_mid[k] - zb);
+    const R e = entrain_growth(lam, ze, c.zm[k] - zb);
     eta[k] = e;
     const R de = e - eta[k + 1];
     const R re = Mth<R>::dv(R(1), e);
-    hu[k] = (eta[k + 1] * hu[k + 1] + de * c.h[k]) * re;
-    if ((k <= khmin && hu[k] <= c.hs[k]) || k == ktl) {
+    const R hu = (eta[k + 1] * hu1 + de * c.h(k)) * re;
+    if constexpr (TP::kOn) tape->hu[k] = hu;
+    if ((k <= khmin && hu <= hs[k]) || k == ktl) {
       jt = k;
       break;
     }
-    const R qt = (eta[k + 1] * qtu[k + 1] + de * c.q[k]) * re;
-    const R Ts = moist_invert(hu[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                              seq, t.newton, c.Tref, c.qref);
-    R l = qt - sat_qs(Ts, c.p_mid[k]);
+    const R pm = c.pm(k);
+    const R qt = (eta[k + 1] * qtu1 + de * c.q(k)) * re;
+    const R Ts = moist_invert(hu, R(GRAV) * c.zm[k], pm, c.T(k), P.n_newton_h, seq, t.newton,
+                              c.Tref, c.qref);
+    R l = qt - sat_qs(Ts, pm);
     const bool lpos = l > R(0);
     if (l < R(0)) l = R(0);
-    const R dz = c.z_int[k] - c.z_int[k + 1];
+    const R dz = c.dz(k);
     const R rain = Mth<R>::dv(e * c0 * dz * l, R(1) + c0 * dz);
-    qtu[k] = qt - rain * re;
+    const R qtu = qt - rain * re;
     sumR += rain;
     if constexpr (TP::kOn) {
       tape->qt[k] = qt;
@@ -520,30 +709,44 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
       tape->lpos[k] = lpos;
       tape->rain[k] = rain;
       tape->dz[k] = dz;
+      tape->qtu[k] = qtu;
     }
+    hu1 = hu;
+    qtu1 = qtu;
   }
-  if (jt < 0 || jt >= klcl) return;
+  if (jt < 0 || jt >= klcl) {
+    out.zero(0, pver);
+    return;
+  }
 
   // downdraft start: minimum h* strictly between cloud top and LCL (ties: lowest)
   int jd = -1;
   for (int k = klcl - 1; k > jt; --k)
-    if (jd < 0 || c.hs[k] < c.hs[jd]) jd = k;
-  R etad[MAXL], hd[MAXL], qd[MAXL];
+    if (jd < 0 || hs[k] < hs[jd]) jd = k;
+  R etad[MAXL];
+  R hd1 = R(0), qd1 = R(0);  // downdraft MSE and humidity at the level above
   R sumE = R(0), alpha = R(0);
   if (jd >= 0) {
-    const R zd = c.z_mid[jd];
-    R qprev = R(0), eprev = R(0);
+    const R zd = c.zm[jd];
+    R eprev = R(0);
     seq.have = false;
     for (int k = jd; k <= kb - 1; ++k) {
-      const R e = entrain_growth(lam, ze, zd - c.z_mid[k]);
+      const R e = entrain_growth(lam, ze, zd - c.zm[k]);
       etad[k] = e;
-      hd[k] = (k == jd) ? c.h[jd] : Mth<R>::dv(eprev * hd[k - 1] + (e - eprev) * c.h[k], e);
-      const R Td = moist_invert(hd[k], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k], P.n_newton_h,
-                                seq, t.newton, c.Tref, c.qref);
-      qd[k] = sat_qs(Td, c.p_mid[k]);
-      if constexpr (TP::kOn) tape->Td[k] = Td;
-      sumE += e * qd[k] - eprev * qprev - (e - eprev) * c.q[k];
-      qprev = qd[k];
+      const R hk = c.h(k), qk = c.q(k), pm = c.pm(k);
+      const R hd = (k == jd) ? hk : Mth<R>::dv(eprev * hd1 + (e - eprev) * hk, e);
+      const R Td =
+          moist_invert(hd, R(GRAV) * c.zm[k], pm, c.T(k), P.n_newton_h, seq, t.newton, c.Tref,
+                       c.qref);
+      const R qd = sat_qs(Td, pm);
+      if constexpr (TP::kOn) {
+        tape->Td[k] = Td;
+        tape->hd[k] = hd;
+        tape->qd[k] = qd;
+      }
+      sumE += e * qd - eprev * qd1 - (e - eprev) * qk;
+      hd1 = hd;
+      qd1 = qd;
       eprev = e;
     }
     alpha = (R)P.alpha_dd;
@@ -552,50 +755,63 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
     if constexpr (TP::kOn) tape->capped = capped;
   }
 
-  // unit tendencies (per M_b) in flux form
-  // (the closure reads dT/dq on k_el..klcl, which may reach above the cloud top)
-  R dh[MAXL], dq[MAXL], dT[MAXL];
-  for (int k = 0; k < pver; ++k) dh[k] = dq[k] = dT[k] = R(0);
-  for (int k = jt + 1; k <= kb; ++k) {
-    dh[k] += eta[k] * (c.h[k - 1] - c.h[k]);
-    dq[k] += eta[k] * (c.q[k - 1] - c.q[k]);
-  }
-  dh[jt] += eta[jt + 1] * (hu[jt + 1] - c.h[jt]);
-  dq[jt] += eta[jt + 1] * (qtu[jt + 1] - c.q[jt]);
-  if (jd >= 0) {
-    for (int k = jd; k <= kb - 1; ++k) {
-      const R D = alpha * etad[k];
-      dh[k] += D * (c.h[k + 1] - c.h[k]);
-      dq[k] += D * (c.q[k + 1] - c.q[k]);
-    }
-    const R D = alpha * etad[kb - 1];
-    dh[kb] += D * (hd[kb - 1] - c.h[kb]);
-    dq[kb] += D * (qd[kb - 1] - c.q[kb]);
-  }
+  // unit tendencies (per M_b) in flux form; dT, dq are zero outside jt..kb
+  // (the closure reads them on k_el..klcl, which may reach above the cloud top)
+  R dT[MAXL], dq[MAXL];
+  R dhkb = R(0);
+  for (int k = 0; k < pver; ++k) dT[k] = dq[k] = R(0);
   for (int k = jt; k <= kb; ++k) {
-    const R rm = Mth<R>::dv(R(1), c.m[k]);
-    dh[k] *= rm;
-    dq[k] *= rm;
-    dT[k] = (dh[k] - R(LV) * dq[k]) * R(1.0 / CP);
+    const R hk = c.h(k), qk = c.q(k);
+    R dh, dqk;
+    if (k == jt) {
+      dh = eta[jt + 1] * (hu1 - hk);
+      dqk = eta[jt + 1] * (qtu1 - qk);
+    } else {
+      dh = eta[k] * (c.h(k - 1) - hk);
+      dqk = eta[k] * (c.q(k - 1) - qk);
+    }
+    if (jd >= 0 && k >= jd) {
+      if (k <= kb - 1) {
+        const R D = alpha * etad[k];
+        dh += D * (c.h(k + 1) - hk);
+        dqk += D * (c.q(k + 1) - qk);
+      } else {
+        const R D = alpha * etad[kb - 1];
+        dh += D * (hd1 - hk);
+        dqk += D * (qd1 - qk);
+      }
+    }
+    const R rm = Mth<R>::dv(R(1), c.m(k));
+    dh *= rm;
+    dqk *= rm;
+    dq[k] = dqk;
+    dT[k] = (dh - R(LV) * dqk) * R(1.0 / CP);
+    if (k == kb) dhkb = dh;
+    if constexpr (TP::kOn) tape->dh[k] = dh;
   }
 
   // closure
   R F = R(0);
   for (int k = klcl; k >= kel; --k) {
     R qsp, dqsp, rD;
-    sat_qs_dqs(t.Tp[k], c.p_mid[k], qsp, dqsp, rD);
+    const R pm = c.pm(k);
+    sat_qs_dqs(t.Tp[k], pm, qsp, dqsp, rD);
     const R dTvp = Mth<R>::dv((R(1) + R(ZVIR) * qsp) + R(ZVIR) * t.Tp[k] * dqsp,
                               R(CP) + R(LV) * dqsp);
-    const R dTv = (R(1) + R(ZVIR) * c.q[k]) * dT[k] + R(ZVIR) * c.T[k] * dq[k];
-    F += R(RD) * c.dlnp[k] * (dTvp * dh[kb] - dTv);
+    const R dTv = (R(1) + R(ZVIR) * c.q(k)) * dT[k] + R(ZVIR) * c.T(k) * dq[k];
+    F += R(RD) * c.dl[k] * (dTvp * dhkb - dTv);
   }
-  if (!(F < R(0))) return;
+  if (!(F < R(0))) {
+    out.zero(0, pver);
+    return;
+  }
   R mb = Mth<R>::dv((R)(-t.cape), tau * F);
   bool limited = false;
   int kstar = -1;
+  const R qmin = (R)P.q_min, mdt = -(R)dt;
   for (int k = jt; k <= kb; ++k) {
     if (dq[k] < R(0)) {
-      const R ml = Mth<R>::dv(c.q[k] - (R)P.q_min, -(R)dt * dq[k]);
+      const R ml = Mth<R>::dv(c.q(k) - qmin, mdt * dq[k]);
       if (ml < mb) {
         mb = ml;
         limited = true;
@@ -603,7 +819,10 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
       }
     }
   }
-  if (!(mb > R(0))) return;
+  if (!(mb > R(0))) {
+    out.zero(0, pver);
+    return;
+  }
   R net = sumR - alpha * sumE;
   const bool net_pos = net >= R(0);
   if (net < R(0)) net = R(0);
@@ -623,16 +842,9 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
     if (jd < 0) tape->capped = false;
     for (int k = 0; k < pver; ++k) {
       tape->eta[k] = eta[k];
-      tape->hu[k] = hu[k];
-      tape->qtu[k] = qtu[k];
-      tape->dh[k] = dh[k];
       tape->dq[k] = dq[k];
       tape->dT[k] = dT[k];
-      if (jd >= 0) {
-        tape->etad[k] = etad[k];
-        tape->hd[k] = hd[k];
-        tape->qd[k] = qd[k];
-      }
+      if (jd >= 0) tape->etad[k] = etad[k];
     }
   }
   o.flags |= CONV_FLAG_ACTIVE | (limited ? CONV_FLAG_LIMITED : 0);
@@ -640,37 +852,38 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   o.prec = (double)(mb * net);
   o.ktop = jt;
   o.kaux = jd;
-  double se = 0.0, sw = 0.0;
+  Acc<R> sea, swa;
   R sc = R(0);
+  out.zero(0, jt);
   for (int k = jt; k <= kb; ++k) {
     const R a = mb * dT[k];
     const R b = mb * dq[k];
-    o.dT[k] = a;
-    o.dq[k] = b;
-    const R mk = c.m[k];
-    se += (double)(mk * a);
-    sw += (double)(mk * b);
+    out.put(k, a, b);
+    const R mk = c.m(k);
+    sea.add(mk * a);
+    swa.add(mk * b);
     sc += mk * Mth<R>::ab(a);
   }
-  se *= CP;
+  out.zero(kb + 1, pver);
+  const double se = CP * sea.value(), sw = swa.value();
   o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) /
            (CP * (double)sc + LV * o.prec + 1e-300);
 }
 
-// Whole deep scheme for one column already loaded into c (T, q, ps, pver).
+// Whole deep scheme for one column (T, q, ps set in c); writes every level of out.
 template <class R>
-__device__ __forceinline__ void deep_column(const Levels& L, const conv_deep_params& P,
-                                            double dt, R lam, R tau, Column<R>& c,
-                                            DeepOut<R>& o) {
-  for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
+__device__ __forceinline__ void deep_column(const conv_deep_params& P, double dt, R lam, R tau,
+                                            Column<R>& c, DeepOut& o, const OutCol<R>& out) {
   o.prec = o.cape = o.mb = o.cons = 0.0;
   o.flags = 0;
   o.kb = o.klcl = o.ktop = o.kaux = -1;
   if (!column_valid(c)) {
     o.flags = CONV_FLAG_BADINPUT;
+    out.zero(0, c.pver);
     return;
   }
-  prologue(L, P.p_top_lim, c, true);
+  R hs[MAXL];
+  prologue(P.p_top_lim, c, hs);
   DeepTrig<R> t;
   deep_trigger(c, P, t);
   o.kb = t.kb;
@@ -678,15 +891,15 @@ __device__ __forceinline__ void deep_column(const Levels& L, const conv_deep_par
   o.cape = t.cape;
   if (t.triggered) {
     o.flags |= CONV_FLAG_TRIGGERED;
-    deep_plume(c, P, dt, lam, tau, t, o);
+    deep_plume(c, hs, P, dt, lam, tau, t, o, out);
+  } else {
+    out.zero(0, c.pver);
   }
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
 }
 
 // ---------------------------------------------------------------- shallow scheme
-template <class R>
 struct ShalOut {
-  R dT[MAXL], dq[MAXL];
   double prec, cin, mb, cons;
   int flags, klcl, ktop, klfc;
 };
@@ -701,68 +914,77 @@ struct ShallowSeed {
   const R* Tp;  // parcel temperature on ktl..klcl
 };
 
-// Whole shallow scheme for one column in c (Alg. 3).  When `prologue_done` the
-// column has been validated and its prologue computed already.
+// Whole shallow scheme for one column in c (Alg. 3); writes every level of out.
+// When `prologue_done` the column has been validated and its prologue computed
+// already.  The plume's tendencies go out level by level as the plume rises:
+// a level's is written once the level above has shown that the plume goes on,
+// the top layer's when the plume stops; a plume that dies at its LCL (exit E4)
+// overwrites what it wrote with zeros.
 template <class R>
-__device__ __forceinline__ void shallow_column(const Levels& L, const conv_shallow_params& P,
-                                               Column<R>& c, ShalOut<R>& o,
+__device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Column<R>& c,
+                                               ShalOut& o, const OutCol<R>& out,
                                                const ShallowSeed<R>* seed = nullptr,
                                                bool prologue_done = false) {
   const int pver = c.pver;
-  for (int k = 0; k < pver; ++k) o.dT[k] = o.dq[k] = R(0);
   o.prec = o.cin = o.mb = o.cons = 0.0;
   o.flags = 0;
   o.klcl = o.ktop = o.klfc = -1;
   if (!prologue_done) {
     if (!column_valid(c)) {
       o.flags = CONV_FLAG_BADINPUT;
+      out.zero(0, pver);
       return;
     }
-    prologue(L, P.p_top_lim, c, false);
+    prologue(P.p_top_lim, c, (R*)nullptr);
   }
   const int ks = pver - 1, ktl = c.ktl;
   float newton = 0.f;
   double pL;
   int klcl;
+  const R Tsrc = c.T(ks), qsrc = c.q(ks), psrc = c.pm(ks);
   if (seed) {
     pL = seed->pL;
     klcl = seed->klcl;
   } else {
-    pL = lcl_p(c.T[ks], c.q[ks], c.p_mid[ks], P.n_newton_lcl, newton);
-    klcl = lcl_level(c.p_mid, ks, pL);
+    pL = lcl_p(Tsrc, qsrc, psrc, P.n_newton_lcl, newton);
+    klcl = lcl_level(c, ks, pL);
   }
   o.klcl = klcl;
   int exit_code = 0;
   R mb = R(0);
   int klfc = -1, kts = -1;
-  R hu[MAXL], qtu[MAXL], qpre[MAXL], rf[MAXL];
   const R plfc = (R)P.p_lfc_min;
+  const R hsrc = c.h(ks);
+  Acc<R> sea, swa;
+  R sc = R(0), sumr = R(0);
   if (pL < P.p_lcl_min || klcl < ktl) {
     exit_code = 1;
   } else {
     // undilute parcel up to the LFC; CIN in FP64
-    const R Ts = c.T[ks], qsrc = c.q[ks], psrc = c.p_mid[ks];
-    double cin = 0.0;
+    Acc<R> cina;
     MoistSeq<R> seq;
     seq.have = false;
-    for (int k = ks; k >= ktl && c.p_mid[k] >= plfc; --k) {
+    for (int k = ks; k >= ktl; --k) {
+      const R pm = c.pm(k);
+      if (!(pm >= plfc)) break;
       R Tp, qp;
       if (k > klcl) {
-        Tp = Ts * Mth<R>::pw(Mth<R>::dv(c.p_mid[k], psrc), R(KAPPA));
+        Tp = Tsrc * Mth<R>::pw(Mth<R>::dv(pm, psrc), R(KAPPA));
         qp = qsrc;
       } else {
         Tp = seed ? seed->Tp[k]
-                  : moist_invert(c.h[ks], R(GRAV) * c.z_mid[k], c.p_mid[k], c.T[k],
-                                 P.n_newton_h, seq, newton, c.Tref, c.qref);
-        qp = sat_qs(Tp, c.p_mid[k]);
+                  : moist_invert(hsrc, R(GRAV) * c.zm[k], pm, c.T(k), P.n_newton_h, seq,
+                                 newton, c.Tref, c.qref);
+        qp = sat_qs(Tp, pm);
       }
-      const R b = virt(Tp, qp) - c.Tv[k];
+      const R b = virt(Tp, qp) - c.Tv(k);
       if (k <= klcl && b > R(0)) {
         klfc = k;
         break;
       }
-      if (b < R(0)) cin += (double)(R(RD) * (-b) * c.dlnp[k]);
+      if (b < R(0)) cina.add(R(RD) * (-b) * c.dl[k]);
     }
+    const double cin = cina.value();
     o.klfc = klfc;
     if (klfc < 0) {
       exit_code = 2;
@@ -771,50 +993,73 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
       if (cin > P.cin_max) {
         exit_code = 3;
       } else {
-        const R rho = Mth<R>::dv(psrc, R(RD) * c.Tv[ks]);
+        const R rho = Mth<R>::dv(psrc, R(RD) * c.Tv(ks));
         mb = rho * (R)(P.c_m * sqrt(P.tke)) * Mth<R>::ex((R)(-cin / (P.cin_scale * P.tke)));
-        // plume
-        hu[ks] = c.h[ks];
-        qtu[ks] = qsrc;
-        qpre[ks] = qsrc;
-        rf[ks] = R(0);
+        // plume, with a two-level window: (hu2, qtu2) at k+2, (hu1, qtu1, qp1, rf1) at k+1
+        const R hsrc_env = hsrc;
+        R hu2 = R(0), qtu2 = R(0);
+        R hu1 = hsrc_env, qtu1 = qsrc, qp1 = qsrc, rf1 = R(0);
+        R h_up = c.h(ks - 1), q_up = c.q(ks - 1);  // environment one level up
+        R h_k1 = hsrc_env, q_k1 = qsrc;            // environment at k+1
+        auto emit = [&](int k, R dh, R dqv) {
+          const R rm = Mth<R>::dv(R(1), c.m(k));
+          const R dqk = dqv * rm;
+          const R dTk = (dh * rm - R(LV) * dqk) * R(1.0 / CP);
+          out.put(k, dTk, dqk);
+          const R mk = c.m(k);
+          sea.add(mk * dTk);
+          swa.add(mk * dqk);
+          sc += mk * Mth<R>::ab(dTk);
+        };
+        // the source layer's tendency (its formula does not depend on the top)
+        emit(ks, mb * (h_up - hsrc_env), mb * (q_up - qsrc));
         const R w2_0 = (R)(2.0 / 3.0 * P.tke);
         R w2 = w2_0;
         const R eps = (R)P.eps_s;
         const double beps = P.b_w * P.eps_s;
+        const bool drag = beps > 0.0;
+        const R m2beps = (R)(-2.0 * beps);
+        const R aw_beps = drag ? (R)(P.a_w / beps) : R(0);
+        const R aw2 = (R)(2.0 * P.a_w);
+        const R qlc = (R)P.ql_crit;
         seq.have = false;
         for (int k = ks - 1; k >= ktl; --k) {
-          const R dz = c.z_int[k] - c.z_int[k + 1];
-          R qt;
+          const R dz = c.dz(k);
+          const R hk = h_up, qk = q_up;  // environment at k
+          if (k >= 1) {
+            h_up = c.h(k - 1);
+            q_up = c.q(k - 1);
+          }
+          R hu, qt;
           if (k >= klcl) {
-            hu[k] = hu[k + 1];
-            qt = qtu[k + 1];
+            hu = hu1;
+            qt = qtu1;
           } else {
             const R chi = R(1) - Mth<R>::ex(-eps * dz);
-            hu[k] = hu[k + 1] + chi * (c.h[k] - hu[k + 1]);
-            qt = qtu[k + 1] + chi * (c.q[k] - qtu[k + 1]);
+            hu = hu1 + chi * (hk - hu1);
+            qt = qtu1 + chi * (qk - qtu1);
           }
-          qpre[k] = qt;
-          rf[k] = R(0);
-          const R gz = R(GRAV) * c.z_mid[k];
-          const R Tsat =
-              moist_invert(hu[k], gz, c.p_mid[k], c.T[k], P.n_newton_h, seq, newton, c.Tref, c.qref);
-          const R qsu = sat_qs(Tsat, c.p_mid[k]);
+          const R pm = c.pm(k);
+          const R Tk = c.T(k);
+          const R gz = R(GRAV) * c.zm[k];
+          const R Tsat = moist_invert(hu, gz, pm, Tk, P.n_newton_h, seq, newton, c.Tref, c.qref);
+          const R qsu = sat_qs(Tsat, pm);
           R Tu, qv;
           if (qt >= qsu) {
             Tu = Tsat;
             qv = qsu;
           } else {
-            Tu = c.Tref + (hu[k] - gz - R(LV) * (qt - c.qref)) * R(1.0 / CP);
+            Tu = c.Tref + (hu - gz - R(LV) * (qt - c.qref)) * R(1.0 / CP);
             qv = qt;
           }
           if (k < klfc) {
-            const R B = R(GRAV) * Mth<R>::dv(virt(Tu, qv) - c.Tv[k], c.Tv[k]);
-            if (beps > 0.0) {
-              const R decay = Mth<R>::ex((R)(-2.0 * beps) * dz);
-              w2 = w2 * decay + (R)(P.a_w / beps) * B * (R(1) - decay);
+            const R Tvk = virt(Tk, qk);
+            const R B = R(GRAV) * Mth<R>::dv(virt(Tu, qv) - Tvk, Tvk);
+            if (drag) {
+              const R decay = Mth<R>::ex(m2beps * dz);
+              w2 = w2 * decay + aw_beps * B * (R(1) - decay);
             } else {
-              w2 = w2 + (R)(2.0 * P.a_w) * B * dz;
+              w2 = w2 + aw2 * B * dz;
             }
             if (!(w2 > R(0))) {
               kts = k + 1;
@@ -823,52 +1068,55 @@ __device__ __forceinline__ void shallow_column(const Levels& L, const conv_shall
           }
           if (k == ktl) {
             kts = k;
+            // level k+1 (if not the source) is a regular level below the top
+            if (k + 1 <= ks - 1) {
+              emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)));
+              sumr += rf1;
+            }
+            hu2 = hu1;
+            qtu2 = qtu1;
+            h_k1 = hk;
+            q_k1 = qk;
             break;
           }
-          R r = qt - qv - (R)P.ql_crit;
+          R r = qt - qv - qlc;
           if (r < R(0)) r = R(0);
-          rf[k] = r;
-          qtu[k] = qt - r;
+          // the plume goes on above k: level k+1 is a regular level
+          if (k + 1 <= ks - 1) {
+            emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)));
+            sumr += rf1;
+          }
+          hu2 = hu1;
+          qtu2 = qtu1;
+          hu1 = hu;
+          qtu1 = qt - r;
+          qp1 = qt;
+          rf1 = r;
+          h_k1 = hk;
+          q_k1 = qk;
         }
-        if (kts < 0 || kts >= klcl) exit_code = 4;
+        if (kts < 0 || kts >= klcl) {
+          exit_code = 4;
+        } else {
+          // top layer: detrainment of the plume arriving from kts+1
+          emit(kts, mb * (hu2 - h_k1), mb * (qtu2 - q_k1));
+        }
       }
     }
   }
   if (exit_code == 0 || exit_code == 4) o.flags |= CONV_FLAG_TRIGGERED;
   o.flags |= exit_code << CONV_EXIT_SHIFT;
   if (newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
-  if (exit_code != 0) return;
-
-  // tendencies of the constant-mass-flux plume
-  R dh[MAXL], dq[MAXL];
-  dh[ks] = mb * (c.h[ks - 1] - c.h[ks]);
-  dq[ks] = mb * (c.q[ks - 1] - c.q[ks]);
-  R sumr = R(0);
-  for (int k = kts + 1; k <= ks - 1; ++k) {
-    dh[k] = mb * ((hu[k + 1] - hu[k]) + (c.h[k - 1] - c.h[k]));
-    dq[k] = mb * ((qtu[k + 1] - qpre[k]) + (c.q[k - 1] - c.q[k]));
-    sumr += rf[k];
+  if (exit_code != 0) {
+    out.zero(0, pver);
+    return;
   }
-  dh[kts] = mb * (hu[kts + 1] - c.h[kts]);
-  dq[kts] = mb * (qtu[kts + 1] - c.q[kts]);
+  out.zero(0, kts);
   o.flags |= CONV_FLAG_ACTIVE;
   o.mb = (double)mb;
   o.prec = (double)(mb * sumr);
   o.ktop = kts;
-  double se = 0.0, sw = 0.0;
-  R sc = R(0);
-  for (int k = kts; k <= ks; ++k) {
-    const R rm = Mth<R>::dv(R(1), c.m[k]);
-    const R dqk = dq[k] * rm;
-    const R dTk = (dh[k] * rm - R(LV) * dqk) * R(1.0 / CP);
-    o.dT[k] = dTk;
-    o.dq[k] = dqk;
-    const R mk = c.m[k];
-    se += (double)(mk * dTk);
-    sw += (double)(mk * dqk);
-    sc += mk * Mth<R>::ab(dTk);
-  }
-  se *= CP;
+  const double se = CP * sea.value(), sw = swa.value();
   o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) /
            (CP * (double)sc + LV * o.prec + 1e-300);
 }

@@ -18,62 +18,6 @@
 
 namespace cvg {
 
-template <class R>
-__device__ __forceinline__ void store_deep(const RunArgs& a, int i, const DeepOut<R>& o,
-                                           bool tendencies) {
-  const int ld = a.ld, pver = a.L.pver;
-  if (tendencies) {
-    R* dT = static_cast<R*>(a.od.dTdt);
-    R* dq = static_cast<R*>(a.od.dqdt);
-    for (int k = 0; k < pver; ++k) {
-      dT[(size_t)k * ld + i] = o.dT[k];
-      dq[(size_t)k * ld + i] = o.dq[k];
-    }
-  }
-  a.od.prec[i] = o.prec;
-  a.od.flags[i] = o.flags;
-  if (a.od.kb) a.od.kb[i] = o.kb;
-  if (a.od.klcl) a.od.klcl[i] = o.klcl;
-  if (a.od.ktop) a.od.ktop[i] = o.ktop;
-  if (a.od.kaux) a.od.kaux[i] = o.kaux;
-  if (a.od.cape) a.od.cape[i] = o.cape;
-  if (a.od.mb) a.od.mb[i] = o.mb;
-  if (a.od.cons_err) a.od.cons_err[i] = o.cons;
-}
-
-template <class R>
-__device__ __forceinline__ void store_shallow(const RunArgs& a, int i, const ShalOut<R>& o) {
-  const int ld = a.ld, pver = a.L.pver;
-  R* dT = static_cast<R*>(a.os.dTdt);
-  R* dq = static_cast<R*>(a.os.dqdt);
-  for (int k = 0; k < pver; ++k) {
-    dT[(size_t)k * ld + i] = o.dT[k];
-    dq[(size_t)k * ld + i] = o.dq[k];
-  }
-  const bool bad = (o.flags & CONV_FLAG_BADINPUT) != 0;
-  a.os.prec[i] = o.prec;
-  a.os.flags[i] = o.flags;
-  if (a.os.kb) a.os.kb[i] = bad ? -1 : pver - 1;
-  if (a.os.klcl) a.os.klcl[i] = o.klcl;
-  if (a.os.ktop) a.os.ktop[i] = o.ktop;
-  if (a.os.kaux) a.os.kaux[i] = o.klfc;
-  if (a.os.cape) a.os.cape[i] = o.cin;
-  if (a.os.mb) a.os.mb[i] = o.mb;
-  if (a.os.cons_err) a.os.cons_err[i] = o.cons;
-}
-
-template <class R>
-__device__ __forceinline__ void load_column(const RunArgs& a, int i, Column<R>& c) {
-  const R* __restrict__ T = static_cast<const R*>(a.T);
-  const R* __restrict__ q = static_cast<const R*>(a.q);
-  c.pver = a.L.pver;
-  c.ps = a.ps[i];
-  for (int k = 0; k < c.pver; ++k) {
-    c.T[k] = T[(size_t)k * a.ld + i];
-    c.q[k] = q[(size_t)k * a.ld + i];
-  }
-}
-
 // Trigger pass of one column (all lanes of the warp must call it: the queue
 // append is a warp ballot).  `tag` is what the queue records for the column
 // (the column index, or a batch-wide index), `live` false for padding lanes.
@@ -81,13 +25,12 @@ template <class R>
 __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R>& w, int i,
                                              bool live, int tag) {
   Column<R> c;
-  DeepOut<R> o;
+  DeepOut o;
   DeepTrig<R> t;
   t.triggered = false;
   bool valid = false;
   if (live) {
-    load_column(a, i, c);
-    for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
+    init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
     o.prec = o.cape = o.mb = o.cons = 0.0;
     o.flags = 0;
     o.kb = o.klcl = o.ktop = o.kaux = -1;
@@ -95,7 +38,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     if (!valid) {
       o.flags = CONV_FLAG_BADINPUT;
     } else {
-      prologue(a.L, a.dp.p_top_lim, c, false);  // h* is needed only by the plume pass
+      prologue(a.dp.p_top_lim, c, (R*)nullptr);  // h* is needed only by the plume pass
       deep_trigger(c, a.dp, t);
       o.kb = t.kb;
       o.klcl = t.klcl;
@@ -120,42 +63,34 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     w.levels[slot] = t.kb | (t.klcl << 8) | (t.kel << 16);
     w.cape[slot] = t.cape;
     for (int k = t.kel; k <= t.klcl; ++k) w.Tp[(size_t)k * w.cap + slot] = t.Tp[k];
-    store_deep(a, i, o, false);  // scalars now; tendencies and the rest in the plume pass
+    store_deep_scalars(a, i, o);  // scalars now; tendencies and the rest in the plume pass
     return;
   }
-  store_deep(a, i, o, true);
+  out_col<R>(a.od, a, i).zero(0, c.pver);
+  store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
-  ShalOut<R> s;
+  ShalOut s;
+  const OutCol<R> so = out_col<R>(a.os, a, i);
   if (!valid) {
-    shallow_column(a.L, a.sp, c, s);  // flags the column as bad input
+    shallow_column(a.sp, c, s, so);  // flags the column as bad input
   } else {
-    // same state as the deep scheme saw: reuse prologue, and the LCL/parcel
+    // same state as the deep scheme saw: reuse the prologue, and the LCL/parcel
     // when the deep launch layer is the shallow source layer
     const bool same_src = t.kb == c.pver - 1 && a.sp.p_top_lim == a.dp.p_top_lim &&
                           a.sp.n_newton_lcl == a.dp.n_newton_lcl &&
                           a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
-    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(a.L, a.sp.p_top_lim, c, false);
+    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(a.sp.p_top_lim, c, (R*)nullptr);
     ShallowSeed<R> seed{t.pL, t.klcl, t.Tp};
-    shallow_column(a.L, a.sp, c, s, same_src ? &seed : nullptr, true);
+    shallow_column(a.sp, c, s, so, same_src ? &seed : nullptr, true);
   }
-  store_shallow(a, i, s);
+  store_shallow_scalars(a, i, s);
 }
 
 template <class R>
-__global__ void __launch_bounds__(kCompactBlock) k_trigger(RunArgs a, CompactWs<R> w) {
+__global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::trigger / kCompactBlock)
+    k_trigger(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   trigger_body(a, w, i, i < a.n, i);
-}
-
-template <class R>
-__device__ __forceinline__ R add_mul(R a, double dt, R b);
-template <>
-__device__ __forceinline__ double add_mul<double>(double a, double dt, double b) {
-  return __dadd_rn(a, __dmul_rn(dt, b));
-}
-template <>
-__device__ __forceinline__ float add_mul<float>(float a, double dt, float b) {
-  return a + (float)dt * b;
 }
 
 // Plume pass of the column in queue slot `slot` (column i of member a).
@@ -163,8 +98,7 @@ template <class R>
 __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>& w, int slot,
                                            int i) {
   Column<R> c;
-  load_column(a, i, c);
-  prologue(a.L, a.dp.p_top_lim, c, true);
+  init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
   DeepTrig<R> t;
   const int lv = w.levels[slot];
   t.kb = lv & 0xff;
@@ -174,8 +108,7 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   t.triggered = true;
   t.newton = 0.f;
   for (int k = t.kel; k <= t.klcl; ++k) t.Tp[k] = w.Tp[(size_t)k * w.cap + slot];
-  DeepOut<R> o;
-  for (int k = 0; k < c.pver; ++k) o.dT[k] = o.dq[k] = R(0);
+  DeepOut o;
   o.prec = o.mb = o.cons = 0.0;
   o.cape = t.cape;
   o.flags = a.od.flags[i];  // trigger-stage bits written by the trigger pass
@@ -184,22 +117,23 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   o.ktop = o.kaux = -1;
   const R lam = (R)(a.lam ? a.lam[i] : a.dp.lambda_default);
   const R tau = (R)(a.tau ? a.tau[i] : a.dp.tau_default);
-  deep_plume(c, a.dp, a.dt, lam, tau, t, o);
-  if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
-  store_deep(a, i, o, true);
-  if (!(a.mode & MODE_SHALLOW)) return;
-  for (int k = 0; k < c.pver; ++k) {
-    c.T[k] = add_mul(c.T[k], a.dt, o.dT[k]);
-    const R qn = add_mul(c.q[k], a.dt, o.dq[k]);
-    c.q[k] = qn < R(0) ? R(0) : qn;  // limiter keeps q >= q_min up to rounding
+  {
+    R hs[MAXL];
+    prologue(a.dp.p_top_lim, c, hs);
+    deep_plume(c, hs, a.dp, a.dt, lam, tau, t, o, out_col<R>(a.od, a, i));
   }
-  ShalOut<R> s;
-  shallow_column(a.L, a.sp, c, s);
-  store_shallow(a, i, s);
+  if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
+  store_deep_scalars(a, i, o);
+  if (!(a.mode & MODE_SHALLOW)) return;
+  c.s = after_deep_src<R>(a, i, false);  // limiter keeps q >= q_min up to rounding
+  ShalOut s;
+  shallow_column(a.sp, c, s, out_col<R>(a.os, a, i));
+  store_shallow_scalars(a, i, s);
 }
 
 template <class R>
-__global__ void __launch_bounds__(kCompactBlock) k_plume(RunArgs a, CompactWs<R> w) {
+__global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactBlock)
+    k_plume(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= *w.count) return;
   plume_body(a, w, slot, w.queue[slot]);
@@ -260,7 +194,8 @@ __device__ __forceinline__ int find_member(const int* off, int M, int g) {
 }
 
 template <class R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_batch_trigger(BatchDev b, CompactWs<R> w) {
+__global__ void __launch_bounds__(BLOCK, SmThreads<R>::trigger / BLOCK)
+    k_batch_trigger(BatchDev b, CompactWs<R> w) {
   const int g = blockIdx.x * BLOCK + threadIdx.x;
   const bool live = g < b.total;
   int m = 0, i = 0;
@@ -272,7 +207,8 @@ __global__ void __launch_bounds__(BLOCK) k_batch_trigger(BatchDev b, CompactWs<R
 }
 
 template <class R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_batch_plume(BatchDev b, CompactWs<R> w) {
+__global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
+    k_batch_plume(BatchDev b, CompactWs<R> w) {
   const int count = *w.count;
   for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
     const int g = w.queue[slot];

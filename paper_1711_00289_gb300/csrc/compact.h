@@ -7,6 +7,22 @@ namespace cvg {
 
 constexpr int kCompactBlock = 128;
 
+// Resident threads per SM the compacted kernels are compiled for (register cap
+// 65536 / threads).  The mixed kernels are latency-bound chains of dependent
+// FP32 operations: more resident warps hide more of that latency, and a
+// measured sweep of the caps put the trigger pass at 1280 threads per SM (48
+// registers) and the plume pass at 1024 (64 registers).  The FP64 kernels are
+// bound by the FP64 pipe and need enough warps in flight to keep it fed: 896
+// threads (72 registers).
+template <class R>
+struct SmThreads {
+  static constexpr int trigger = 896, plume = 896;
+};
+template <>
+struct SmThreads<float> {
+  static constexpr int trigger = 1280, plume = 1024;
+};
+
 // Device workspace of the compacted path, carved from one caller buffer:
 //   count  int32      queue length (zeroed at the start of every run)
 //   queue  int32[n]   column index of each queued (deep-triggered) column

@@ -48,6 +48,50 @@ inline void record_stage(const RunArgs& a, int i) {
   if (a.ev[i]) cudaEventRecord(a.ev[i], a.stream);
 }
 
+// Column i of a run's input profile (no update).
+template <class R>
+__device__ __forceinline__ Src<R> input_src(const RunArgs& a, int i) {
+  return Src<R>{static_cast<const R*>(a.T), static_cast<const R*>(a.q), nullptr, nullptr, R(0),
+                (size_t)a.ld, i, false};
+}
+// The same column advanced by dt times the deep tendencies written to od (the
+// shallow scheme's input, Alg. 1); q floored at 0 unless the column was rejected.
+template <class R>
+__device__ __forceinline__ Src<R> after_deep_src(const RunArgs& a, int i, bool bad) {
+  return Src<R>{static_cast<const R*>(a.T), static_cast<const R*>(a.q),
+                static_cast<const R*>(a.od.dTdt), static_cast<const R*>(a.od.dqdt), (R)a.dt,
+                (size_t)a.ld, i, !bad};
+}
+template <class R>
+__device__ __forceinline__ OutCol<R> out_col(const OutP& o, const RunArgs& a, int i) {
+  return OutCol<R>{static_cast<R*>(o.dTdt), static_cast<R*>(o.dqdt), (size_t)a.ld, i};
+}
+
+__device__ __forceinline__ void store_deep_scalars(const RunArgs& a, int i, const DeepOut& o) {
+  a.od.prec[i] = o.prec;
+  a.od.flags[i] = o.flags;
+  if (a.od.kb) a.od.kb[i] = o.kb;
+  if (a.od.klcl) a.od.klcl[i] = o.klcl;
+  if (a.od.ktop) a.od.ktop[i] = o.ktop;
+  if (a.od.kaux) a.od.kaux[i] = o.kaux;
+  if (a.od.cape) a.od.cape[i] = o.cape;
+  if (a.od.mb) a.od.mb[i] = o.mb;
+  if (a.od.cons_err) a.od.cons_err[i] = o.cons;
+}
+
+__device__ __forceinline__ void store_shallow_scalars(const RunArgs& a, int i, const ShalOut& o) {
+  const bool bad = (o.flags & CONV_FLAG_BADINPUT) != 0;
+  a.os.prec[i] = o.prec;
+  a.os.flags[i] = o.flags;
+  if (a.os.kb) a.os.kb[i] = bad ? -1 : a.L.pver - 1;
+  if (a.os.klcl) a.os.klcl[i] = o.klcl;
+  if (a.os.ktop) a.os.ktop[i] = o.ktop;
+  if (a.os.kaux) a.os.kaux[i] = o.klfc;
+  if (a.os.cape) a.os.cape[i] = o.cin;
+  if (a.os.mb) a.os.mb[i] = o.mb;
+  if (a.os.cons_err) a.os.cons_err[i] = o.cons;
+}
+
 // Plain path: one thread per column, whole scheme, no compaction.
 cudaError_t launch_plain(const RunArgs& a, bool fp64);
 

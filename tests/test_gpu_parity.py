@@ -176,16 +176,17 @@ def test_full_resolution_grid(oracle, frac):
         assert r["prec_max"] <= 1e-3, f"{tag} {r}"
 
 
-def test_compact_fp64_equals_plain_fp64_bitwise():
-    """The compacted FP64 path runs the same arithmetic per column as the plain
-    kernel (the shallow scheme reuses the deep LCL and parcel only when they are
-    the same computation), so every output is bit-identical."""
+def test_compact_fp64_matches_plain_fp64():
+    """The compacted FP64 path runs the same column code as the plain kernel (the
+    shallow scheme reuses the deep LCL and parcel only when they are the same
+    computation): decisions and integer outputs are identical, and real outputs
+    agree to rounding -- the two kernels are compiled separately, so the
+    compiler may contract a multiply-add differently in each."""
     g = S.latlon_grid()
     a = run_gpu(g, "fp64", "plain")
     b = run_gpu(g, "fp64", "compact")
-    for x, y in zip(a, b):
-        for k in x:
-            assert np.array_equal(x[k], y[k], equal_nan=True), k
+    for x, y, tag in zip(a, b, ("deep", "shallow")):
+        assert_fp64_parity(y, x, tol=1e-12, what=f"compact vs plain {tag}")
 
 
 def test_workspace_errors():
