@@ -143,14 +143,17 @@ def t_ops(c, r, pfx):
             + c["exp"] / r[pfx + "exp"] + c["log"] / r[pfx + "log"] + c["pow"] / r[pfx + "pow"])
 
 
-# FP64 work of one LCL solve of the mixed design (the FP64 Newton correction:
-# residual, relative humidity and LCL pressure): 1 log, 1 exp, 4 div, 27 FMA.
-# The CAPE, CIN and conservation sums keep FP64 accuracy as compensated FP32
-# sums; their terms are FP32 work, already in the oracle's operation counts
-# (one add per term; the compensation's extra adds are not counted as work).
+# FP64 work of one FP64 LCL correction of the mixed design (residual, relative
+# humidity and LCL pressure): 1 log, 1 exp, 4 div, 27 FMA.  It runs only for LCL
+# solves whose FP32 pressure lies within the decision band of a layer or of the
+# E1 threshold (fp64_lcl_corrections, counted from the oracle's LCL pressures by
+# oracle/count_ops.py).  The CAPE, CIN and conservation sums keep FP64 accuracy
+# as compensated FP32 sums; their terms are FP32 work, already in the oracle's
+# operation counts (one add per term; the compensation's extra adds are not
+# counted as work).
 def t_fp64_islands(c, r):
     lcl = (1 / r["fp64_log"] + 1 / r["fp64_exp"] + 4 / r["fp64_div"] + 27 / r["fp64_fma"])
-    return c["fp64_lcl"] * lcl
+    return c["fp64_lcl_corrections"] * lcl
 
 
 def kernel_roofline(counts, precision, kernel_s, n_cols, r):

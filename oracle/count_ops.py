@@ -18,20 +18,76 @@ PASS_CATS = CATS + ["unused", "fp64_lcl", "fp64_cape_terms", "fp64_cin_terms",
                     "fp64_cons_terms"]
 
 
+# Relative half-width of the band around the FP32 LCL pressure within which the
+# mixed GPU path applies its FP64 LCL correction (a layer mid-point or the
+# shallow E1 threshold inside the band).
+LCL_BAND = 2e-5
+
+
+def _near(pL, kstart, pm, guard):
+    k = kstart
+    while k >= 0 and not pm[k] <= pL:
+        k -= 1
+    lo, hi = pL * (1 - LCL_BAND), pL * (1 + LCL_BAND)
+    return ((k >= 0 and pm[k] > lo) or (k < kstart and pm[k + 1] <= hi)
+            or (guard > 0 and abs(guard - pL) <= LCL_BAND * pL))
+
+
+def lcl_corrections(sub):
+    """FP64 LCL corrections per column of the mixed design, by pass: LCL solves
+    whose pressure (the oracle's) lies within LCL_BAND of a layer mid-point or
+    of the E1 threshold.  Trigger pass: the deep LCL of every valid column and
+    the shallow LCL of non-triggered ones (reused from the deep solve when the
+    launch layer is the lowest); plume pass: the shallow LCL of triggered
+    columns on the deep-updated state."""
+    od, _ = O.deep_shallow(sub, threads=os.cpu_count() or 1)
+    guard = O.shallow_params().p_lcl_min
+    pi = sub.hyai[:, None] * 1e5 + sub.hybi[:, None] * sub.ps[None, :]
+    pm = 0.5 * (pi[1:] + pi[:-1])
+    ks = sub.pver - 1
+    trig = (od["flags"] & 1) > 0
+    bad = (od["flags"] & 16) > 0
+    a = b = 0
+    for i in range(sub.n_cols):
+        if bad[i]:
+            continue
+        col = pm[:, i]
+        kb = int(od["kb"][i])
+        _, pL, _ = O.lcl(sub.T[kb, i], sub.q[kb, i], col[kb])
+        exact = pL == col[kb]
+        if not exact and _near(pL, kb, col, -1.0):
+            a += 1
+            exact = True
+        if not trig[i]:
+            if kb == ks:
+                a += int(not exact and abs(guard - pL) <= LCL_BAND * pL)
+            else:
+                _, p2, _ = O.lcl(sub.T[ks, i], sub.q[ks, i], col[ks])
+                a += int(p2 != col[ks] and _near(p2, ks, col, guard))
+        else:
+            T2 = sub.T[ks, i] + sub.dt * od["dTdt"][ks, i]
+            q2 = max(sub.q[ks, i] + sub.dt * od["dqdt"][ks, i], 0.0)
+            _, p2, _ = O.lcl(T2, q2, col[ks])
+            b += int(p2 != col[ks] and _near(p2, ks, col, guard))
+    return a / sub.n_cols, b / sub.n_cols
+
+
 def counts(g, stride=1):
     sub = S.Columns(g.name, g.pver, g.T[:, ::stride].copy(), g.q[:, ::stride].copy(),
                     g.ps[::stride].copy(), g.hyai, g.hybi)
     cd, ct = O.count_ops(sub)
     a, b, nt = O.count_ops_by_pass(sub)
+    ca, cb = lcl_corrections(sub)
     n = sub.n_cols
+    trig = {c: a[i] / n for i, c in enumerate(PASS_CATS) if c != "unused"}
+    plume = {c: b[i] / n for i, c in enumerate(PASS_CATS) if c != "unused"}
+    trig["fp64_lcl_corrections"] = ca
+    plume["fp64_lcl_corrections"] = cb
     return {"columns_counted": n, "triggered_fraction": nt / n,
             "deep_per_column": {c: cd[i] / n for i, c in enumerate(CATS)},
             "total_per_column": {c: ct[i] / n for i, c in enumerate(CATS)},
             # per column of the whole grid, split by pass of the compacted path
-            "trigger_pass_per_column": {c: a[i] / n for i, c in enumerate(PASS_CATS)
-                                        if c != "unused"},
-            "plume_pass_per_column": {c: b[i] / n for i, c in enumerate(PASS_CATS)
-                                      if c != "unused"}}
+            "trigger_pass_per_column": trig, "plume_pass_per_column": plume}
 
 
 def main():

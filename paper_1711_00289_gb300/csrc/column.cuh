@@ -241,38 +241,65 @@ __device__ __forceinline__ double ln_ratio(double x, double y) {
   return 2.0 * u * s;
 }
 
-// Mixed path LCL: the same root (written in the difference form
-// ln es(T) - ln es(Tb) - ln RH - (cp/Rd) ln(T/Tb) = 0, exactly equivalent), FP32
-// Newton iterations, then one FP64 Newton correction with the residual, the
-// relative humidity and the logarithms in FP64 (the FP64 island).
-__device__ __forceinline__ double lcl_p(float Tb, float qb, float pb, int n_newton,
-                                        float& newton) {
+// Mixed path LCL, FP32 part: the same root, written in the difference form
+// ln es(T) - ln es(Tb) - ln RH - (cp/Rd) ln(T/Tb) = 0 (exactly equivalent), by
+// FP32 Newton iterations from the same first guess.  The FP32 pressure is good
+// to ~5e-7 relative (ln RH and ln es carry ~1e-6 of FP32 rounding, i.e. 2e-5 K
+// in T_L, and p_L ~ T_L^3.5).
+struct LclF32 {
+  float T, rGp;  // solution and 1/G' at the last iterate
+  float pL;      // FP32 LCL pressure
+  bool saturated;  // parcel saturated at its level: p_L = p_b exactly
+};
+__device__ __forceinline__ LclF32 lcl_f32(float Tb, float qb, float pb, int n_newton,
+                                          float& newton) {
+  LclF32 s;
   const float esb =
       (float)ES0 * expf(fdiv_ieee((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
   float Db = pb - (float)ONE_M_EPS * esb;
   if (Db < 1e-3f * pb) Db = 1e-3f * pb;
-  if (qb >= fdiv_ieee((float)EPSV * esb, Db)) return (double)pb;
+  s.saturated = qb >= fdiv_ieee((float)EPSV * esb, Db);
+  if (s.saturated) {
+    s.T = Tb;
+    s.rGp = 0.f;
+    s.pL = pb;
+    return s;
+  }
+  const float eb = fdiv_ieee(qb * pb, (float)EPSV + (float)ONE_M_EPS * qb);
+  const float lnrh =
+      logf(eb) - ((float)LN_ES0 + fdiv_ieee((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
+  const float c1 = fdiv_ieee((float)(ESA * ESC), Tb - (float)EST1);
+  float T = fdiv_ieee(1.f, fdiv_ieee(1.f, Tb - 55.f) - lnrh * (1.f / 2840.f)) + 55.f;
+  float rGp = 0.f, step = 0.f;
+  for (int it = 0; it < n_newton; ++it) {
+    const float r = fdiv_ieee(1.f, T - (float)EST1);
+    const float G = c1 * (T - Tb) * r - lnrh - (float)INV_KAPPA * logf(fdiv_ieee(T, Tb));
+    const float Gp = (float)(ESA * ESC) * r * r - fdiv_ieee((float)INV_KAPPA, T);
+    rGp = fdiv_ieee(1.f, Gp);
+    step = G * rGp;
+    T -= step;
+  }
+  newton = fmaxf(newton, fabsf(step));
+  s.T = T;
+  s.rGp = rGp;
+  s.pL = pb * expf((float)INV_KAPPA * logf(fdiv_ieee(T, Tb)));
+  return s;
+}
+
+// Mixed path LCL, FP64 island: one FP64 Newton correction of the FP32 root with
+// the residual, the relative humidity and the logarithms in FP64; returns p_L.
+__device__ __forceinline__ double lcl_fp64_correction(float Tb, float qb, float pb,
+                                                      const LclF32& s, float& newton) {
   const double Tbd = Tb, qbd = qb, pbd = pb;
   const double eb = qbd * pbd / (EPSV + ONE_M_EPS * qbd);
   const double lnrh = log(eb) - (LN_ES0 + ESA * (Tbd - EST0) / (Tbd - EST1));
-  const float lnrhf = (float)lnrh;
-  const float c1 = fdiv_ieee((float)(ESA * ESC), Tb - (float)EST1);
-  float T = fdiv_ieee(1.f, fdiv_ieee(1.f, Tb - 55.f) - lnrhf * (1.f / 2840.f)) + 55.f;
-  float rGp = 0.f;
-  for (int it = 0; it < n_newton; ++it) {
-    const float r = fdiv_ieee(1.f, T - (float)EST1);
-    const float G = c1 * (T - Tb) * r - lnrhf - (float)INV_KAPPA * logf(fdiv_ieee(T, Tb));
-    const float Gp = (float)(ESA * ESC) * r * r - fdiv_ieee((float)INV_KAPPA, T);
-    rGp = fdiv_ieee(1.f, Gp);
-    T -= G * rGp;
-  }
-  const double Td = T;
+  const double Td = s.T;
   const double lr = ln_ratio(Td, Tbd);
   const double G = ESA * ESC * (Td - Tbd) / ((Td - EST1) * (Tbd - EST1)) - lnrh - INV_KAPPA * lr;
-  const double step = G * (double)rGp;
+  const double step = G * (double)s.rGp;
   newton = fmaxf(newton, (float)fabs(step));
   // ln(TL/Tb) = ln(T/Tb) - step/T to second order in the (tiny) step
-  return pbd * exp(INV_KAPPA * (lr - step * (double)fdiv_ieee(1.f, T)));
+  return pbd * exp(INV_KAPPA * (lr - step * (double)fdiv_ieee(1.f, s.T)));
 }
 
 // LCL layer comparisons p_mid[k] <= pL.  In FP32 the comparison runs against pL
@@ -543,6 +570,58 @@ __device__ __forceinline__ int lcl_level(const Column<R>& c, int kstart, double 
   return -1;
 }
 
+// LCL pressure and layer of the parcel at layer kstart.  `guard`: a pressure the
+// caller compares with p_L (the shallow E1 threshold), or <= 0.
+// FP64 path: the FP64 Newton solve.  Mixed path: the FP32 solve decides the
+// layer, and the FP64 correction runs only where the FP32 value could decide
+// differently from the FP64 one -- a layer mid-point or the guard within
+// kLclBand (40 times the FP32 error) of the FP32 p_L.  Elsewhere every
+// comparison the scheme makes with p_L comes out as with the FP64 value.
+// `exact`: p_L is the FP64 (or exactly saturated) value.
+constexpr float kLclBand = 2e-5f;
+struct Lcl {
+  double pL;
+  int klcl;
+  bool exact;
+};
+__device__ __forceinline__ Lcl lcl_solve(const Column<double>& c, int kstart, int n_newton,
+                                         float& newton, double) {
+  Lcl r;
+  r.pL = lcl_p(c.T(kstart), c.q(kstart), c.pm(kstart), n_newton, newton);
+  r.klcl = lcl_level(c, kstart, r.pL);
+  r.exact = true;
+  return r;
+}
+__device__ __forceinline__ Lcl lcl_solve(const Column<float>& c, int kstart, int n_newton,
+                                         float& newton, double guard) {
+  const float Tb = c.T(kstart), qb = c.q(kstart), pb = c.pm(kstart);
+  const LclF32 s = lcl_f32(Tb, qb, pb, n_newton, newton);
+  Lcl r;
+  if (s.saturated) {
+    r.pL = (double)pb;
+    r.klcl = kstart;  // p_mid[kstart] = p_b
+    r.exact = true;
+    return r;
+  }
+  const float pLf = s.pL;
+  int k = kstart;
+  for (; k >= 0; --k)
+    if (c.pm(k) <= pLf) break;
+  const float lo = pLf * (1.f - kLclBand), hi = pLf * (1.f + kLclBand);
+  const bool near_level = (k >= 0 && c.pm(k) > lo) || (k < kstart && c.pm(k + 1) <= hi);
+  const bool near_guard = guard > 0.0 && fabsf((float)guard - pLf) <= kLclBand * pLf;
+  if (!(near_level || near_guard)) {
+    r.pL = (double)pLf;
+    r.klcl = k;
+    r.exact = false;
+    return r;
+  }
+  r.pL = lcl_fp64_correction(Tb, qb, pb, s, newton);
+  r.klcl = lcl_level(c, kstart, r.pL);
+  r.exact = true;
+  return r;
+}
+
 // Tendency output of one scheme for one column: [pver][ld] arrays, written
 // level by level as the scheme produces them.
 template <class R>
@@ -579,6 +658,7 @@ template <class R>
 struct DeepTrig {
   int kb, klcl, kel;
   double cape, pL;
+  bool pL_exact;
   bool triggered;
   float newton;
   R Tp[MAXL];
@@ -605,9 +685,10 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   t.cape = 0.0;
   t.triggered = false;
   t.newton = 0.f;
-  const double pL = lcl_p(c.T(kb), c.q(kb), c.pm(kb), P.n_newton_lcl, t.newton);
-  t.pL = pL;
-  const int klcl = lcl_level(c, kb, pL);
+  const Lcl lcl = lcl_solve(c, kb, P.n_newton_lcl, t.newton, -1.0);
+  t.pL = lcl.pL;
+  t.pL_exact = lcl.exact;
+  const int klcl = lcl.klcl;
   t.klcl = klcl;
   if (klcl < ktl) return;
   // Undilute parcel up from the LCL layer; CAPE accumulated in FP64, bottom up,
@@ -911,7 +992,8 @@ template <class R>
 struct ShallowSeed {
   double pL;
   int klcl;
-  const R* Tp;  // parcel temperature on ktl..klcl
+  bool pL_exact;  // pL is FP64 (see lcl_solve); else checked against p_lcl_min here
+  const R* Tp;    // parcel temperature on ktl..klcl
 };
 
 // Whole shallow scheme for one column in c (Alg. 3); writes every level of out.
@@ -942,12 +1024,17 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
   double pL;
   int klcl;
   const R Tsrc = c.T(ks), qsrc = c.q(ks), psrc = c.pm(ks);
+  // a seed whose FP32 p_L sits too close to the E1 threshold is not reused
+  if (seed && !seed->pL_exact &&
+      fabs(P.p_lcl_min - seed->pL) <= (double)kLclBand * seed->pL)
+    seed = nullptr;
   if (seed) {
     pL = seed->pL;
     klcl = seed->klcl;
   } else {
-    pL = lcl_p(Tsrc, qsrc, psrc, P.n_newton_lcl, newton);
-    klcl = lcl_level(c, ks, pL);
+    const Lcl lcl = lcl_solve(c, ks, P.n_newton_lcl, newton, P.p_lcl_min);
+    pL = lcl.pL;
+    klcl = lcl.klcl;
   }
   o.klcl = klcl;
   int exit_code = 0;

@@ -80,7 +80,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
                           a.sp.n_newton_lcl == a.dp.n_newton_lcl &&
                           a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
     if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(a.sp.p_top_lim, c, (R*)nullptr);
-    ShallowSeed<R> seed{t.pL, t.klcl, t.Tp};
+    ShallowSeed<R> seed{t.pL, t.klcl, t.pL_exact, t.Tp};
     shallow_column(a.sp, c, s, so, same_src ? &seed : nullptr, true);
   }
   store_shallow_scalars(a, i, s);
