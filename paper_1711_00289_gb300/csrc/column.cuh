@@ -661,7 +661,27 @@ struct DeepTrig {
   bool pL_exact;
   bool triggered;
   float newton;
+  uint32_t maybe_buoy;  // bit k: parcel buoyancy > -kBuoyMargin at layer k (klcl..ktl)
   R Tp[MAXL];
+};
+
+// Margin (K) of the buoyancy bound the shallow scheme takes from the deep
+// trigger (DeepBound): far above the rounding of either parcel's virtual
+// temperature (~1e-5 K in FP32).
+constexpr double kBuoyMargin = 1e-2;
+
+// What the deep trigger on the same column state tells the shallow scheme about
+// buoyancy.  The deep parcel starts from the launch layer, whose MSE is the
+// largest below p_launch_min, so at least that of the shallow source (the
+// lowest layer); at every layer above both LCLs the saturated parcel
+// temperature grows with the parcel's MSE, and so does its buoyancy.  Where the
+// deep parcel is not buoyant even within kBuoyMargin, the shallow parcel is not
+// buoyant either.  The shallow scheme uses this (certainly_no_lfc) to settle
+// exit E2 (no LFC) -- the outcome of the full search -- without its moist
+// inversions when it can.
+struct DeepBound {
+  int klcl, ktl;        // the deep parcel's LCL layer and top limit
+  uint32_t maybe_buoy;  // DeepTrig::maybe_buoy
 };
 
 // Launch level, LCL, undilute parcel, CAPE and trigger (deep "stage A").
@@ -685,6 +705,7 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   t.cape = 0.0;
   t.triggered = false;
   t.newton = 0.f;
+  t.maybe_buoy = 0u;
   const Lcl lcl = lcl_solve(c, kb, P.n_newton_lcl, t.newton, -1.0);
   t.pL = lcl.pL;
   t.pL_exact = lcl.exact;
@@ -704,6 +725,7 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
     t.Tp[k] = Tp;
     const R b = virt(Tp, sat_qs(Tp, pm)) - virt(Tk, c.q(k));
     run.add(R(RD) * b * c.dl[k]);
+    if (b > R(-kBuoyMargin)) t.maybe_buoy |= 1u << k;
     if (b > R(0)) {
       kel = k;
       at_el = run;
@@ -952,12 +974,16 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
 }
 
 // Whole deep scheme for one column (T, q, ps set in c); writes every level of out.
+// bound (may be nullptr): set valid when the column did not trigger, the deep
+// trigger converged and the state is unchanged for the shallow scheme.
 template <class R>
 __device__ __forceinline__ void deep_column(const conv_deep_params& P, double dt, R lam, R tau,
-                                            Column<R>& c, DeepOut& o, const OutCol<R>& out) {
+                                            Column<R>& c, DeepOut& o, const OutCol<R>& out,
+                                            DeepBound* bound = nullptr, bool* bound_ok = nullptr) {
   o.prec = o.cape = o.mb = o.cons = 0.0;
   o.flags = 0;
   o.kb = o.klcl = o.ktop = o.kaux = -1;
+  if (bound_ok) *bound_ok = false;
   if (!column_valid(c)) {
     o.flags = CONV_FLAG_BADINPUT;
     out.zero(0, c.pver);
@@ -975,6 +1001,10 @@ __device__ __forceinline__ void deep_column(const conv_deep_params& P, double dt
     deep_plume(c, hs, P, dt, lam, tau, t, o, out);
   } else {
     out.zero(0, c.pver);
+    if (bound && t.newton <= Mth<R>::newton_tol) {
+      *bound = DeepBound{t.klcl, c.ktl, t.maybe_buoy};
+      *bound_ok = true;
+    }
   }
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
 }
@@ -996,6 +1026,48 @@ struct ShallowSeed {
   const R* Tp;    // parcel temperature on ktl..klcl
 };
 
+// Upper bound on the saturated parcel's buoyancy at layer k, below -kBuoyMargin?
+// The residual f(T) = cp (T - Tref) + g z + Lv (qs(T) - qref) - h of the
+// saturated parcel is increasing and convex in T (es is convex for T < 2000 K
+// and qs a convex increasing function of es while unclamped), so the zero of
+// its tangent at any point -- one Newton step, here from the environment
+// temperature -- lies at or above the parcel temperature, and buoyancy grows
+// with the parcel temperature.  Declines (returns false) where the qs clamp
+// could be active.
+template <class R>
+__device__ __forceinline__ bool tangent_not_buoyant(const Column<R>& c, int k, R pm, R h) {
+  const R Te = c.T(k);
+  const R rt = Mth<R>::dv(R(1), Te - R(EST1));
+  const R es0 = R(ES0) * Mth<R>::es(R(ESA) * (Te - R(EST0)) * rt);
+  const R D0 = pm - R(ONE_M_EPS) * es0;
+  if (!(D0 >= R(1e-3) * pm)) return false;
+  const R qs0 = Mth<R>::dv(R(EPSV) * es0, D0);
+  const R dqs0 = Mth<R>::dv(qs0 * pm, D0) * (R(ESA * ESC) * rt * rt);
+  const R f0 = R(CP) * (Te - c.Tref) + R(GRAV) * c.zm[k] + R(LV) * (qs0 - c.qref) - h;
+  const R T1 = Te - Mth<R>::dv(f0, R(CP) + R(LV) * dqs0);
+  const R es1 = R(ES0) * Mth<R>::es(Mth<R>::dv(R(ESA) * (T1 - R(EST0)), T1 - R(EST1)));
+  const R D1 = pm - R(ONE_M_EPS) * es1;
+  if (!(D1 >= R(1e-3) * pm)) return false;
+  const R bup = virt(T1, Mth<R>::dv(R(EPSV) * es1, D1)) - c.Tv(k);
+  return bup < R(-kBuoyMargin);
+}
+
+// True when no layer the shallow LFC search can reach (k <= klcl, p_mid >= plfc,
+// k >= ktl) can hold a buoyant parcel of MSE h: layers the deep parcel covers
+// by the deep bound, the others by the tangent bound.  False does not mean an
+// LFC exists, only that the full search must decide.
+template <class R>
+__device__ __forceinline__ bool certainly_no_lfc(const Column<R>& c, const DeepBound& b, R h,
+                                                 int klcl, R plfc) {
+  for (int k = klcl; k >= c.ktl; --k) {
+    const R pm = c.pm(k);
+    if (!(pm >= plfc)) return true;
+    if (k <= b.klcl && k >= b.ktl && !((b.maybe_buoy >> k) & 1u)) continue;
+    if (!tangent_not_buoyant(c, k, pm, h)) return false;
+  }
+  return true;
+}
+
 // Whole shallow scheme for one column in c (Alg. 3); writes every level of out.
 // When `prologue_done` the column has been validated and its prologue computed
 // already.  The plume's tendencies go out level by level as the plume rises:
@@ -1006,7 +1078,8 @@ template <class R>
 __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Column<R>& c,
                                                ShalOut& o, const OutCol<R>& out,
                                                const ShallowSeed<R>* seed = nullptr,
-                                               bool prologue_done = false) {
+                                               bool prologue_done = false,
+                                               const DeepBound* bound = nullptr) {
   const int pver = c.pver;
   o.prec = o.cin = o.mb = o.cons = 0.0;
   o.flags = 0;
@@ -1051,7 +1124,11 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
     Acc<R> cina;
     MoistSeq<R> seq;
     seq.have = false;
-    for (int k = ks; k >= ktl; --k) {
+    // a column the deep scheme found stable: first try to settle exit E2 (no LFC)
+    // by bounds alone
+    const bool no_lfc =
+        bound != nullptr && seed == nullptr && certainly_no_lfc(c, *bound, hsrc, klcl, plfc);
+    for (int k = ks; !no_lfc && k >= ktl; --k) {
       const R pm = c.pm(k);
       if (!(pm >= plfc)) break;
       R Tp, qp;

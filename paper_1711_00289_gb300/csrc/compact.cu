@@ -79,9 +79,11 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     const bool same_src = t.kb == c.pver - 1 && a.sp.p_top_lim == a.dp.p_top_lim &&
                           a.sp.n_newton_lcl == a.dp.n_newton_lcl &&
                           a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
+    const DeepBound bound{t.klcl, c.ktl, t.maybe_buoy};
+    const bool bound_ok = t.newton <= Mth<R>::newton_tol;
     if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(a.sp.p_top_lim, c, (R*)nullptr);
     ShallowSeed<R> seed{t.pL, t.klcl, t.pL_exact, t.Tp};
-    shallow_column(a.sp, c, s, so, same_src ? &seed : nullptr, true);
+    shallow_column(a.sp, c, s, so, same_src ? &seed : nullptr, true, bound_ok ? &bound : nullptr);
   }
   store_shallow_scalars(a, i, s);
 }

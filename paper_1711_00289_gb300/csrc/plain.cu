@@ -26,19 +26,24 @@ __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
   if (i >= a.n) return;
   Column<R> c;
   init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
+  DeepBound bound;
+  bool bound_ok = false;
   if (a.mode & MODE_DEEP) {
     DeepOut o;
     const R lam = (R)(a.lam ? a.lam[i] : a.dp.lambda_default);
     const R tau = (R)(a.tau ? a.tau[i] : a.dp.tau_default);
-    deep_column(a.dp, a.dt, lam, tau, c, o, out_col<R>(a.od, a, i));
+    deep_column(a.dp, a.dt, lam, tau, c, o, out_col<R>(a.od, a, i), &bound, &bound_ok);
     store_deep_scalars(a, i, o);
-    // the limiter keeps q >= q_min up to rounding; a rejected column passes unchanged
+    // the limiter keeps q >= q_min up to rounding; a rejected column passes
+    // unchanged.  A column that did not trigger has zero tendencies: the shallow
+    // scheme sees the state the deep trigger saw.
     if (a.mode & MODE_SHALLOW)
       c.s = after_deep_src<R>(a, i, (o.flags & CONV_FLAG_BADINPUT) != 0);
   }
   if (a.mode & MODE_SHALLOW) {
     ShalOut o;
-    shallow_column(a.sp, c, o, out_col<R>(a.os, a, i));
+    shallow_column(a.sp, c, o, out_col<R>(a.os, a, i), (const ShallowSeed<R>*)nullptr, false,
+                   bound_ok ? &bound : nullptr);
     store_shallow_scalars(a, i, o);
   }
 }
