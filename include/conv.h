@@ -46,8 +46,10 @@
  *   bit 0  CONV_FLAG_TRIGGERED  deep: CAPE > capelmt; shallow: passed exits E1-E3
  *   bit 1  CONV_FLAG_ACTIVE     scheme produced non-zero tendencies
  *   bit 2  CONV_FLAG_LIMITED    deep mass flux cut by the q >= q_min limiter
- *   bit 3  CONV_FLAG_NEWTON     a Newton solve's last correction exceeded 1e-4 K
- *                               (FP64; 1e-3 K in the mixed path, above FP32 noise)
+ *   bit 3  CONV_FLAG_NEWTON     a Newton solve did not converge: FP64, its last
+ *                               correction exceeded 1e-4 K; mixed path, the error
+ *                               its last step leaves (0.1/K x correction^2 by
+ *                               quadratic convergence) exceeded 1e-3 K
  *   bit 4  CONV_FLAG_BADINPUT   T outside (100, 400) K, q outside [0, 0.1),
  *                               ps outside (5e4, 1.2e5) Pa or not finite;
  *                               all outputs of the column are zero
