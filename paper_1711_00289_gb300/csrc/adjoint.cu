@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(64) k_deep_adjoint(const __grid_constant__ Adj
   const double gP = A.gP ? A.gP[i] : 0.0, gH = A.gH ? A.gH[i] : 0.0;
   const bool rev = A.gT != nullptr;
   double bT[MAXL], bq[MAXL], blam, btau, Pv, Hv;
-  deep_adjoint_column(a.dp, a.dt, lam, tau, c, gP, gH, A.w.given ? A.w.w : nullptr, rev, bT,
+  deep_adjoint_column(a.dp, a.dqd, lam, tau, c, gP, gH, A.w.given ? A.w.w : nullptr, rev, bT,
                       bq, blam, btau, Pv, Hv);
   if (rev) {
     for (int k = 0; k < pver; ++k) {

@@ -46,8 +46,8 @@ __device__ __forceinline__ void inv_adj(double T, double p, double bT, double& b
 // H = sum_k w_k m_k cp dTdt_k into Pv, Hv, and -- when `reverse` -- the gradient
 // of J = gP P + gH H into bT, bq [pver], blam, btau (all zeroed first).
 // w_heat: [pver] weights, or nullptr for w_k = p_mid_k / ps.
-__device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P, double dt,
-                                                    double lam, double tau,
+__device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P,
+                                                    const DeepQ<double>& Q, double lam, double tau,
                                                     Column<double>& c, double gP, double gH,
                                                     const double* w_heat, bool reverse,
                                                     double* bT, double* bq, double& blam,
@@ -60,12 +60,12 @@ __device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P, d
   DeepTrig<double> t;
   if (column_valid(c)) {
     double hs[MAXL];
-    prologue(P.p_top_lim, c, hs);
-    deep_trigger(c, P, t);
+    prologue(Q.p_top_lim, c, hs);
+    deep_trigger(c, P, Q, t);
     if (t.triggered) {
       DeepOut o;
       o.flags = 0;
-      deep_plume<double, DeepTape<double>>(c, hs, P, dt, lam, tau, t, o, NoOut<double>(), &tp);
+      deep_plume<double, DeepTape<double>>(c, hs, P, Q, lam, tau, t, o, NoOut<double>(), &tp);
     }
   }
   if (!tp.active) return;
@@ -102,9 +102,9 @@ __device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P, d
     // closure or limiter
     if (tp.limited) {
       const int ks = tp.kstar;
-      const double N = c.q(ks) - P.q_min, Dn = -dt * tp.dq[ks];
+      const double N = c.q(ks) - P.q_min, Dn = -Q.dt * tp.dq[ks];
       bq[ks] += bMb / Dn;
-      bdq[ks] += bMb * N * dt / (Dn * Dn);
+      bdq[ks] += bMb * N * Q.dt / (Dn * Dn);
     } else {
       const double F = tp.F, cape = t.cape;
       bCAPE += -bMb / (tau * F);

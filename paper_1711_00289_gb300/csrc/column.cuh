@@ -37,6 +37,7 @@
 //            dw2/dz = 2 a B - 2 b eps w2 integrated exactly per layer.
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 
 #include "conv.h"
@@ -357,6 +358,54 @@ struct Acc<float> {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// ---------------------------------------------------------------- parameters
+// Scheme parameters in the working precision, with the parameter-only
+// expressions the schemes need, computed once on the host: in a kernel, a
+// double-to-float conversion or an FP64 operation runs on the FP64 pipe, at
+// 1/67 of the FP32 rate on this device.
+template <class R>
+struct DeepQ {
+  R p_launch_min, p_top_lim, ent_zscale, c0, alpha_dd, q_min, dt, lambda_default, tau_default;
+};
+template <class R>
+struct ShalQ {
+  R p_top_lim, p_lfc_min, p_lcl_min, eps, w2_0, m2beps, aw_beps, aw2, ql_crit;
+  R cm_sqrt_tke;  // c_m sqrt(tke)
+  R m_inv_cin;    // -1 / (cin_scale tke)
+  bool drag;      // b_w eps_s > 0
+};
+template <class R>
+inline DeepQ<R> make_deep_q(const conv_deep_params& P, double dt) {
+  return DeepQ<R>{(R)P.p_launch_min, (R)P.p_top_lim, (R)P.ent_zscale, (R)P.c0, (R)P.alpha_dd,
+                  (R)P.q_min, (R)dt, (R)P.lambda_default, (R)P.tau_default};
+}
+template <class R>
+inline ShalQ<R> make_shal_q(const conv_shallow_params& P) {
+  const double beps = P.b_w * P.eps_s;
+  ShalQ<R> q;
+  q.p_top_lim = (R)P.p_top_lim;
+  q.p_lfc_min = (R)P.p_lfc_min;
+  q.p_lcl_min = (R)P.p_lcl_min;
+  q.eps = (R)P.eps_s;
+  q.w2_0 = (R)(2.0 / 3.0 * P.tke);
+  q.drag = beps > 0.0;
+  q.m2beps = (R)(-2.0 * beps);
+  q.aw_beps = q.drag ? (R)(P.a_w / beps) : R(0);
+  q.aw2 = (R)(2.0 * P.a_w);
+  q.ql_crit = (R)P.ql_crit;
+  q.cm_sqrt_tke = (R)(P.c_m * std::sqrt(P.tke));
+  q.m_inv_cin = (R)(-1.0 / (P.cin_scale * P.tke));
+  return q;
+}
+
+// Conservation residual ratio of a scheme's outputs: numerator and denominator
+// in FP64 (the numerator is a cancellation), the ratio -- a diagnostic -- in
+// the working precision.
+__device__ __forceinline__ double cons_ratio(double num, double den, double) { return num / den; }
+__device__ __forceinline__ double cons_ratio(double num, double den, float) {
+  return (double)((float)num / (float)den);
+}
+
 // ---------------------------------------------------------------- column state
 // T + dt*dT/dt as the schemes chain it (Alg. 1): FP64 without contraction.
 // (dt already in the working precision: the mixed path converts it once.)
@@ -534,10 +583,9 @@ __device__ __forceinline__ bool column_valid(const Column<R>& c) {
 // Heights, log-thicknesses, top limit and (when hs != nullptr) saturation moist
 // static energies (shared by both schemes).
 template <class R>
-__device__ __forceinline__ void prologue(double p_top_lim, Column<R>& c, R* hs) {
+__device__ __forceinline__ void prologue(R ptl, Column<R>& c, R* hs) {
   const auto P = c.press();
   const int pver = c.pver;
-  const R ptl = (R)p_top_lim;
   R pi_lo = P.pi(pver);
   R zi = R(0);
   if constexpr (ColCache<R>::on) {
@@ -605,7 +653,7 @@ __device__ __forceinline__ Lcl lcl_solve(const Column<double>& c, int kstart, in
   return r;
 }
 __device__ __forceinline__ Lcl lcl_solve(const Column<float>& c, int kstart, int n_newton,
-                                         float& newton, double guard) {
+                                         float& newton, float guard) {
   const float Tb = c.T(kstart), qb = c.q(kstart), pb = c.pm(kstart);
   const LclF32 s = lcl_f32(Tb, qb, pb, n_newton, newton);
   Lcl r;
@@ -621,7 +669,7 @@ __device__ __forceinline__ Lcl lcl_solve(const Column<float>& c, int kstart, int
     if (c.pm(k) <= pLf) break;
   const float lo = pLf * (1.f - kLclBand), hi = pLf * (1.f + kLclBand);
   const bool near_level = (k >= 0 && c.pm(k) > lo) || (k < kstart && c.pm(k + 1) <= hi);
-  const bool near_guard = guard > 0.0 && fabsf((float)guard - pLf) <= kLclBand * pLf;
+  const bool near_guard = guard > 0.f && fabsf(guard - pLf) <= kLclBand * pLf;
   if (!(near_level || near_guard)) {
     r.pL = (double)pLf;
     r.klcl = k;
@@ -700,9 +748,9 @@ struct DeepBound {
 // t.Tp holds the parcel temperature on ktl..klcl whenever klcl >= ktl.
 template <class R>
 __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep_params& P,
-                                             DeepTrig<R>& t) {
+                                             const DeepQ<R>& Q, DeepTrig<R>& t) {
   const int pver = c.pver, ktl = c.ktl;
-  const R plaunch = (R)P.p_launch_min;
+  const R plaunch = Q.p_launch_min;
   int kb = pver - 1;
   R hb = c.h(kb);
   for (int k = pver - 2; k >= 0 && c.pm(k) >= plaunch; --k) {
@@ -718,7 +766,7 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   t.triggered = false;
   t.newton = 0.f;
   t.maybe_buoy = 0u;
-  const Lcl lcl = lcl_solve(c, kb, P.n_newton_lcl, t.newton, -1.0);
+  const Lcl lcl = lcl_solve(c, kb, P.n_newton_lcl, t.newton, R(-1));
   t.pL = lcl.pL;
   t.pL_exact = lcl.exact;
   const int klcl = lcl.klcl;
@@ -773,12 +821,12 @@ struct DeepTape {
 // column's saturation MSE; writes every level of `out`.
 template <class R, class TP = NoTape, class OUT = OutCol<R>>
 __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
-                                           const conv_deep_params& P, double dt, R lam, R tau,
-                                           DeepTrig<R>& t, DeepOut& o, const OUT& out,
+                                           const conv_deep_params& P, const DeepQ<R>& Q, R lam,
+                                           R tau, DeepTrig<R>& t, DeepOut& o, const OUT& out,
                                            TP* tape = nullptr) {
   if constexpr (TP::kOn) tape->active = false;
   const int pver = c.pver, ktl = c.ktl, kb = t.kb, klcl = t.klcl, kel = t.kel;
-  const R ze = (R)P.ent_zscale;
+  const R ze = Q.ent_zscale;
   // minimum h* layer above the LCL (ties: lowest)
   int khmin = -1;
   for (int k = klcl - 1; k >= ktl; --k)
@@ -791,7 +839,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
     tape->qtu[kb] = qtu1;
   }
   const R zb = c.zm[kb];
-  const R c0 = (R)P.c0;
+  const R c0 = Q.c0;
   int jt = -1;
   R sumR = R(0);
   MoistSeq<R> seq;
@@ -864,7 +912,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
       qd1 = qd;
       eprev = e;
     }
-    alpha = (R)P.alpha_dd;
+    alpha = Q.alpha_dd;
     const bool capped = alpha * sumE > sumR;
     if (capped) alpha = Mth<R>::dv(sumR, sumE);
     if constexpr (TP::kOn) tape->capped = capped;
@@ -923,7 +971,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
   R mb = Mth<R>::dv((R)(-t.cape), tau * F);
   bool limited = false;
   int kstar = -1;
-  const R qmin = (R)P.q_min, mdt = -(R)dt;
+  const R qmin = Q.q_min, mdt = -Q.dt;
   for (int k = jt; k <= kb; ++k) {
     if (dq[k] < R(0)) {
       const R ml = Mth<R>::dv(c.q(k) - qmin, mdt * dq[k]);
@@ -981,16 +1029,16 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
   }
   out.zero(kb + 1, pver);
   const double se = CP * sea.value(), sw = swa.value();
-  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) /
-           (CP * (double)sc + LV * o.prec + 1e-300);
+  o.cons = cons_ratio(fabs(se - LV * o.prec) + LV * fabs(sw + o.prec),
+                      CP * (double)sc + LV * o.prec + 1e-300, R(0));
 }
 
 // Whole deep scheme for one column (T, q, ps set in c); writes every level of out.
 // bound (may be nullptr): set valid when the column did not trigger, the deep
 // trigger converged and the state is unchanged for the shallow scheme.
 template <class R>
-__device__ __forceinline__ void deep_column(const conv_deep_params& P, double dt, R lam, R tau,
-                                            Column<R>& c, DeepOut& o, const OutCol<R>& out,
+__device__ __forceinline__ void deep_column(const conv_deep_params& P, const DeepQ<R>& Q, R lam,
+                                            R tau, Column<R>& c, DeepOut& o, const OutCol<R>& out,
                                             DeepBound* bound = nullptr, bool* bound_ok = nullptr) {
   o.prec = o.cape = o.mb = o.cons = 0.0;
   o.flags = 0;
@@ -1002,15 +1050,15 @@ __device__ __forceinline__ void deep_column(const conv_deep_params& P, double dt
     return;
   }
   R hs[MAXL];
-  prologue(P.p_top_lim, c, hs);
+  prologue(Q.p_top_lim, c, hs);
   DeepTrig<R> t;
-  deep_trigger(c, P, t);
+  deep_trigger(c, P, Q, t);
   o.kb = t.kb;
   o.klcl = t.klcl;
   o.cape = t.cape;
   if (t.triggered) {
     o.flags |= CONV_FLAG_TRIGGERED;
-    deep_plume(c, hs, P, dt, lam, tau, t, o, out);
+    deep_plume(c, hs, P, Q, lam, tau, t, o, out);
   } else {
     out.zero(0, c.pver);
     if (bound && t.newton <= Mth<R>::newton_tol) {
@@ -1087,7 +1135,8 @@ __device__ __forceinline__ bool certainly_no_lfc(const Column<R>& c, const DeepB
 // the top layer's when the plume stops; a plume that dies at its LCL (exit E4)
 // overwrites what it wrote with zeros.
 template <class R>
-__device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Column<R>& c,
+__device__ __forceinline__ void shallow_column(const conv_shallow_params& P, const ShalQ<R>& Q,
+                                               Column<R>& c,
                                                ShalOut& o, const OutCol<R>& out,
                                                const ShallowSeed<R>* seed = nullptr,
                                                bool prologue_done = false,
@@ -1102,7 +1151,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
       out.zero(0, pver);
       return;
     }
-    prologue(P.p_top_lim, c, (R*)nullptr);
+    prologue(Q.p_top_lim, c, (R*)nullptr);
   }
   const int ks = pver - 1, ktl = c.ktl;
   float newton = 0.f;
@@ -1117,7 +1166,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
     pL = seed->pL;
     klcl = seed->klcl;
   } else {
-    const Lcl lcl = lcl_solve(c, ks, P.n_newton_lcl, newton, P.p_lcl_min);
+    const Lcl lcl = lcl_solve(c, ks, P.n_newton_lcl, newton, Q.p_lcl_min);
     pL = lcl.pL;
     klcl = lcl.klcl;
   }
@@ -1125,7 +1174,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
   int exit_code = 0;
   R mb = R(0);
   int klfc = -1, kts = -1;
-  const R plfc = (R)P.p_lfc_min;
+  const R plfc = Q.p_lfc_min;
   const R hsrc = c.h(ks);
   Acc<R> sea, swa;
   R sc = R(0), sumr = R(0);
@@ -1170,7 +1219,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
         exit_code = 3;
       } else {
         const R rho = Mth<R>::dv(psrc, R(RD) * c.Tv(ks));
-        mb = rho * (R)(P.c_m * sqrt(P.tke)) * Mth<R>::ex((R)(-cin / (P.cin_scale * P.tke)));
+        mb = rho * Q.cm_sqrt_tke * Mth<R>::ex((R)cin * Q.m_inv_cin);
         // plume, with a two-level window: (hu2, qtu2) at k+2, (hu1, qtu1, qp1, rf1) at k+1
         const R hsrc_env = hsrc;
         R hu2 = R(0), qtu2 = R(0);
@@ -1189,15 +1238,10 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
         };
         // the source layer's tendency (its formula does not depend on the top)
         emit(ks, mb * (h_up - hsrc_env), mb * (q_up - qsrc));
-        const R w2_0 = (R)(2.0 / 3.0 * P.tke);
-        R w2 = w2_0;
-        const R eps = (R)P.eps_s;
-        const double beps = P.b_w * P.eps_s;
-        const bool drag = beps > 0.0;
-        const R m2beps = (R)(-2.0 * beps);
-        const R aw_beps = drag ? (R)(P.a_w / beps) : R(0);
-        const R aw2 = (R)(2.0 * P.a_w);
-        const R qlc = (R)P.ql_crit;
+        R w2 = Q.w2_0;
+        const R eps = Q.eps;
+        const bool drag = Q.drag;
+        const R m2beps = Q.m2beps, aw_beps = Q.aw_beps, aw2 = Q.aw2, qlc = Q.ql_crit;
         seq.have = false;
         for (int k = ks - 1; k >= ktl; --k) {
           const R dz = c.dz(k);
@@ -1293,8 +1337,8 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, Col
   o.prec = (double)(mb * sumr);
   o.ktop = kts;
   const double se = CP * sea.value(), sw = swa.value();
-  o.cons = (fabs(se - LV * o.prec) + LV * fabs(sw + o.prec)) /
-           (CP * (double)sc + LV * o.prec + 1e-300);
+  o.cons = cons_ratio(fabs(se - LV * o.prec) + LV * fabs(sw + o.prec),
+                      CP * (double)sc + LV * o.prec + 1e-300, R(0));
 }
 
 }  // namespace cvg

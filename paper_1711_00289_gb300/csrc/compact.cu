@@ -38,8 +38,8 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     if (!valid) {
       o.flags = CONV_FLAG_BADINPUT;
     } else {
-      prologue(a.dp.p_top_lim, c, (R*)nullptr);  // h* is needed only by the plume pass
-      deep_trigger(c, a.dp, t);
+      prologue(deep_q(a, R(0)).p_top_lim, c, (R*)nullptr);  // h* only in the plume pass
+      deep_trigger(c, a.dp, deep_q(a, R(0)), t);
       o.kb = t.kb;
       o.klcl = t.klcl;
       o.cape = t.cape;
@@ -72,7 +72,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
   ShalOut s;
   const OutCol<R> so = out_col<R>(a.os, a, i);
   if (!valid) {
-    shallow_column(a.sp, c, s, so);  // flags the column as bad input
+    shallow_column(a.sp, shal_q(a, R(0)), c, s, so);  // flags the column as bad input
   } else {
     // same state as the deep scheme saw: reuse the prologue, and the LCL/parcel
     // when the deep launch layer is the shallow source layer
@@ -81,9 +81,10 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
                           a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
     const DeepBound bound{t.klcl, c.ktl, t.maybe_buoy};
     const bool bound_ok = t.newton <= Mth<R>::newton_tol;
-    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(a.sp.p_top_lim, c, (R*)nullptr);
+    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(shal_q(a, R(0)).p_top_lim, c, (R*)nullptr);
     ShallowSeed<R> seed{t.pL, t.klcl, t.pL_exact, t.Tp};
-    shallow_column(a.sp, c, s, so, same_src ? &seed : nullptr, true, bound_ok ? &bound : nullptr);
+    shallow_column(a.sp, shal_q(a, R(0)), c, s, so, same_src ? &seed : nullptr, true,
+                   bound_ok ? &bound : nullptr);
   }
   store_shallow_scalars(a, i, s);
 }
@@ -117,19 +118,20 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   o.kb = t.kb;
   o.klcl = t.klcl;
   o.ktop = o.kaux = -1;
-  const R lam = (R)(a.lam ? a.lam[i] : a.dp.lambda_default);
-  const R tau = (R)(a.tau ? a.tau[i] : a.dp.tau_default);
+  const DeepQ<R>& Q = deep_q(a, R(0));
+  const R lam = a.lam ? (R)a.lam[i] : Q.lambda_default;
+  const R tau = a.tau ? (R)a.tau[i] : Q.tau_default;
   {
     R hs[MAXL];
-    prologue(a.dp.p_top_lim, c, hs);
-    deep_plume(c, hs, a.dp, a.dt, lam, tau, t, o, out_col<R>(a.od, a, i));
+    prologue(Q.p_top_lim, c, hs);
+    deep_plume(c, hs, a.dp, Q, lam, tau, t, o, out_col<R>(a.od, a, i));
   }
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
   c.s = after_deep_src<R>(a, i, false);  // limiter keeps q >= q_min up to rounding
   ShalOut s;
-  shallow_column(a.sp, c, s, out_col<R>(a.os, a, i));
+  shallow_column(a.sp, shal_q(a, R(0)), c, s, out_col<R>(a.os, a, i));
   store_shallow_scalars(a, i, s);
 }
 

@@ -92,6 +92,7 @@ size_t needed_ws(int n, int pver, conv_precision prec, int path) {
 
 conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch, void* ws,
                      size_t ws_bytes) {
+  cvg::fill_q(a);
   if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
   if (launch && (launch->path < CONV_PATH_AUTO || launch->path > CONV_PATH_COMPACT))
     return CONV_ERR_ARG;
@@ -260,6 +261,7 @@ conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
   a.dp = *par;
   a.mode = cvg::MODE_DEEP;
   a.stream = reinterpret_cast<cudaStream_t>(stream);
+  cvg::fill_q(a);
   const cudaError_t e =
       cvg::launch_deep_adjoint(a, gP, gH, w, gT, gq, glambda, gtau, P_out, H_out);
   return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
@@ -322,6 +324,7 @@ conv_status conv_batch_plan(const conv_member* members, int n_members, conv_prec
     a.os = to_outp(&mb.shallow_out);
     a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
     a.stream = nullptr;
+    cvg::fill_q(a);
     off[m] = (int)total;
     total += a.n;
     if (a.L.pver > max_pver) max_pver = a.L.pver;

@@ -37,12 +37,31 @@ struct RunArgs {
   conv_deep_params dp;
   conv_shallow_params sp;
   double dt;
+  // working-precision copies (fill_q, on the host)
+  DeepQ<float> dqf;
+  DeepQ<double> dqd;
+  ShalQ<float> sqf;
+  ShalQ<double> sqd;
   OutP od, os;
   int mode;
   int block;
   cudaStream_t stream;
   cudaEvent_t ev[3];  // optional stage events (nullptr = none)
 };
+
+// Fill the working-precision parameter copies from dp, sp and dt (host).
+inline void fill_q(RunArgs& a) {
+  a.dqf = make_deep_q<float>(a.dp, a.dt);
+  a.dqd = make_deep_q<double>(a.dp, a.dt);
+  a.sqf = make_shal_q<float>(a.sp);
+  a.sqd = make_shal_q<double>(a.sp);
+}
+__device__ __forceinline__ const DeepQ<float>& deep_q(const RunArgs& a, float) { return a.dqf; }
+__device__ __forceinline__ const DeepQ<double>& deep_q(const RunArgs& a, double) { return a.dqd; }
+__device__ __forceinline__ const ShalQ<float>& shal_q(const RunArgs& a, float) { return a.sqf; }
+__device__ __forceinline__ const ShalQ<double>& shal_q(const RunArgs& a, double) {
+  return a.sqd;
+}
 
 inline void record_stage(const RunArgs& a, int i) {
   if (a.ev[i]) cudaEventRecord(a.ev[i], a.stream);

@@ -30,9 +30,10 @@ __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
   bool bound_ok = false;
   if (a.mode & MODE_DEEP) {
     DeepOut o;
-    const R lam = (R)(a.lam ? a.lam[i] : a.dp.lambda_default);
-    const R tau = (R)(a.tau ? a.tau[i] : a.dp.tau_default);
-    deep_column(a.dp, a.dt, lam, tau, c, o, out_col<R>(a.od, a, i), &bound, &bound_ok);
+    const DeepQ<R>& Q = deep_q(a, R(0));
+    const R lam = a.lam ? (R)a.lam[i] : Q.lambda_default;
+    const R tau = a.tau ? (R)a.tau[i] : Q.tau_default;
+    deep_column(a.dp, Q, lam, tau, c, o, out_col<R>(a.od, a, i), &bound, &bound_ok);
     store_deep_scalars(a, i, o);
     // the limiter keeps q >= q_min up to rounding; a rejected column passes
     // unchanged.  A column that did not trigger has zero tendencies: the shallow
@@ -42,7 +43,8 @@ __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
   }
   if (a.mode & MODE_SHALLOW) {
     ShalOut o;
-    shallow_column(a.sp, c, o, out_col<R>(a.os, a, i), (const ShallowSeed<R>*)nullptr, false,
+    shallow_column(a.sp, shal_q(a, R(0)), c, o, out_col<R>(a.os, a, i),
+                   (const ShallowSeed<R>*)nullptr, false,
                    bound_ok ? &bound : nullptr);
     store_shallow_scalars(a, i, o);
   }
