@@ -386,6 +386,9 @@ def ours_arm(args, rank, world, local_rank):
                                              n, r)
         kernels["k_trigger"]["share"] = kt / (kt + kp)
         kernels["k_plume"]["share"] = kp / (kt + kp)
+    traffic = ncu_traffic(g.name)
+    for k in kernels:
+        kernels[k]["traffic"] = traffic.get(k)
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     roof = dict(kernels[dom])
     roof["kernel"] = dom
@@ -517,6 +520,42 @@ def l2_note(prec, n, pver):
         return f"profile inputs ({mb:.0f} MB) larger than the 129 MB L2; no flush"
     return (f"profile inputs ({mb:.0f} MB) fit in L2: timings of this small case are not "
             f"HBM-representative")
+
+
+def kernel_sources_sha256():
+    """Digest of the CUDA sources, to match an ncu capture to the kernels it measured."""
+    import hashlib
+    h = hashlib.sha256()
+    for d in (os.path.join(ROOT, "paper_1711_00289_gb300", "csrc"), os.path.join(ROOT, "include")):
+        for name in sorted(os.listdir(d)):
+            if name.endswith((".cu", ".cuh", ".h")):
+                h.update(name.encode())
+                with open(os.path.join(d, name), "rb") as fh:
+                    h.update(fh.read())
+    return h.hexdigest()
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
+    kernel from the ncu capture summarised under profiles/, if it was taken of
+    these sources on this workload; otherwise {} (traffic is then reported null).
+    Records are lines `traffic-record: sha256=<digest> workload=<name>
+    <kernel>=<bytes> ...`."""
+    d = os.path.join(ROOT, "profiles")
+    want = kernel_sources_sha256()
+    out = {}
+    for name in sorted(os.listdir(d)) if os.path.isdir(d) else []:
+        if not name.endswith(".md"):
+            continue
+        with open(os.path.join(d, name)) as fh:
+            for line in fh:
+                if not line.startswith("traffic-record:"):
+                    continue
+                f = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+                if f.get("sha256") == want and f.get("workload") == workload:
+                    out.update({k: float(v) for k, v in f.items()
+                                if k not in ("sha256", "workload")})
+    return out
 
 
 def measured_hbm():
