@@ -59,13 +59,13 @@ __device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P,
   tp.active = false;
   DeepTrig<double> t;
   if (column_valid(c)) {
-    double hs[MAXL];
-    prologue(Q.p_top_lim, c, hs);
+    prologue(Q.p_top_lim, c);
     deep_trigger(c, P, Q, t);
     if (t.triggered) {
       DeepOut o;
       o.flags = 0;
-      deep_plume<double, DeepTape<double>>(c, hs, P, Q, lam, tau, t, o, NoOut<double>(), &tp);
+      deep_plume<double, DeepTape<double>>(c, P, Q, lam, tau, t, t.Tp, 1, o, NoOut<double>(),
+                                           &tp);
     }
   }
   if (!tp.active) return;

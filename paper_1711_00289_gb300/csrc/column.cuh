@@ -551,6 +551,11 @@ struct Column {
     if constexpr (ColCache<R>::on) return cc.h[k];
     else return mse(T(k), q(k), zm[k], Tref, qref);
   }
+  // saturation moist static energy h*
+  __device__ __forceinline__ R hs(int k) const {
+    const R Tk = T(k);
+    return mse(Tk, sat_qs(Tk, pm(k)), zm[k], Tref, qref);
+  }
   // layer depth z_int,k - z_int,k+1 = (Rd Tv / g) ln(p_k+1/p_k)
   __device__ __forceinline__ R dz(int k) const { return R(RD / GRAV) * Tv(k) * dl[k]; }
 };
@@ -580,10 +585,9 @@ __device__ __forceinline__ bool column_valid(const Column<R>& c) {
   return ok;
 }
 
-// Heights, log-thicknesses, top limit and (when hs != nullptr) saturation moist
-// static energies (shared by both schemes).
+// Heights, log-thicknesses and top limit (shared by both schemes).
 template <class R>
-__device__ __forceinline__ void prologue(R ptl, Column<R>& c, R* hs) {
+__device__ __forceinline__ void prologue(R ptl, Column<R>& c) {
   const auto P = c.press();
   const int pver = c.pver;
   R pi_lo = P.pi(pver);
@@ -614,7 +618,6 @@ __device__ __forceinline__ void prologue(R ptl, Column<R>& c, R* hs) {
       c.cc.Tv[k] = tv;
       c.cc.h[k] = mse(Tk, qk, zm, c.Tref, c.qref);
     }
-    if (hs) hs[k] = mse(Tk, sat_qs(Tk, pm), zm, c.Tref, c.qref);
     if (pm >= ptl) ktl = k;
     pi_lo = pi_hi;
   }
@@ -820,17 +823,26 @@ struct DeepTape {
 // (deep "stage B": the entrainment and precipitation loops of Alg. 2).  hs: the
 // column's saturation MSE; writes every level of `out`.
 template <class R, class TP = NoTape, class OUT = OutCol<R>>
-__device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
-                                           const conv_deep_params& P, const DeepQ<R>& Q, R lam,
-                                           R tau, DeepTrig<R>& t, DeepOut& o, const OUT& out,
+__device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_params& P,
+                                           const DeepQ<R>& Q, R lam, R tau, DeepTrig<R>& t,
+                                           const R* Tp, size_t tps, DeepOut& o, const OUT& out,
                                            TP* tape = nullptr) {
   if constexpr (TP::kOn) tape->active = false;
   const int pver = c.pver, ktl = c.ktl, kb = t.kb, klcl = t.klcl, kel = t.kel;
   const R ze = Q.ent_zscale;
-  // minimum h* layer above the LCL (ties: lowest)
+  // minimum h* layer above the LCL (ties: lowest); am[k] = argmin of h* over
+  // layers k .. klcl-1, which at k = cloud top + 1 is the downdraft start
+  int8_t am[MAXL];
   int khmin = -1;
-  for (int k = klcl - 1; k >= ktl; --k)
-    if (khmin < 0 || hs[k] < hs[khmin]) khmin = k;
+  R hsmin = R(0);
+  for (int k = klcl - 1; k >= ktl; --k) {
+    const R v = c.hs(k);
+    if (khmin < 0 || v < hsmin) {
+      khmin = k;
+      hsmin = v;
+    }
+    am[k] = (int8_t)khmin;
+  }
   R eta[MAXL];
   eta[kb] = R(1);
   R hu1 = c.h(kb), qtu1 = c.q(kb);  // updraft MSE and total water at level k+1
@@ -851,7 +863,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
     const R re = Mth<R>::dv(R(1), e);
     const R hu = (eta[k + 1] * hu1 + de * c.h(k)) * re;
     if constexpr (TP::kOn) tape->hu[k] = hu;
-    if ((k <= khmin && hu <= hs[k]) || k == ktl) {
+    if ((k <= khmin && hu <= c.hs(k)) || k == ktl) {
       jt = k;
       break;
     }
@@ -883,9 +895,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
   }
 
   // downdraft start: minimum h* strictly between cloud top and LCL (ties: lowest)
-  int jd = -1;
-  for (int k = klcl - 1; k > jt; --k)
-    if (jd < 0 || hs[k] < hs[jd]) jd = k;
+  const int jd = jt + 1 <= klcl - 1 ? am[jt + 1] : -1;
   R etad[MAXL];
   R hd1 = R(0), qd1 = R(0);  // downdraft MSE and humidity at the level above
   R sumE = R(0), alpha = R(0);
@@ -918,12 +928,27 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
     if constexpr (TP::kOn) tape->capped = capped;
   }
 
-  // unit tendencies (per M_b) in flux form; dT, dq are zero outside jt..kb
-  // (the closure reads them on k_el..klcl, which may reach above the cloud top)
+  // unit tendencies (per M_b) in flux form, from the launch layer up; dT, dq are
+  // zero outside jt..kb.  The same pass accumulates the closure's F (the
+  // parcel-fixed dCAPE/dM_b, summed from the LCL up as on k_el..klcl) and finds
+  // the limiter's bound min (q - q_min)/(-dt dq) (first layer from the top
+  // on ties).
   R dT[MAXL], dq[MAXL];
-  R dhkb = R(0);
-  for (int k = 0; k < pver; ++k) dT[k] = dq[k] = R(0);
-  for (int k = jt; k <= kb; ++k) {
+  for (int k = 0; k < jt; ++k) dT[k] = dq[k] = R(0);
+  for (int k = kb + 1; k < pver; ++k) dT[k] = dq[k] = R(0);
+  R dhkb = R(0), F = R(0), mlmin = R(0);
+  int kml = -1;
+  const R qmin = Q.q_min, mdt = -Q.dt;
+  auto f_term = [&](int k, R dTk, R dqk) {
+    R qsp, dqsp, rD;
+    const R Tpk = Tp[(size_t)k * tps];
+    sat_qs_dqs(Tpk, c.pm(k), qsp, dqsp, rD);
+    const R dTvp = Mth<R>::dv((R(1) + R(ZVIR) * qsp) + R(ZVIR) * Tpk * dqsp,
+                              R(CP) + R(LV) * dqsp);
+    const R dTv = (R(1) + R(ZVIR) * c.q(k)) * dTk + R(ZVIR) * c.T(k) * dqk;
+    F += R(RD) * c.dl[k] * (dTvp * dhkb - dTv);
+  };
+  for (int k = kb; k >= jt; --k) {
     const R hk = c.h(k), qk = c.q(k);
     R dh, dqk;
     if (k == jt) {
@@ -947,41 +972,30 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const R* hs,
     const R rm = Mth<R>::dv(R(1), c.m(k));
     dh *= rm;
     dqk *= rm;
+    const R dTk = (dh - R(LV) * dqk) * R(1.0 / CP);
     dq[k] = dqk;
-    dT[k] = (dh - R(LV) * dqk) * R(1.0 / CP);
+    dT[k] = dTk;
     if (k == kb) dhkb = dh;
     if constexpr (TP::kOn) tape->dh[k] = dh;
+    if (k <= klcl && k >= kel) f_term(k, dTk, dqk);
+    if (dqk < R(0)) {
+      const R ml = Mth<R>::dv(qk - qmin, mdt * dqk);
+      if (kml < 0 || ml <= mlmin) {
+        mlmin = ml;
+        kml = k;
+      }
+    }
   }
-
-  // closure
-  R F = R(0);
-  for (int k = klcl; k >= kel; --k) {
-    R qsp, dqsp, rD;
-    const R pm = c.pm(k);
-    sat_qs_dqs(t.Tp[k], pm, qsp, dqsp, rD);
-    const R dTvp = Mth<R>::dv((R(1) + R(ZVIR) * qsp) + R(ZVIR) * t.Tp[k] * dqsp,
-                              R(CP) + R(LV) * dqsp);
-    const R dTv = (R(1) + R(ZVIR) * c.q(k)) * dT[k] + R(ZVIR) * c.T(k) * dq[k];
-    F += R(RD) * c.dl[k] * (dTvp * dhkb - dTv);
-  }
+  // closure terms above the cloud top (dT = dq = 0 there)
+  for (int k = (jt - 1 < klcl ? jt - 1 : klcl); k >= kel; --k) f_term(k, R(0), R(0));
   if (!(F < R(0))) {
     out.zero(0, pver);
     return;
   }
   R mb = Mth<R>::dv((R)(-t.cape), tau * F);
-  bool limited = false;
-  int kstar = -1;
-  const R qmin = Q.q_min, mdt = -Q.dt;
-  for (int k = jt; k <= kb; ++k) {
-    if (dq[k] < R(0)) {
-      const R ml = Mth<R>::dv(c.q(k) - qmin, mdt * dq[k]);
-      if (ml < mb) {
-        mb = ml;
-        limited = true;
-        kstar = k;
-      }
-    }
-  }
+  const bool limited = kml >= 0 && mlmin < mb;
+  const int kstar = limited ? kml : -1;
+  if (limited) mb = mlmin;
   if (!(mb > R(0))) {
     out.zero(0, pver);
     return;
@@ -1049,8 +1063,7 @@ __device__ __forceinline__ void deep_column(const conv_deep_params& P, const Dee
     out.zero(0, c.pver);
     return;
   }
-  R hs[MAXL];
-  prologue(Q.p_top_lim, c, hs);
+  prologue(Q.p_top_lim, c);
   DeepTrig<R> t;
   deep_trigger(c, P, Q, t);
   o.kb = t.kb;
@@ -1058,7 +1071,7 @@ __device__ __forceinline__ void deep_column(const conv_deep_params& P, const Dee
   o.cape = t.cape;
   if (t.triggered) {
     o.flags |= CONV_FLAG_TRIGGERED;
-    deep_plume(c, hs, P, Q, lam, tau, t, o, out);
+    deep_plume(c, P, Q, lam, tau, t, t.Tp, 1, o, out);
   } else {
     out.zero(0, c.pver);
     if (bound && t.newton <= Mth<R>::newton_tol) {
@@ -1151,7 +1164,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
       out.zero(0, pver);
       return;
     }
-    prologue(Q.p_top_lim, c, (R*)nullptr);
+    prologue(Q.p_top_lim, c);
   }
   const int ks = pver - 1, ktl = c.ktl;
   float newton = 0.f;

@@ -38,7 +38,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     if (!valid) {
       o.flags = CONV_FLAG_BADINPUT;
     } else {
-      prologue(deep_q(a, R(0)).p_top_lim, c, (R*)nullptr);  // h* only in the plume pass
+      prologue(deep_q(a, R(0)).p_top_lim, c);
       deep_trigger(c, a.dp, deep_q(a, R(0)), t);
       o.kb = t.kb;
       o.klcl = t.klcl;
@@ -81,7 +81,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
                           a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
     const DeepBound bound{t.klcl, c.ktl, t.maybe_buoy};
     const bool bound_ok = t.newton <= Mth<R>::newton_tol;
-    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(shal_q(a, R(0)).p_top_lim, c, (R*)nullptr);
+    if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(shal_q(a, R(0)).p_top_lim, c);
     ShallowSeed<R> seed{t.pL, t.klcl, t.pL_exact, t.Tp};
     shallow_column(a.sp, shal_q(a, R(0)), c, s, so, same_src ? &seed : nullptr, true,
                    bound_ok ? &bound : nullptr);
@@ -110,7 +110,6 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   t.cape = w.cape[slot];
   t.triggered = true;
   t.newton = 0.f;
-  for (int k = t.kel; k <= t.klcl; ++k) t.Tp[k] = w.Tp[(size_t)k * w.cap + slot];
   DeepOut o;
   o.prec = o.mb = o.cons = 0.0;
   o.cape = t.cape;
@@ -121,11 +120,8 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   const DeepQ<R>& Q = deep_q(a, R(0));
   const R lam = a.lam ? (R)a.lam[i] : Q.lambda_default;
   const R tau = a.tau ? (R)a.tau[i] : Q.tau_default;
-  {
-    R hs[MAXL];
-    prologue(Q.p_top_lim, c, hs);
-    deep_plume(c, hs, a.dp, Q, lam, tau, t, o, out_col<R>(a.od, a, i));
-  }
+  prologue(Q.p_top_lim, c);
+  deep_plume(c, a.dp, Q, lam, tau, t, w.Tp + slot, (size_t)w.cap, o, out_col<R>(a.od, a, i));
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
