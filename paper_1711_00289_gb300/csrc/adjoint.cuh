@@ -57,15 +57,17 @@ __device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P,
   blam = btau = Pv = Hv = 0.0;
   DeepTape<double> tp;
   tp.active = false;
+  double Tpa[MAXL];
   DeepTrig<double> t;
+  t.Tp = Tpa;
+  t.tps = 1;
   if (column_valid(c)) {
     prologue(Q.p_top_lim, c);
     deep_trigger(c, P, Q, t);
     if (t.triggered) {
       DeepOut o;
       o.flags = 0;
-      deep_plume<double, DeepTape<double>>(c, P, Q, lam, tau, t, t.Tp, 1, o, NoOut<double>(),
-                                           &tp);
+      deep_plume<double, DeepTape<double>>(c, P, Q, lam, tau, t, o, NoOut<double>(), &tp);
     }
   }
   if (!tp.active) return;

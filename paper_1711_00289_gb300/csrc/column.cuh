@@ -725,7 +725,8 @@ struct DeepTrig {
   bool triggered;
   float newton;
   uint32_t maybe_buoy;  // bit k: parcel buoyancy > -kBuoyMargin at layer k (klcl..ktl)
-  R Tp[MAXL];
+  R* Tp;                // parcel temperature of layer k at Tp[k * tps] (caller's storage)
+  size_t tps;
 };
 
 // Margin (K) of the buoyancy bound the shallow scheme takes from the deep
@@ -748,7 +749,7 @@ struct DeepBound {
 };
 
 // Launch level, LCL, undilute parcel, CAPE and trigger (deep "stage A").
-// t.Tp holds the parcel temperature on ktl..klcl whenever klcl >= ktl.
+// Writes the parcel temperature on ktl..klcl to t.Tp whenever klcl >= ktl.
 template <class R>
 __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep_params& P,
                                              const DeepQ<R>& Q, DeepTrig<R>& t) {
@@ -785,7 +786,7 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
     const R pm = c.pm(k), Tk = c.T(k);
     const R Tp =
         moist_invert(hb, R(GRAV) * c.zm[k], pm, Tk, P.n_newton_h, seq, t.newton, c.Tref, c.qref);
-    t.Tp[k] = Tp;
+    t.Tp[(size_t)k * t.tps] = Tp;
     const R b = virt(Tp, sat_qs(Tp, pm)) - virt(Tk, c.q(k));
     run.add(R(RD) * b * c.dl[k]);
     if (b > R(-kBuoyMargin)) t.maybe_buoy |= 1u << k;
@@ -825,8 +826,7 @@ struct DeepTape {
 template <class R, class TP = NoTape, class OUT = OutCol<R>>
 __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_params& P,
                                            const DeepQ<R>& Q, R lam, R tau, DeepTrig<R>& t,
-                                           const R* Tp, size_t tps, DeepOut& o, const OUT& out,
-                                           TP* tape = nullptr) {
+                                           DeepOut& o, const OUT& out, TP* tape = nullptr) {
   if constexpr (TP::kOn) tape->active = false;
   const int pver = c.pver, ktl = c.ktl, kb = t.kb, klcl = t.klcl, kel = t.kel;
   const R ze = Q.ent_zscale;
@@ -941,7 +941,7 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   const R qmin = Q.q_min, mdt = -Q.dt;
   auto f_term = [&](int k, R dTk, R dqk) {
     R qsp, dqsp, rD;
-    const R Tpk = Tp[(size_t)k * tps];
+    const R Tpk = t.Tp[(size_t)k * t.tps];
     sat_qs_dqs(Tpk, c.pm(k), qsp, dqsp, rD);
     const R dTvp = Mth<R>::dv((R(1) + R(ZVIR) * qsp) + R(ZVIR) * Tpk * dqsp,
                               R(CP) + R(LV) * dqsp);
@@ -1064,14 +1064,17 @@ __device__ __forceinline__ void deep_column(const conv_deep_params& P, const Dee
     return;
   }
   prologue(Q.p_top_lim, c);
+  R Tp[MAXL];
   DeepTrig<R> t;
+  t.Tp = Tp;
+  t.tps = 1;
   deep_trigger(c, P, Q, t);
   o.kb = t.kb;
   o.klcl = t.klcl;
   o.cape = t.cape;
   if (t.triggered) {
     o.flags |= CONV_FLAG_TRIGGERED;
-    deep_plume(c, P, Q, lam, tau, t, t.Tp, 1, o, out);
+    deep_plume(c, P, Q, lam, tau, t, o, out);
   } else {
     out.zero(0, c.pver);
     if (bound && t.newton <= Mth<R>::newton_tol) {
@@ -1096,7 +1099,8 @@ struct ShallowSeed {
   double pL;
   int klcl;
   bool pL_exact;  // pL is FP64 (see lcl_solve); else checked against p_lcl_min here
-  const R* Tp;    // parcel temperature on ktl..klcl
+  const R* Tp;    // parcel temperature of layer k (ktl..klcl) at Tp[k * tps]
+  size_t tps;
 };
 
 // Upper bound on the saturated parcel's buoyancy at layer k, below -kBuoyMargin?
@@ -1210,7 +1214,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
         Tp = Tsrc * Mth<R>::pw(Mth<R>::dv(pm, psrc), R(KAPPA));
         qp = qsrc;
       } else {
-        Tp = seed ? seed->Tp[k]
+        Tp = seed ? seed->Tp[(size_t)k * seed->tps]
                   : moist_invert(hsrc, R(GRAV) * c.zm[k], pm, c.T(k), P.n_newton_h, seq,
                                  newton, c.Tref, c.qref);
         qp = sat_qs(Tp, pm);

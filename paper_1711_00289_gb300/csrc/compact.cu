@@ -28,6 +28,8 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
   DeepOut o;
   DeepTrig<R> t;
   t.triggered = false;
+  t.Tp = w.Tp + tag;  // parcel temperatures go straight to the workspace, by column
+  t.tps = (size_t)w.cap;
   bool valid = false;
   if (live) {
     init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
@@ -62,7 +64,6 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     w.queue[slot] = tag;
     w.levels[slot] = t.kb | (t.klcl << 8) | (t.kel << 16);
     w.cape[slot] = t.cape;
-    for (int k = t.kel; k <= t.klcl; ++k) w.Tp[(size_t)k * w.cap + slot] = t.Tp[k];
     store_deep_scalars(a, i, o);  // scalars now; tendencies and the rest in the plume pass
     return;
   }
@@ -82,7 +83,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     const DeepBound bound{t.klcl, c.ktl, t.maybe_buoy};
     const bool bound_ok = t.newton <= Mth<R>::newton_tol;
     if (a.sp.p_top_lim != a.dp.p_top_lim) prologue(shal_q(a, R(0)).p_top_lim, c);
-    ShallowSeed<R> seed{t.pL, t.klcl, t.pL_exact, t.Tp};
+    ShallowSeed<R> seed{t.pL, t.klcl, t.pL_exact, t.Tp, t.tps};
     shallow_column(a.sp, shal_q(a, R(0)), c, s, so, same_src ? &seed : nullptr, true,
                    bound_ok ? &bound : nullptr);
   }
@@ -96,10 +97,11 @@ __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::trigger / kCompac
   trigger_body(a, w, i, i < a.n, i);
 }
 
-// Plume pass of the column in queue slot `slot` (column i of member a).
+// Plume pass of the column in queue slot `slot`: column i of member a, queued
+// under `tag` (its index in the workspace's per-column arrays).
 template <class R>
 __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>& w, int slot,
-                                           int i) {
+                                           int i, int tag) {
   Column<R> c;
   init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
   DeepTrig<R> t;
@@ -110,6 +112,8 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   t.cape = w.cape[slot];
   t.triggered = true;
   t.newton = 0.f;
+  t.Tp = w.Tp + tag;
+  t.tps = (size_t)w.cap;
   DeepOut o;
   o.prec = o.mb = o.cons = 0.0;
   o.cape = t.cape;
@@ -121,7 +125,7 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   const R lam = a.lam ? (R)a.lam[i] : Q.lambda_default;
   const R tau = a.tau ? (R)a.tau[i] : Q.tau_default;
   prologue(Q.p_top_lim, c);
-  deep_plume(c, a.dp, Q, lam, tau, t, w.Tp + slot, (size_t)w.cap, o, out_col<R>(a.od, a, i));
+  deep_plume(c, a.dp, Q, lam, tau, t, o, out_col<R>(a.od, a, i));
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
@@ -136,7 +140,8 @@ __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactB
     k_plume(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= *w.count) return;
-  plume_body(a, w, slot, w.queue[slot]);
+  const int i = w.queue[slot];
+  plume_body(a, w, slot, i, i);
 }
 
 size_t compact_workspace_bytes(int n, int pver, bool fp64) {
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
   for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
     const int g = w.queue[slot];
     const int m = find_member(b.offsets, b.n_members, g);
-    plume_body(b.members[m], w, slot, g - b.offsets[m]);
+    plume_body(b.members[m], w, slot, g - b.offsets[m], g);
   }
 }
 

@@ -28,7 +28,8 @@ struct SmThreads<float> {
 //   queue  int32[n]   column index of each queued (deep-triggered) column
 //   levels int32[n]   kb | klcl << 8 | kel << 16 of the queued column
 //   cape   double[n]  CAPE of the queued column
-//   Tp     R[pver][n] undilute parcel temperature on kel..klcl, by queue slot
+//   Tp     R[pver][n] undilute parcel temperature on ktl..klcl, by column (the
+//                     trigger pass writes it for every column with a parcel)
 // (n = queue capacity: the columns of the run, or of all members of a batch)
 template <class R>
 struct CompactWs {
