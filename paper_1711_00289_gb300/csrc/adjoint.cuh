@@ -61,8 +61,7 @@ __device__ __forceinline__ void deep_adjoint_column(const conv_deep_params& P,
   DeepTrig<double> t;
   t.Tp = Tpa;
   t.tps = 1;
-  if (column_valid(c)) {
-    prologue(Q.p_top_lim, c);
+  if (prologue(Q.p_top_lim, c)) {
     deep_trigger(c, P, Q, t);
     if (t.triggered) {
       DeepOut o;

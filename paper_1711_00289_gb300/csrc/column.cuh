@@ -179,9 +179,11 @@ struct MoistSeq {
 };
 
 // h is relative to the column reference cp Tref + Lv qref (see Column).
+// qsol (optional): qs at the solution, qs - dqs * step from the last iterate
+// (the second-order remainder is ~1e-15 relative once converged).
 template <class R>
 __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, MoistSeq<R>& s,
-                                          float& newton, R Tref, R qref) {
+                                          float& newton, R Tref, R qref, R* qsol = nullptr) {
   R T;
   int steps;
   if (Mth<R>::warm && s.have) {
@@ -209,6 +211,7 @@ __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, Mois
   s.gz = gz;
   s.h = h;
   newton = fmaxf(newton, Mth<R>::left(step));
+  if (qsol) *qsol = qs - dqs * step;
   return T;
 }
 
@@ -577,17 +580,12 @@ __device__ __forceinline__ bool in_range(float T, float q) {
   return (T > 100.f && T < 400.f) && (q >= 0.f && q < 0.1f);
 }
 
+// Heights, log-thicknesses and top limit (shared by both schemes), in the same
+// pass over the profile as the input check: returns false for a column whose
+// ps, T or q is out of range or not finite (CONV_FLAG_BADINPUT), whose derived
+// values are then meaningless and unused.
 template <class R>
-__device__ __forceinline__ bool column_valid(const Column<R>& c) {
-  if (!(c.ps > 5.0e4 && c.ps < 1.2e5)) return false;
-  bool ok = true;
-  for (int k = 0; k < c.pver; ++k) ok = ok && in_range(c.s.Tk(k), c.s.qk(k));
-  return ok;
-}
-
-// Heights, log-thicknesses and top limit (shared by both schemes).
-template <class R>
-__device__ __forceinline__ void prologue(R ptl, Column<R>& c) {
+__device__ __forceinline__ bool prologue(R ptl, Column<R>& c) {
   const auto P = c.press();
   const int pver = c.pver;
   R pi_lo = P.pi(pver);
@@ -601,10 +599,12 @@ __device__ __forceinline__ void prologue(R ptl, Column<R>& c) {
   c.Tref = Mth<R>::anomaly ? c.T(pver - 1) : R(0);
   c.qref = Mth<R>::anomaly ? c.q(pver - 1) : R(0);
   int ktl = pver - 1;
+  bool ok = c.ps > 5.0e4 && c.ps < 1.2e5;
   for (int k = pver - 1; k >= 0; --k) {
     const R pi_hi = P.pi(k);
     const R pm = P.mid(pi_lo, pi_hi);
     const R Tk = c.T(k), qk = c.q(k);
+    ok = ok && in_range(Tk, qk);
     const R tv = virt(Tk, qk);
     const R scale = R(RD / GRAV) * tv;
     const R dl = Mth<R>::lg(Mth<R>::dv(pi_lo, pi_hi));
@@ -622,6 +622,7 @@ __device__ __forceinline__ void prologue(R ptl, Column<R>& c) {
     pi_lo = pi_hi;
   }
   c.ktl = ktl;
+  return ok;
 }
 
 // Largest k <= kstart with p_mid[k] <= pL, or -1 (see cmp_bound).
@@ -784,10 +785,11 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   int kel = -1;
   for (int k = klcl; k >= ktl; --k) {
     const R pm = c.pm(k), Tk = c.T(k);
-    const R Tp =
-        moist_invert(hb, R(GRAV) * c.zm[k], pm, Tk, P.n_newton_h, seq, t.newton, c.Tref, c.qref);
+    R qsp;
+    const R Tp = moist_invert(hb, R(GRAV) * c.zm[k], pm, Tk, P.n_newton_h, seq, t.newton, c.Tref,
+                              c.qref, &qsp);
     t.Tp[(size_t)k * t.tps] = Tp;
-    const R b = virt(Tp, sat_qs(Tp, pm)) - virt(Tk, c.q(k));
+    const R b = virt(Tp, qsp) - virt(Tk, c.q(k));
     run.add(R(RD) * b * c.dl[k]);
     if (b > R(-kBuoyMargin)) t.maybe_buoy |= 1u << k;
     if (b > R(0)) {
@@ -1058,12 +1060,11 @@ __device__ __forceinline__ void deep_column(const conv_deep_params& P, const Dee
   o.flags = 0;
   o.kb = o.klcl = o.ktop = o.kaux = -1;
   if (bound_ok) *bound_ok = false;
-  if (!column_valid(c)) {
+  if (!prologue(Q.p_top_lim, c)) {
     o.flags = CONV_FLAG_BADINPUT;
     out.zero(0, c.pver);
     return;
   }
-  prologue(Q.p_top_lim, c);
   R Tp[MAXL];
   DeepTrig<R> t;
   t.Tp = Tp;
@@ -1162,13 +1163,10 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
   o.prec = o.cin = o.mb = o.cons = 0.0;
   o.flags = 0;
   o.klcl = o.ktop = o.klfc = -1;
-  if (!prologue_done) {
-    if (!column_valid(c)) {
-      o.flags = CONV_FLAG_BADINPUT;
-      out.zero(0, pver);
-      return;
-    }
-    prologue(Q.p_top_lim, c);
+  if (!prologue_done && !prologue(Q.p_top_lim, c)) {
+    o.flags = CONV_FLAG_BADINPUT;
+    out.zero(0, pver);
+    return;
   }
   const int ks = pver - 1, ktl = c.ktl;
   float newton = 0.f;

@@ -36,11 +36,10 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     o.prec = o.cape = o.mb = o.cons = 0.0;
     o.flags = 0;
     o.kb = o.klcl = o.ktop = o.kaux = -1;
-    valid = column_valid(c);
+    valid = prologue(deep_q(a, R(0)).p_top_lim, c);
     if (!valid) {
       o.flags = CONV_FLAG_BADINPUT;
     } else {
-      prologue(deep_q(a, R(0)).p_top_lim, c);
       deep_trigger(c, a.dp, deep_q(a, R(0)), t);
       o.kb = t.kb;
       o.klcl = t.klcl;
