@@ -9,18 +9,19 @@ constexpr int kCompactBlock = 128;
 
 // Resident threads per SM the compacted kernels are compiled for (register cap
 // 65536 / threads).  The mixed kernels are latency-bound chains of dependent
-// FP32 operations: more resident warps hide more of that latency, and a
-// measured sweep of the caps put the trigger pass at 1280 threads per SM (48
-// registers) and the plume pass at 1024 (64 registers).  The FP64 kernels are
-// bound by the FP64 pipe and need enough warps in flight to keep it fed: 896
-// threads (72 registers).
+// FP32 operations: more resident warps hide more of that latency, until the
+// spills of a tighter cap cost more.  Measured sweeps of the caps put the
+// trigger pass at 1408 threads per SM (40 registers; 1664 threads, 32
+// registers, was 21% slower) and the plume pass at 896 (72 registers; 768 was
+// 18% slower, 1024 2% slower).  The FP64 kernels are bound by the FP64 pipe and
+// need enough warps in flight to keep it fed: 896 threads (72 registers).
 template <class R>
 struct SmThreads {
   static constexpr int trigger = 896, plume = 896;
 };
 template <>
 struct SmThreads<float> {
-  static constexpr int trigger = 1280, plume = 1024;
+  static constexpr int trigger = 1408, plume = 896;
 };
 
 // Device workspace of the compacted path, carved from one caller buffer:
