@@ -990,6 +990,72 @@ int oracle_deep_adjoint(int n_cols, int pver, int ld, const double* hyai, const 
   return 0;
 }
 
+// Tangent of the fused step (deep convection, then shallow convection on the
+// deep-updated state with q floored at zero, as oracle_deep_shallow):
+//   J = gPd Pd + gHd Hd + gPs Ps + gHs Hs,  H = sum_k w_k m_k cp dT/dt_k of each
+// scheme (w = w_heat, or p_mid/ps), differentiated in forward mode with respect
+// to T, q, lambda and tau (Dual: 2 pver + 2 directions at once).
+int oracle_deep_shallow_adjoint(int n_cols, int pver, int ld, const double* hyai,
+                                const double* hybi, double p0, const double* T, const double* q,
+                                const double* ps, const double* lambda, const double* tau,
+                                const oracle_deep_params* dpar, const oracle_shallow_params* spar,
+                                double dt, const double* gPd, const double* gHd,
+                                const double* gPs, const double* gHs, const double* w_heat,
+                                double* gT, double* gq, double* glambda, double* gtau,
+                                int n_threads) {
+  if (!grid_ok(n_cols, pver, ld) || !dpar || !spar) return 1;
+  const DeepP DP = to_deep(dpar);
+  const ShalP SP = to_shal(spar);
+#pragma omp parallel for schedule(dynamic, 4) num_threads(threads_for(n_threads))
+  for (int i = 0; i < n_cols; ++i) {
+    Dual Tc[MAXLEV], qc[MAXLEV], T2[MAXLEV], q2[MAXLEV];
+    for (int k = 0; k < pver; ++k) {
+      Tc[k] = Dual(T[k * ld + i]);
+      Tc[k].d[k] = 1.0;
+      qc[k] = Dual(q[k * ld + i]);
+      qc[k].d[pver + k] = 1.0;
+    }
+    Dual lam(lambda ? lambda[i] : DP.lambda_default);
+    lam.d[2 * pver] = 1.0;
+    Dual ta(tau ? tau[i] : DP.tau_default);
+    ta.d[2 * pver + 1] = 1.0;
+    std::unique_ptr<DeepState<Dual>> sp(new DeepState<Dual>());
+    std::unique_ptr<ShalState<Dual>> tp(new ShalState<Dual>());
+    DeepState<Dual>& s = *sp;
+    ShalState<Dual>& t = *tp;
+    deep_column<Dual>(pver, hyai, hybi, p0, Tc, qc, Dual(ps[i]), lam, ta, DP, dt, s);
+    for (int k = 0; k < pver; ++k) {
+      T2[k] = Tc[k] + dt * s.dTdt[k];
+      q2[k] = qc[k] + dt * s.dqdt[k];
+      if (!s.bad && q2[k].v < 0.0) q2[k] = Dual(0.0);
+    }
+    shallow_column<Dual>(pver, hyai, hybi, p0, T2, q2, Dual(ps[i]), SP, t);
+    const double gpd = gPd ? gPd[i] : 0.0, ghd = gHd ? gHd[i] : 0.0;
+    const double gps = gPs ? gPs[i] : 0.0, ghs = gHs ? gHs[i] : 0.0;
+    Dual J = gpd * s.prec;
+    if (s.active) {
+      for (int k = 0; k < pver; ++k) {
+        const double w = w_heat ? w_heat[k] : s.p_mid[k].v / ps[i];
+        J = J + (ghd * w) * (s.m[k] * CP * s.dTdt[k]);
+      }
+    }
+    if (t.active) {
+      J = J + gps * t.prec;
+      for (int k = 0; k < pver; ++k) {
+        const double w = w_heat ? w_heat[k] : t.p_mid[k].v / ps[i];
+        J = J + (ghs * w) * (t.m[k] * CP * t.dT[k]);
+      }
+    }
+    for (int k = 0; k < pver; ++k) {
+      gT[k * ld + i] = J.d[k];
+      gq[k * ld + i] = J.d[pver + k];
+    }
+    glambda[i] = J.d[2 * pver];
+    gtau[i] = J.d[2 * pver + 1];
+  }
+  return 0;
+}
+
 int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const double* hybi,
                      double p0, const double* T, const double* q, const double* ps,
                      const oracle_deep_params* dpar, const oracle_shallow_params* spar,

@@ -113,6 +113,20 @@ int oracle_deep_adjoint(int n_cols, int pver, int ld, const double* hyai, const 
                         const double* gH, const double* w_heat, double* gT, double* gq,
                         double* glambda, double* gtau, int n_threads);
 
+/* Forward-mode tangent of the fused deep -> shallow step (shallow on the
+ * deep-updated state, q floored at 0): gradients of
+ *   J = gPd*Pd + gHd*sum w m cp dTdt_deep + gPs*Ps + gHs*sum w m cp dTdt_shallow
+ * (w = w_heat, or p_mid/ps) with respect to T, q ([pver][ld]), lambda, tau
+ * ([ld]).  Any of gPd, gHd, gPs, gHs may be NULL (zero). */
+int oracle_deep_shallow_adjoint(int n_cols, int pver, int ld, const double* hyai,
+                                const double* hybi, double p0, const double* T, const double* q,
+                                const double* ps, const double* lambda, const double* tau,
+                                const oracle_deep_params* dpar, const oracle_shallow_params* spar,
+                                double dt, const double* gPd, const double* gHd,
+                                const double* gPs, const double* gHs, const double* w_heat,
+                                double* gT, double* gq, double* glambda, double* gtau,
+                                int n_threads);
+
 /* Floating-point operation counts of the path, by category:
  * [0] add/sub, [1] mul, [2] div, [3] exp, [4] log, [5] pow, [6] sqrt, [7] unused.
  * counts_deep: the deep scheme alone; counts_total: deep + shallow; both summed

@@ -138,12 +138,15 @@ def lib():
                                           C.POINTER(Out), i]
         L.oracle_deep_adjoint.argtypes = [i, i, i, p, p, d, p, p, p, p, p, C.POINTER(DeepParams),
                                           d, p, p, p, p, p, p, p, i]
+        L.oracle_deep_shallow_adjoint.argtypes = [i, i, i, p, p, d, p, p, p, p, p,
+                                                  C.POINTER(DeepParams), C.POINTER(ShallowParams),
+                                                  d, p, p, p, p, p, p, p, p, p, i]
         L.oracle_count_ops.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                        C.POINTER(ShallowParams), d, p, p]
         L.oracle_count_ops_by_pass.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                                C.POINTER(ShallowParams), d, p, p, p]
         for fn in ("oracle_deep", "oracle_shallow", "oracle_deep_shallow", "oracle_deep_adjoint",
-                   "oracle_count_ops", "oracle_count_ops_by_pass"):
+                   "oracle_deep_shallow_adjoint", "oracle_count_ops", "oracle_count_ops_by_pass"):
             getattr(L, fn).restype = i
         _lib = L
     return _lib
@@ -241,6 +244,30 @@ def deep_adjoint(g, gP, gH, w_heat=None, par=None, dt=None, threads: int = 1, la
                                    _ptr(ps), _ptr(lam), _ptr(tau), C.byref(par), dt, _ptr(gP),
                                    _ptr(gH), _ptr(w), _ptr(gT), _ptr(gq), _ptr(gl), _ptr(gt),
                                    threads)
+    assert rc == 0
+    return gT, gq, gl, gt
+
+
+def deep_shallow_adjoint(g, gPd=None, gHd=None, gPs=None, gHs=None, w_heat=None, dpar=None,
+                         spar=None, dt=None, threads: int = 1, lam=None, tau=None):
+    """Tangent-mode gradients of J = gPd*Pd + gHd*Hd + gPs*Ps + gHs*Hs of the fused
+    deep -> shallow step, H = sum w m cp dTdt of each scheme."""
+    dpar = dpar or deep_params()
+    spar = spar or shallow_params()
+    dt = g.dt if dt is None else dt
+    n, pver = g.n_cols, g.pver
+    T, q, ps = _c64(g.T), _c64(g.q), _c64(g.ps)
+    lam = _c64(lam if lam is not None else g.lam)
+    tau = _c64(tau if tau is not None else g.tau)
+    seeds = [_c64(x) for x in (gPd, gHd, gPs, gHs)]
+    w = _c64(w_heat)
+    gT, gq = np.zeros((pver, n)), np.zeros((pver, n))
+    gl, gt = np.zeros(n), np.zeros(n)
+    hyai, hybi = _c64(g.hyai), _c64(g.hybi)
+    rc = lib().oracle_deep_shallow_adjoint(
+        n, pver, n, _ptr(hyai), _ptr(hybi), 1e5, _ptr(T), _ptr(q), _ptr(ps), _ptr(lam),
+        _ptr(tau), C.byref(dpar), C.byref(spar), dt, *[_ptr(x) for x in seeds], _ptr(w),
+        _ptr(gT), _ptr(gq), _ptr(gl), _ptr(gt), threads)
     assert rc == 0
     return gT, gq, gl, gt
 
