@@ -253,6 +253,33 @@ conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
                               double* gT, double* gq, double* glambda, double* gtau,
                               double* P_out, double* H_out, conv_stream stream);
 
+/* Adjoint of the fused step (no counterpart in the paper): deep convection,
+ * then shallow convection on T + dt*dTdt_deep, max(q + dt*dqdt_deep, 0), as
+ * conv_deep_shallow_run computes it.  Per column it evaluates
+ *   Pd, Hd, Ps, Hs   precipitation and H = sum_k w_k m_k cp dTdt_k of the deep
+ *                    and of the shallow scheme (w as for conv_deep_adjoint)
+ * into obj ([4][ld] DEVICE doubles: rows Pd, Hd, Ps, Hs; NULL = not wanted) and,
+ * when `gradient` is non-zero, the gradient of
+ *   J = gPd*Pd + gHd*Hd + gPs*Ps + gHs*Hs
+ * with respect to T, q (gT, gq: [pver][ld]), lambda and tau (glambda, gtau:
+ * [ld]).  gT and gq are required in both modes: they also hold the deep
+ * tendencies the shallow scheme reads.  gPd..gHs: DEVICE [ld] doubles or NULL
+ * (zero).  The gradient flows through the shallow scheme into its input state,
+ * and from there into T, q directly and through the deep tendencies (the q
+ * floor at zero passes no gradient where it binds).  Shallow level choices
+ * (LCL, LFC, cloud top), saturation and rain on/off are held, as the deep
+ * scheme's are in conv_deep_adjoint; the shallow closure is differentiated
+ * through CIN and the source density.  FP64 only; one thread per column
+ * recomputes both schemes with tapes; no workspace; asynchronous on `stream`. */
+conv_status conv_deep_shallow_adjoint(const conv_grid* grid, const conv_in* in,
+                                      const conv_deep_params* dpar,
+                                      const conv_shallow_params* spar, double dt,
+                                      conv_precision prec, const double* gPd, const double* gHd,
+                                      const double* gPs, const double* gHs,
+                                      const double* w_heat, double* gT, double* gq,
+                                      double* glambda, double* gtau, double* obj, int gradient,
+                                      conv_stream stream);
+
 /* ------------------------------------------------------------------ batches
  * Many grids / ensemble members of uneven column counts and level counts in one
  * trigger launch over all their columns and one persistent launch over a common

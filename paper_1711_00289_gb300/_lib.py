@@ -122,6 +122,10 @@ def lib(build: bool = True):
     L.conv_deep_adjoint.argtypes = [P(Grid), P(In), P(DeepParams), d, st, vp, vp,
                                     P(C.c_double), vp, vp, vp, vp, vp, vp, vp]
     L.conv_deep_adjoint.restype = st
+    L.conv_deep_shallow_adjoint.argtypes = [P(Grid), P(In), P(DeepParams), P(ShallowParams), d,
+                                            st, vp, vp, vp, vp, P(C.c_double), vp, vp, vp, vp,
+                                            vp, st, vp]
+    L.conv_deep_shallow_adjoint.restype = st
     _lib = L
     return L
 

@@ -373,3 +373,92 @@ def deep_precip_heating(T, q, ps, vgrid: VerticalGrid, *, lam=None, tau=None,
                         dt: float = 1800.0, params=None, w_heat=None):
     """(P, H) of the deep scheme per column, differentiable w.r.t. T, q, lam, tau."""
     return DeepConvection.apply(T, q, lam, tau, ps, vgrid, dt, params, w_heat)
+
+
+def deep_shallow_adjoint(T, q, ps, vgrid: VerticalGrid, *, gPd=None, gHd=None, gPs=None,
+                         gHs=None, w_heat=None, dt: float = 1800.0, lam=None, tau=None,
+                         deep_params=None, shallow_params=None, n_cols=None, gradient=True,
+                         objective=False, stream=None):
+    """Fused-step objective and/or adjoint (FP64, conv_deep_shallow_adjoint).
+
+    Per column: Pd, Hd, Ps, Hs (precipitation and H = sum_k w_k m_k cp dTdt_k of
+    the deep and of the shallow scheme, the shallow scheme run on the
+    deep-updated state), and the gradient of J = gPd Pd + gHd Hd + gPs Ps + gHs Hs
+    with respect to T, q ([pver, ld]), lambda and tau ([ld]).  Returns a dict
+    with gT, gq, glambda, gtau (if ``gradient``) and obj ([4, ld] rows Pd, Hd, Ps,
+    Hs; if ``objective``)."""
+    if not (gradient or objective):
+        raise ValueError("nothing requested")
+    pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, "fp64", lam, tau)
+    f64 = torch.float64
+    seeds = (gPd, gHd, gPs, gHs)
+    for name, t in zip(("gPd", "gHd", "gPs", "gHs"), seeds):
+        if t is not None:
+            _require_cuda(t, name, f64, (ld,))
+    w = None
+    if w_heat is not None:
+        wa = np.ascontiguousarray(w_heat, dtype=np.float64)
+        if wa.shape != (pver,):
+            raise ValueError(f"w_heat must have {pver} entries")
+        w = wa.ctypes.data_as(C.POINTER(C.c_double))
+    res = dict(gT=torch.empty((pver, ld), dtype=f64, device=T.device),
+               gq=torch.empty((pver, ld), dtype=f64, device=T.device))
+    if gradient:
+        res["glambda"] = torch.empty(ld, dtype=f64, device=T.device)
+        res["gtau"] = torch.empty(ld, dtype=f64, device=T.device)
+    if objective:
+        res["obj"] = torch.empty((4, ld), dtype=f64, device=T.device)
+    dp = deep_params or L.deep_defaults()
+    sp = shallow_params or L.shallow_defaults()
+    g = vgrid.struct(n, ld)
+    st = L.lib().conv_deep_shallow_adjoint(
+        C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp), float(dt), L.CONV_FP64,
+        *[_ptr(x) for x in seeds], w, _ptr(res["gT"]), _ptr(res["gq"]),
+        _ptr(res.get("glambda")), _ptr(res.get("gtau")), _ptr(res.get("obj")),
+        1 if gradient else 0, _stream(stream))
+    L.check(st, "conv_deep_shallow_adjoint")
+    if not gradient:
+        del res["gT"], res["gq"]
+    return res
+
+
+class DeepShallowStep(torch.autograd.Function):
+    """Differentiable fused step: (T, q, lam, tau) -> (Pd, Hd, Ps, Hs) per column
+    (deep scheme, then shallow scheme on the deep-updated state).  Forward and
+    backward both run in the library (conv_deep_shallow_adjoint); the backward
+    recomputes both schemes in its kernel.  lam / tau may be None."""
+
+    @staticmethod
+    def forward(ctx, T, q, lam, tau, ps, vgrid, dt, deep_params, shallow_params, w_heat):
+        ctx.save_for_backward(T, q, lam, tau, ps)
+        ctx.cfg = (vgrid, dt, deep_params, shallow_params, w_heat)
+        r = deep_shallow_adjoint(T.detach(), q.detach(), ps, vgrid, w_heat=w_heat, dt=dt,
+                                 lam=None if lam is None else lam.detach(),
+                                 tau=None if tau is None else tau.detach(),
+                                 deep_params=deep_params, shallow_params=shallow_params,
+                                 gradient=False, objective=True)
+        o = r["obj"]
+        return o[0].clone(), o[1].clone(), o[2].clone(), o[3].clone()
+
+    @staticmethod
+    def backward(ctx, gPd, gHd, gPs, gHs):
+        T, q, lam, tau, ps = ctx.saved_tensors
+        vgrid, dt, deep_params, shallow_params, w_heat = ctx.cfg
+        r = deep_shallow_adjoint(T.detach(), q.detach(), ps, vgrid, gPd=gPd.contiguous(),
+                                 gHd=gHd.contiguous(), gPs=gPs.contiguous(),
+                                 gHs=gHs.contiguous(), w_heat=w_heat, dt=dt,
+                                 lam=None if lam is None else lam.detach(),
+                                 tau=None if tau is None else tau.detach(),
+                                 deep_params=deep_params, shallow_params=shallow_params)
+        need = ctx.needs_input_grad
+        return (r["gT"] if need[0] else None, r["gq"] if need[1] else None,
+                r["glambda"] if need[2] else None, r["gtau"] if need[3] else None,
+                None, None, None, None, None, None)
+
+
+def deep_shallow_step(T, q, ps, vgrid: VerticalGrid, *, lam=None, tau=None, dt: float = 1800.0,
+                      deep_params=None, shallow_params=None, w_heat=None):
+    """(Pd, Hd, Ps, Hs) of the fused step per column, differentiable w.r.t. T, q,
+    lam, tau."""
+    return DeepShallowStep.apply(T, q, lam, tau, ps, vgrid, dt, deep_params, shallow_params,
+                                 w_heat)

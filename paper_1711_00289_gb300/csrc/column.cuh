@@ -1146,19 +1146,35 @@ __device__ __forceinline__ bool certainly_no_lfc(const Column<R>& c, const DeepB
   return true;
 }
 
+// Intermediate state of shallow_column, recorded only for the adjoint kernel.
+template <class R>
+struct ShalTape {
+  static constexpr bool kOn = true;
+  R Tp[MAXL], b[MAXL];                 // undilute parcel temperature and buoyancy
+  R hu[MAXL], qt[MAXL], qtu[MAXL];     // plume MSE, total water before / after rain
+  R Tsat[MAXL], r[MAXL], chi[MAXL];    // saturated temperature, rain, mixing
+  R dT[MAXL];                          // dT/dt output
+  bool sat[MAXL];
+  R mb, rho, sumr;
+  double cin;
+  int klcl, klfc, kts;
+  bool active;
+};
+
 // Whole shallow scheme for one column in c (Alg. 3); writes every level of out.
 // When `prologue_done` the column has been validated and its prologue computed
 // already.  The plume's tendencies go out level by level as the plume rises:
 // a level's is written once the level above has shown that the plume goes on,
 // the top layer's when the plume stops; a plume that dies at its LCL (exit E4)
 // overwrites what it wrote with zeros.
-template <class R>
+template <class R, class TP = NoTape, class OUT = OutCol<R>>
 __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, const ShalQ<R>& Q,
-                                               Column<R>& c,
-                                               ShalOut& o, const OutCol<R>& out,
+                                               Column<R>& c, ShalOut& o, const OUT& out,
                                                const ShallowSeed<R>* seed = nullptr,
                                                bool prologue_done = false,
-                                               const DeepBound* bound = nullptr) {
+                                               const DeepBound* bound = nullptr,
+                                               TP* tape = nullptr) {
+  if constexpr (TP::kOn) tape->active = false;
   const int pver = c.pver;
   o.prec = o.cin = o.mb = o.cons = 0.0;
   o.flags = 0;
@@ -1186,6 +1202,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
     klcl = lcl.klcl;
   }
   o.klcl = klcl;
+  if constexpr (TP::kOn) tape->klcl = klcl;
   int exit_code = 0;
   R mb = R(0);
   int klfc = -1, kts = -1;
@@ -1218,6 +1235,10 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
         qp = sat_qs(Tp, pm);
       }
       const R b = virt(Tp, qp) - c.Tv(k);
+      if constexpr (TP::kOn) {
+        tape->Tp[k] = Tp;
+        tape->b[k] = b;
+      }
       if (k <= klcl && b > R(0)) {
         klfc = k;
         break;
@@ -1235,6 +1256,13 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
       } else {
         const R rho = Mth<R>::dv(psrc, R(RD) * c.Tv(ks));
         mb = rho * Q.cm_sqrt_tke * Mth<R>::ex((R)cin * Q.m_inv_cin);
+        if constexpr (TP::kOn) {
+          tape->rho = rho;
+          tape->mb = mb;
+          tape->cin = cin;
+          tape->hu[ks] = hsrc;
+          tape->qtu[ks] = qsrc;
+        }
         // plume, with a two-level window: (hu2, qtu2) at k+2, (hu1, qtu1, qp1, rf1) at k+1
         const R hsrc_env = hsrc;
         R hu2 = R(0), qtu2 = R(0);
@@ -1246,6 +1274,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           const R dqk = dqv * rm;
           const R dTk = (dh * rm - R(LV) * dqk) * R(1.0 / CP);
           out.put(k, dTk, dqk);
+          if constexpr (TP::kOn) tape->dT[k] = dTk;
           const R mk = c.m(k);
           sea.add(mk * dTk);
           swa.add(mk * dqk);
@@ -1269,10 +1298,12 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           if (k >= klcl) {
             hu = hu1;
             qt = qtu1;
+            if constexpr (TP::kOn) tape->chi[k] = R(0);
           } else {
             const R chi = R(1) - Mth<R>::ex(-eps * dz);
             hu = hu1 + chi * (hk - hu1);
             qt = qtu1 + chi * (qk - qtu1);
+            if constexpr (TP::kOn) tape->chi[k] = chi;
           }
           const R pm = c.pm(k);
           const R Tk = c.T(k);
@@ -1280,6 +1311,12 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           const R Tsat = moist_invert(hu, gz, pm, Tk, P.n_newton_h, seq, newton, c.Tref, c.qref);
           const R qsu = sat_qs(Tsat, pm);
           R Tu, qv;
+          if constexpr (TP::kOn) {
+            tape->hu[k] = hu;
+            tape->qt[k] = qt;
+            tape->Tsat[k] = Tsat;
+            tape->sat[k] = qt >= qsu;
+          }
           if (qt >= qsu) {
             Tu = Tsat;
             qv = qsu;
@@ -1316,6 +1353,10 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           }
           R r = qt - qv - qlc;
           if (r < R(0)) r = R(0);
+          if constexpr (TP::kOn) {
+            tape->r[k] = r;
+            tape->qtu[k] = qt - r;
+          }
           // the plume goes on above k: level k+1 is a regular level
           if (k + 1 <= ks - 1) {
             emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)));
@@ -1351,6 +1392,12 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
   o.mb = (double)mb;
   o.prec = (double)(mb * sumr);
   o.ktop = kts;
+  if constexpr (TP::kOn) {
+    tape->active = true;
+    tape->klfc = klfc;
+    tape->kts = kts;
+    tape->sumr = sumr;
+  }
   const double se = CP * sea.value(), sw = swa.value();
   o.cons = cons_ratio(fabs(se - LV * o.prec) + LV * fabs(sw + o.prec),
                       CP * (double)sc + LV * o.prec + 1e-300, R(0));

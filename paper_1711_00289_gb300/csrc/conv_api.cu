@@ -267,6 +267,38 @@ conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
   return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
 }
 
+conv_status conv_deep_shallow_adjoint(const conv_grid* grid, const conv_in* in,
+                                      const conv_deep_params* dpar,
+                                      const conv_shallow_params* spar, double dt,
+                                      conv_precision prec, const double* gPd, const double* gHd,
+                                      const double* gPs, const double* gHs,
+                                      const double* w_heat, double* gT, double* gq,
+                                      double* glambda, double* gtau, double* obj, int gradient,
+                                      conv_stream stream) {
+  if (prec != CONV_FP64) return prec == CONV_MIXED ? CONV_ERR_UNSUPPORTED : CONV_ERR_ARG;
+  RunArgs a;
+  conv_status s = common_in(grid, in, dt, a);
+  if (s != CONV_OK) return s;
+  if (!deep_params_ok(dpar) || !shallow_params_ok(spar) || !gT || !gq) return CONV_ERR_ARG;
+  if (gradient && (!glambda || !gtau)) return CONV_ERR_ARG;
+  if (!gradient && !obj) return CONV_ERR_ARG;
+  cvg::AdjW w;
+  w.given = w_heat != nullptr;
+  for (int k = 0; k < CONV_MAX_LEVELS; ++k) {
+    w.w[k] = (w_heat && k < grid->pver) ? w_heat[k] : 0.0;
+    if (!std::isfinite(w.w[k])) return CONV_ERR_ARG;
+  }
+  a.dp = *dpar;
+  a.sp = *spar;
+  a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  cvg::fill_q(a);
+  const double* g[4] = {gPd, gHd, gPs, gHs};
+  const cudaError_t e =
+      cvg::launch_step_adjoint(a, g, w, gT, gq, glambda, gtau, obj, gradient != 0);
+  return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
+
 }  // extern "C"
 
 // ================================================================ batches

@@ -156,3 +156,25 @@ def test_adjoint_arguments_checked_on_host():
     assert call(wh=w) == L.CONV_ERR_ARG
     dp.tau_default = 0.0
     assert call() == L.CONV_ERR_ARG
+
+
+def test_step_adjoint_arguments_checked_on_host():
+    g, inp, out, keep = _args()
+    dp, sp = L.deep_defaults(), L.shallow_defaults()
+    lib = L.lib()
+    fake = C.c_void_p(0x1000)
+
+    def call(prec=L.CONV_FP64, gT=fake, gq=fake, gl=fake, gt=fake, obj=None, grad=1):
+        return lib.conv_deep_shallow_adjoint(C.byref(g), C.byref(inp), C.byref(dp),
+                                             C.byref(sp), 1800.0, prec, None, None, None,
+                                             None, None, gT, gq, gl, gt, obj, grad, None)
+
+    # n_cols = 0: nothing is enqueued
+    assert call() == L.CONV_OK
+    assert call(gl=None, gt=None, obj=fake, grad=0) == L.CONV_OK
+    assert call(prec=L.CONV_MIXED) == L.CONV_ERR_UNSUPPORTED
+    assert call(gT=None) == L.CONV_ERR_ARG  # gT, gq are always needed (deep tendencies)
+    assert call(gl=None) == L.CONV_ERR_ARG
+    assert call(grad=0) == L.CONV_ERR_ARG  # nothing requested
+    sp.tke = 0.0
+    assert call() == L.CONV_ERR_ARG
