@@ -280,6 +280,22 @@ conv_status conv_deep_shallow_adjoint(const conv_grid* grid, const conv_in* in,
                                       double* glambda, double* gtau, double* obj, int gradient,
                                       conv_stream stream);
 
+/* ------------------------------------------------------------------ driver
+ * State advance of a multi-step column driver (no counterpart in the paper,
+ * whose scheme runs inside a full model): after one conv_deep_shallow_run on
+ * (T, q), update in place, level by level,
+ *   T <- T + dt*((dTdt_deep + dTdt_shallow) + (T_relax - T)/tau_relax)
+ *   q <- max(q + dt*((dqdt_deep + dqdt_shallow) + (q_relax - q)/tau_relax), 0)
+ * The Newtonian relaxation towards reference profiles stands in for the large
+ * scale forcing the rest of the model would supply; tau_relax <= 0 switches it
+ * off (T_relax, q_relax may then be NULL).  T, q, T_relax, q_relax and the
+ * output tendencies are DEVICE [pver][ld] arrays of the precision's type;
+ * asynchronous on `stream`. */
+conv_status conv_advance(const conv_grid* grid, void* T, void* q, const void* T_relax,
+                         const void* q_relax, double tau_relax, const conv_out* deep_out,
+                         const conv_out* shallow_out, double dt, conv_precision prec,
+                         conv_stream stream);
+
 /* ------------------------------------------------------------------ batches
  * Many grids / ensemble members of uneven column counts and level counts in one
  * trigger launch over all their columns and one persistent launch over a common

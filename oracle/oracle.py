@@ -272,6 +272,34 @@ def deep_shallow_adjoint(g, gPd=None, gHd=None, gPs=None, gHs=None, w_heat=None,
     return gT, gq, gl, gt
 
 
+def advance(T, q, deep, shallow, dt, T_relax=None, q_relax=None, tau_relax=0.0):
+    """State advance of the multi-step column driver (numpy, FP64):
+    T + dt*((dTdt_deep + dTdt_shallow) + (T_relax - T)/tau_relax), likewise q,
+    floored at 0; no relaxation for tau_relax <= 0."""
+    rt = 1.0 / tau_relax if tau_relax > 0 else 0.0
+    Tr = T if T_relax is None else T_relax
+    qr = q if q_relax is None else q_relax
+    fT = (deep["dTdt"] + shallow["dTdt"]) + (Tr - T) * rt
+    fq = (deep["dqdt"] + shallow["dqdt"]) + (qr - q) * rt
+    return T + dt * fT, np.maximum(q + dt * fq, 0.0)
+
+
+def column_model(g, steps, tau_relax=86400.0, threads: int = 1, record=None):
+    """Runs the oracle's fused step `steps` times from g's state, relaxing towards
+    the initial profiles; record(step, T, q, deep, shallow) after every step.
+    Returns the final (T, q)."""
+    import copy
+    T, q = g.T.copy(), g.q.copy()
+    for s in range(steps):
+        sub = copy.copy(g)
+        sub.T, sub.q = T, q
+        d, sh = deep_shallow(sub, threads=threads)
+        T, q = advance(T, q, d, sh, g.dt, g.T, g.q, tau_relax)
+        if record:
+            record(s, T, q, d, sh)
+    return T, q
+
+
 def count_ops(g, dpar=None, spar=None, dt=None):
     """Operation counts (add, mul, div, exp, log, pow, sqrt, -) summed over columns."""
     dpar = dpar or deep_params()

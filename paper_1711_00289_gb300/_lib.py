@@ -126,6 +126,8 @@ def lib(build: bool = True):
                                             st, vp, vp, vp, vp, P(C.c_double), vp, vp, vp, vp,
                                             vp, st, vp]
     L.conv_deep_shallow_adjoint.restype = st
+    L.conv_advance.argtypes = [P(Grid), vp, vp, vp, vp, d, P(Out), P(Out), d, st, vp]
+    L.conv_advance.restype = st
     _lib = L
     return L
 

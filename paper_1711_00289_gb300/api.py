@@ -462,3 +462,61 @@ def deep_shallow_step(T, q, ps, vgrid: VerticalGrid, *, lam=None, tau=None, dt: 
     lam, tau."""
     return DeepShallowStep.apply(T, q, lam, tau, ps, vgrid, dt, deep_params, shallow_params,
                                  w_heat)
+
+
+def advance(T, q, vgrid: VerticalGrid, deep_out, shallow_out, *, dt: float, precision="fp64",
+            T_relax=None, q_relax=None, tau_relax: float = 0.0, n_cols=None, stream=None):
+    """In-place state advance after one fused step (conv_advance):
+    T += dt*((dTdt_deep + dTdt_shallow) + (T_relax - T)/tau_relax), likewise q
+    (floored at 0); tau_relax <= 0 switches the relaxation off."""
+    rd = real_dtype(precision)
+    pver, ld = T.shape
+    _require_cuda(T, "T", rd, (pver, ld))
+    _require_cuda(q, "q", rd, (pver, ld))
+    if tau_relax > 0:
+        _require_cuda(T_relax, "T_relax", rd, (pver, ld))
+        _require_cuda(q_relax, "q_relax", rd, (pver, ld))
+    n = ld if n_cols is None else int(n_cols)
+    g = vgrid.struct(n, ld)
+    st = L.lib().conv_advance(C.byref(g), _ptr(T), _ptr(q), _ptr(T_relax), _ptr(q_relax),
+                              float(tau_relax),
+                              C.byref(_out_struct(deep_out, pver, ld, precision)),
+                              C.byref(_out_struct(shallow_out, pver, ld, precision)), float(dt),
+                              _PREC[precision], _stream(stream))
+    L.check(st, "conv_advance")
+
+
+class ColumnModel:
+    """Multi-step column driver: every step runs the fused deep -> shallow scheme
+    on the current state and advances the state with the tendencies and a
+    Newtonian relaxation (time scale tau_relax, s) towards the initial profiles,
+    which stand in for the large-scale forcing of a full model.  T, q: [pver, ld]
+    device tensors of the precision's type (copied); ps [ld] float64."""
+
+    def __init__(self, T, q, ps, vgrid: VerticalGrid, *, precision="fp64", dt: float = 1800.0,
+                 tau_relax: float = 86400.0, lam=None, tau=None, deep_params=None,
+                 shallow_params=None, path="auto"):
+        rd = real_dtype(precision)
+        self.T, self.q = T.to(rd).clone(), q.to(rd).clone()
+        self.T_ref, self.q_ref = self.T.clone(), self.q.clone()
+        self.ps, self.vgrid, self.precision, self.dt = ps, vgrid, precision, float(dt)
+        self.tau_relax, self.lam, self.tau, self.path = float(tau_relax), lam, tau, path
+        self.deep_params, self.shallow_params = deep_params, shallow_params
+        pver, ld = self.T.shape
+        self.out_deep = new_outputs(pver, ld, precision, T.device)
+        self.out_shallow = new_outputs(pver, ld, precision, T.device)
+        self.ws = Workspace(T.device)
+        self.steps = 0
+
+    def step(self, n: int = 1, stream=None):
+        for _ in range(n):
+            deep_shallow(self.T, self.q, self.ps, self.vgrid, dt=self.dt,
+                         precision=self.precision, lam=self.lam, tau=self.tau,
+                         deep_params=self.deep_params, shallow_params=self.shallow_params,
+                         path=self.path, out_deep=self.out_deep, out_shallow=self.out_shallow,
+                         workspace=self.ws, stream=stream)
+            advance(self.T, self.q, self.vgrid, self.out_deep, self.out_shallow, dt=self.dt,
+                    precision=self.precision, T_relax=self.T_ref, q_relax=self.q_ref,
+                    tau_relax=self.tau_relax, stream=stream)
+            self.steps += 1
+        return self.T, self.q

@@ -299,6 +299,30 @@ conv_status conv_deep_shallow_adjoint(const conv_grid* grid, const conv_in* in,
   return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
 }
 
+conv_status conv_advance(const conv_grid* grid, void* T, void* q, const void* T_relax,
+                         const void* q_relax, double tau_relax, const conv_out* deep_out,
+                         const conv_out* shallow_out, double dt, conv_precision prec,
+                         conv_stream stream) {
+  if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
+  RunArgs a;
+  std::memset(&a, 0, sizeof a);
+  conv_status s = fill_grid(grid, a);
+  if (s != CONV_OK) return s;
+  if (!T || !q || !(std::isfinite(dt) && dt > 0.0) || !std::isfinite(tau_relax)) return CONV_ERR_ARG;
+  if (tau_relax > 0.0 && (!T_relax || !q_relax)) return CONV_ERR_ARG;
+  if (!deep_out || !shallow_out || !deep_out->dTdt || !deep_out->dqdt || !shallow_out->dTdt ||
+      !shallow_out->dqdt)
+    return CONV_ERR_ARG;
+  a.od = to_outp(deep_out);
+  a.os = to_outp(shallow_out);
+  a.dt = dt;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  const cudaError_t e = cvg::launch_advance(a, prec == CONV_FP64, T, q,
+                                            tau_relax > 0.0 ? T_relax : T,
+                                            tau_relax > 0.0 ? q_relax : q, tau_relax);
+  return e == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
+
 }  // extern "C"
 
 // ================================================================ batches

@@ -124,6 +124,10 @@ struct AdjW {
 cudaError_t launch_deep_adjoint(const RunArgs& a, const double* gP, const double* gH,
                                 const AdjW& w, double* gT, double* gq, double* glam,
                                 double* gtau, double* Pout, double* Hout);
+// State advance of the multi-step driver (in place on T, q).
+cudaError_t launch_advance(const RunArgs& a, bool fp64, void* T, void* q, const void* Tr,
+                           const void* qr, double tau);
+
 // Fused deep -> shallow step adjoint (FP64): one thread per column.  gT, gq are
 // also the scratch of the deep tendencies (always written); obj may be nullptr.
 cudaError_t launch_step_adjoint(const RunArgs& a, const double* const g[4], const AdjW& w,
