@@ -296,6 +296,27 @@ conv_status conv_advance(const conv_grid* grid, void* T, void* q, const void* T_
                          const conv_out* shallow_out, double dt, conv_precision prec,
                          conv_stream stream);
 
+/* ------------------------------------------------------------------ host pipeline
+ * conv_deep_shallow_run on HOST buffers (no counterpart in the paper: there the
+ * data never leaves the host).  A plan splits the grid's columns into chunks of
+ * chunk_cols; a run copies chunk j+1 in while chunk j computes and chunk j-1
+ * copies out, on three streams of the plan, so the host link carries both
+ * directions at once.  Plan time allocates (device staging for three chunks,
+ * streams, events); runs allocate nothing and are asynchronous with respect to
+ * the host: they are ordered after earlier work on `stream`, and later work on
+ * `stream` waits for the last copy out.  Host arrays: conv_in / conv_out
+ * layouts of the plan's grid (n_cols, ld), HOST pointers, page-locked for the
+ * copies to be asynchronous; the optional outputs (kb ... cons_err) and
+ * lambda/tau may be NULL.  The grid's hyai/hybi are copied at plan time. */
+typedef struct conv_pipeline conv_pipeline;
+conv_status conv_pipeline_plan(const conv_grid* grid, conv_precision prec, int chunk_cols,
+                               conv_pipeline** out);
+conv_status conv_pipeline_run(conv_pipeline* p, const conv_in* host_in,
+                              const conv_deep_params* dpar, const conv_shallow_params* spar,
+                              double dt, const conv_out* host_deep, const conv_out* host_shallow,
+                              conv_stream stream);
+void conv_pipeline_free(conv_pipeline* p);
+
 /* ------------------------------------------------------------------ batches
  * Many grids / ensemble members of uneven column counts and level counts in one
  * trigger launch over all their columns and one persistent launch over a common

@@ -128,6 +128,13 @@ def lib(build: bool = True):
     L.conv_deep_shallow_adjoint.restype = st
     L.conv_advance.argtypes = [P(Grid), vp, vp, vp, vp, d, P(Out), P(Out), d, st, vp]
     L.conv_advance.restype = st
+    L.conv_pipeline_plan.argtypes = [P(Grid), st, st, P(vp)]
+    L.conv_pipeline_plan.restype = st
+    L.conv_pipeline_run.argtypes = [vp, P(In), P(DeepParams), P(ShallowParams), d, P(Out),
+                                    P(Out), vp]
+    L.conv_pipeline_run.restype = st
+    L.conv_pipeline_free.argtypes = [vp]
+    L.conv_pipeline_free.restype = None
     _lib = L
     return L
 

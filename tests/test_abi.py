@@ -178,3 +178,17 @@ def test_step_adjoint_arguments_checked_on_host():
     assert call(grad=0) == L.CONV_ERR_ARG  # nothing requested
     sp.tke = 0.0
     assert call() == L.CONV_ERR_ARG
+
+
+def test_pipeline_plan_validated_before_touching_a_device():
+    g, inp, out, keep = _args(n=10, ld=10)
+    lib = L.lib()
+    h = C.c_void_p()
+    assert lib.conv_pipeline_plan(C.byref(g), L.CONV_MIXED, 0, C.byref(h)) == L.CONV_ERR_ARG
+    assert lib.conv_pipeline_plan(C.byref(g), 7, 16, C.byref(h)) == L.CONV_ERR_ARG
+    g.pver = 3
+    assert lib.conv_pipeline_plan(C.byref(g), L.CONV_MIXED, 16, C.byref(h)) == L.CONV_ERR_ARG
+    assert lib.conv_pipeline_run(None, C.byref(inp), C.byref(L.deep_defaults()),
+                                 C.byref(L.shallow_defaults()), 1800.0, C.byref(out),
+                                 C.byref(out), None) == L.CONV_ERR_ARG
+    lib.conv_pipeline_free(None)
