@@ -25,7 +25,9 @@
 // Bolton cross-checks, Newton residuals, brute-force level scans on tiny columns,
 // column energy/water conservation, non-negativity, exact zeros outside the
 // trigger, linearity of the closure in 1/tau, and finite differences for the
-// tangent.
+// tangent.  Tracer transport (tests/test_oracle_transport.py): uniform tracers
+// unchanged, column tracer mass conserved, upwind monotone transport matrices,
+// the moist static energy transported as each scheme transports it.
 
 #include "conv_oracle.h"
 
@@ -760,6 +762,114 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
   s.cons_err = (std::fabs(se - LV * P_) + LV * std::fabs(sw + P_)) / (scale + LV * P_ + 1e-300);
 }
 
+// ---------------------------------------------------------------- tracer transport
+// Convective transport of passive tracers (a variant both cited schemes carry,
+// Sec. II-A: ZM and UW move constituents with their plume mass fluxes; the paper
+// itself times only the thermodynamic loops).  This project's reading: a tracer
+// c (mixing ratio) is mixed exactly like each scheme's conserved moist static
+// energy in its own flux-form tendency equations above, with no source term
+// (no rain-out, no phase change), so every step below repeats the matching MSE
+// step with h replaced by c.  Inactive columns have zero tendencies.
+//
+// Mass-flux profiles (kg m-2 s-1) that describe the same transport:
+//   mu[k]  updraft mass flux leaving layer k through its top interface;
+//   du[k]  updraft air detrained into layer k, carrying the plume value
+//          arriving from layer k+1;
+//   md[k]  downdraft mass flux leaving layer k through its bottom interface
+//          (downward positive); the downdraft detrains all of it into the layer
+//          below its lowest level.
+// Deep: mu = M_b eta on jt+1..kb, du[jt] = M_b eta[jt+1], md = M_b alpha etad
+// on jd..kb-1.  Shallow: mu = M_b on kts+1..ks, du = M_b (1 - exp(-eps dz)) on
+// kts+1..klcl-1 and du[kts] = M_b, md = 0.
+
+// Deep tracer tendency of one column (s from deep_column; c this column's tracer).
+void deep_transport(int pver, const DeepState<double>& s, const double* c, double* tend) {
+  for (int k = 0; k < pver; ++k) tend[k] = 0.0;
+  if (!s.active) return;
+  const int kb = s.kb, jt = s.jt, jd = s.jd;
+  double cu[MAXLEV], cd[MAXLEV], dc[MAXLEV];
+  for (int k = 0; k < pver; ++k) cu[k] = cd[k] = dc[k] = 0.0;
+  // updraft, mixed as the plume MSE is
+  cu[kb] = c[kb];
+  for (int k = kb - 1; k > jt; --k)
+    cu[k] = (s.eta[k + 1] * cu[k + 1] + (s.eta[k] - s.eta[k + 1]) * c[k]) / s.eta[k];
+  // downdraft, mixed as the downdraft MSE is
+  if (jd >= 0) {
+    cd[jd] = c[jd];
+    for (int k = jd + 1; k <= kb - 1; ++k)
+      cd[k] = (s.etad[k - 1] * cd[k - 1] + (s.etad[k] - s.etad[k - 1]) * c[k]) / s.etad[k];
+  }
+  // flux-form terms per unit M_b: subsidence, detrainment at the top, the
+  // downdraft's compensating ascent and its detrainment into the launch layer
+  for (int k = jt + 1; k <= kb; ++k) dc[k] = dc[k] + s.eta[k] * (c[k - 1] - c[k]);
+  dc[jt] = dc[jt] + s.eta[jt + 1] * (cu[jt + 1] - c[jt]);
+  if (jd >= 0) {
+    for (int k = jd; k <= kb - 1; ++k) dc[k] = dc[k] + s.alpha * s.etad[k] * (c[k + 1] - c[k]);
+    dc[kb] = dc[kb] + s.alpha * s.etad[kb - 1] * (cd[kb - 1] - c[kb]);
+  }
+  for (int k = jt; k <= kb; ++k) tend[k] = s.mb * (dc[k] / s.m[k]);
+}
+
+// Shallow tracer tendency of one column (s from shallow_column on the state the
+// shallow scheme saw; c the tracer it sees).
+void shallow_transport(int pver, const ShalState<double>& s, const ShalP& P, const double* c,
+                       double* tend) {
+  for (int k = 0; k < pver; ++k) tend[k] = 0.0;
+  if (!s.active) return;
+  const int ks = pver - 1, kts = s.kts;
+  double cu[MAXLEV], dc[MAXLEV];
+  for (int k = 0; k < pver; ++k) cu[k] = dc[k] = 0.0;
+  // constant-mass-flux plume: undilute up to the LCL layer, relaxing towards
+  // the environment by 1 - exp(-eps dz) per layer above it
+  cu[ks] = c[ks];
+  for (int k = ks - 1; k > kts; --k) {
+    if (k >= s.klcl) {
+      cu[k] = cu[k + 1];
+    } else {
+      const double dz = s.z_int[k] - s.z_int[k + 1];
+      const double chi = 1.0 - std::exp(-P.eps_s * dz);
+      cu[k] = cu[k + 1] + chi * (c[k] - cu[k + 1]);
+    }
+  }
+  dc[ks] = s.mb * (c[ks - 1] - c[ks]);
+  for (int k = kts + 1; k <= ks - 1; ++k)
+    dc[k] = s.mb * ((cu[k + 1] - cu[k]) + (c[k - 1] - c[k]));
+  dc[kts] = s.mb * (cu[kts + 1] - c[kts]);
+  for (int k = kts; k <= ks; ++k) tend[k] = dc[k] / s.m[k];
+}
+
+void deep_fluxes(int pver, const DeepState<double>& s, double* mu, double* du, double* md) {
+  for (int k = 0; k < pver; ++k) mu[k] = du[k] = md[k] = 0.0;
+  if (!s.active) return;
+  for (int k = s.jt + 1; k <= s.kb; ++k) mu[k] = s.mb * s.eta[k];
+  du[s.jt] = s.mb * s.eta[s.jt + 1];
+  if (s.jd >= 0)
+    for (int k = s.jd; k <= s.kb - 1; ++k) md[k] = s.mb * s.alpha * s.etad[k];
+}
+
+void shallow_fluxes(int pver, const ShalState<double>& s, const ShalP& P, double* mu, double* du,
+                    double* md) {
+  for (int k = 0; k < pver; ++k) mu[k] = du[k] = md[k] = 0.0;
+  if (!s.active) return;
+  const int ks = pver - 1;
+  for (int k = s.kts + 1; k <= ks; ++k) mu[k] = s.mb;
+  for (int k = s.kts + 1; k <= s.klcl - 1 && k <= ks - 1; ++k) {
+    const double dz = s.z_int[k] - s.z_int[k + 1];
+    du[k] = s.mb * (1.0 - std::exp(-P.eps_s * dz));
+  }
+  du[s.kts] = s.mb;
+}
+
+void store_flux(const oracle_flux* f, int pver, int ld, int i, const double* mu, const double* du,
+                const double* md) {
+  if (!f) return;
+  for (int k = 0; k < pver; ++k) {
+    if (f->mu) f->mu[k * ld + i] = mu[k];
+    if (f->du) f->du[k * ld + i] = du[k];
+    if (f->md) f->md[k * ld + i] = md[k];
+  }
+}
+
 // ---------------------------------------------------------------- grid drivers
 inline void set_i(int32_t* a, int i, int v) { if (a) a[i] = v; }
 inline void set_d(double* a, int i, double v) { if (a) a[i] = v; }
@@ -945,6 +1055,59 @@ int oracle_deep_shallow(int n_cols, int pver, int ld, const double* hyai, const 
     ShalState<double> t;
     shallow_column<double>(pver, hyai, hybi, p0, T2, q2, ps[i], SP, t);
     store_shallow(t, pver, ld, i, shallow);
+  }
+  return 0;
+}
+
+int oracle_deep_shallow_tracers(int n_cols, int pver, int ld, const double* hyai,
+                                const double* hybi, double p0, const double* T, const double* q,
+                                const double* ps, const double* lambda, const double* tau,
+                                const oracle_deep_params* dpar, const oracle_shallow_params* spar,
+                                double dt, int ntr, const double* tracers, double* tend_deep,
+                                double* tend_shallow, const oracle_flux* flux_deep,
+                                const oracle_flux* flux_shallow, int n_threads) {
+  if (!grid_ok(n_cols, pver, ld) || !dpar || !spar || ntr < 0 || (ntr > 0 && !tracers) ||
+      (ntr > 0 && (!tend_deep || !tend_shallow)))
+    return 1;
+  const DeepP DP = to_deep(dpar);
+  const ShalP SP = to_shal(spar);
+  const size_t tstride = (size_t)pver * ld;
+#pragma omp parallel for schedule(dynamic, 8) num_threads(threads_for(n_threads))
+  for (int i = 0; i < n_cols; ++i) {
+    double Tc[MAXLEV], qc[MAXLEV], T2[MAXLEV], q2[MAXLEV];
+    for (int k = 0; k < pver; ++k) { Tc[k] = T[k * ld + i]; qc[k] = q[k * ld + i]; }
+    DeepState<double> s;
+    deep_column<double>(pver, hyai, hybi, p0, Tc, qc, ps[i],
+                        lambda ? lambda[i] : DP.lambda_default, tau ? tau[i] : DP.tau_default,
+                        DP, dt, s);
+    for (int k = 0; k < pver; ++k) {
+      T2[k] = Tc[k] + dt * s.dTdt[k];
+      q2[k] = qc[k] + dt * s.dqdt[k];
+      if (!s.bad && q2[k] < 0.0) q2[k] = 0.0;
+    }
+    ShalState<double> t;
+    shallow_column<double>(pver, hyai, hybi, p0, T2, q2, ps[i], SP, t);
+    double mu[MAXLEV], du[MAXLEV], md[MAXLEV];
+    deep_fluxes(pver, s, mu, du, md);
+    store_flux(flux_deep, pver, ld, i, mu, du, md);
+    shallow_fluxes(pver, t, SP, mu, du, md);
+    store_flux(flux_shallow, pver, ld, i, mu, du, md);
+    // each tracer: deep transport, then the shallow transport of the
+    // deep-updated tracer (floored at zero, as the humidity is)
+    for (int n = 0; n < ntr; ++n) {
+      double c[MAXLEV], c2[MAXLEV], td[MAXLEV], ts[MAXLEV];
+      for (int k = 0; k < pver; ++k) c[k] = tracers[n * tstride + k * ld + i];
+      deep_transport(pver, s, c, td);
+      for (int k = 0; k < pver; ++k) {
+        c2[k] = c[k] + dt * td[k];
+        if (c2[k] < 0.0) c2[k] = 0.0;
+      }
+      shallow_transport(pver, t, SP, c2, ts);
+      for (int k = 0; k < pver; ++k) {
+        tend_deep[n * tstride + k * ld + i] = td[k];
+        tend_shallow[n * tstride + k * ld + i] = ts[k];
+      }
+    }
   }
   return 0;
 }

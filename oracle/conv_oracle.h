@@ -45,6 +45,16 @@ typedef struct {
   double *cape, *mb, *cons_err;              /* [ld] (shallow: cape holds CIN)     */
 } oracle_out;
 
+/* Mass-flux profiles of one scheme ([pver][ld] kg m-2 s-1, any pointer may be
+ * NULL): mu = updraft flux leaving layer k through its top; du = updraft air
+ * detrained into layer k (carrying the plume value from layer k+1); md =
+ * downdraft flux leaving layer k through its bottom (downward positive), all
+ * detrained into the layer below the downdraft's lowest level.  Zero in
+ * inactive columns. */
+typedef struct {
+  double *mu, *du, *md;
+} oracle_flux;
+
 /* Scalar thermodynamics (for pin tests). */
 double oracle_es(double T);
 double oracle_qs(double T, double p);
@@ -131,6 +141,20 @@ int oracle_deep_shallow_adjoint(int n_cols, int pver, int ld, const double* hyai
  * [0] add/sub, [1] mul, [2] div, [3] exp, [4] log, [5] pow, [6] sqrt, [7] unused.
  * counts_deep: the deep scheme alone; counts_total: deep + shallow; both summed
  * over the given columns (8 doubles each, either may be NULL). */
+/* Convective transport of ntr passive tracers ([ntr][pver][ld], stride
+ * pver*ld) by the fused step: tend_deep = the deep scheme's tendency of each
+ * tracer; tend_shallow = the shallow scheme's tendency of max(c + dt*tend_deep,
+ * 0), the tracer the shallow scheme sees after the deep update (Alg. 1 order).
+ * Each scheme mixes a tracer as it mixes its conserved moist static energy.
+ * flux_deep / flux_shallow (may be NULL) receive the mass-flux profiles. */
+int oracle_deep_shallow_tracers(int n_cols, int pver, int ld, const double* hyai,
+                                const double* hybi, double p0, const double* T, const double* q,
+                                const double* ps, const double* lambda, const double* tau,
+                                const oracle_deep_params* dpar, const oracle_shallow_params* spar,
+                                double dt, int ntr, const double* tracers, double* tend_deep,
+                                double* tend_shallow, const oracle_flux* flux_deep,
+                                const oracle_flux* flux_shallow, int n_threads);
+
 int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const double* hybi,
                      double p0, const double* T, const double* q, const double* ps,
                      const oracle_deep_params* dpar, const oracle_shallow_params* spar,

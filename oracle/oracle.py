@@ -73,6 +73,10 @@ class Out(C.Structure):
                 ("mb", C.c_void_p), ("cons_err", C.c_void_p)]
 
 
+class Flux(C.Structure):
+    _fields_ = [("mu", C.c_void_p), ("du", C.c_void_p), ("md", C.c_void_p)]
+
+
 N32 = 32
 
 
@@ -141,11 +145,16 @@ def lib():
         L.oracle_deep_shallow_adjoint.argtypes = [i, i, i, p, p, d, p, p, p, p, p,
                                                   C.POINTER(DeepParams), C.POINTER(ShallowParams),
                                                   d, p, p, p, p, p, p, p, p, p, i]
+        L.oracle_deep_shallow_tracers.argtypes = [i, i, i, p, p, d, p, p, p, p, p,
+                                                  C.POINTER(DeepParams), C.POINTER(ShallowParams),
+                                                  d, i, p, p, p, C.POINTER(Flux), C.POINTER(Flux),
+                                                  i]
         L.oracle_count_ops.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                        C.POINTER(ShallowParams), d, p, p]
         L.oracle_count_ops_by_pass.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                                C.POINTER(ShallowParams), d, p, p, p]
         for fn in ("oracle_deep", "oracle_shallow", "oracle_deep_shallow", "oracle_deep_adjoint",
+                   "oracle_deep_shallow_tracers",
                    "oracle_deep_shallow_adjoint", "oracle_count_ops", "oracle_count_ops_by_pass"):
             getattr(L, fn).restype = i
         _lib = L
@@ -225,6 +234,38 @@ def deep_shallow(g, dpar=None, spar=None, dt=None, threads: int = 1, lam=None, t
                                    threads)
     assert rc == 0
     return od, os_
+
+
+def deep_shallow_tracers(g, tracers, dpar=None, spar=None, dt=None, threads: int = 1, lam=None,
+                         tau=None, T=None, q=None):
+    """Convective transport of passive tracers ([ntr][pver][n]) by the fused step.
+
+    Returns (tend_deep, tend_shallow, flux_deep, flux_shallow): tendencies
+    [ntr][pver][n] (the shallow one of the deep-updated tracers) and dicts of the
+    mass-flux profiles mu, du, md ([pver][n])."""
+    dpar = dpar or deep_params()
+    spar = spar or shallow_params()
+    dt = g.dt if dt is None else dt
+    T = _c64(g.T if T is None else T)
+    q = _c64(g.q if q is None else q)
+    ps = _c64(g.ps)
+    lam = _c64(lam if lam is not None else g.lam)
+    tau = _c64(tau if tau is not None else g.tau)
+    n, pver = g.n_cols, g.pver
+    tr = _c64(tracers)
+    assert tr.ndim == 3 and tr.shape[1:] == (pver, n), tr.shape
+    ntr = tr.shape[0]
+    td, ts = np.zeros_like(tr), np.zeros_like(tr)
+    fd = {k: np.zeros((pver, n)) for k in ("mu", "du", "md")}
+    fs = {k: np.zeros((pver, n)) for k in ("mu", "du", "md")}
+    hyai, hybi = _c64(g.hyai), _c64(g.hybi)
+    rc = lib().oracle_deep_shallow_tracers(
+        n, pver, n, _ptr(hyai), _ptr(hybi), 1e5, _ptr(T), _ptr(q), _ptr(ps), _ptr(lam), _ptr(tau),
+        C.byref(dpar), C.byref(spar), dt, ntr, _ptr(tr), _ptr(td), _ptr(ts),
+        C.byref(Flux(*[fd[k].ctypes.data for k in ("mu", "du", "md")])),
+        C.byref(Flux(*[fs[k].ctypes.data for k in ("mu", "du", "md")])), threads)
+    assert rc == 0
+    return td, ts, fd, fs
 
 
 def deep_adjoint(g, gP, gH, w_heat=None, par=None, dt=None, threads: int = 1, lam=None,
