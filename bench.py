@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-transport", action="store_true",
+                   help="skip the tracer-transport measurement")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the deep-adjoint timing")
     p.add_argument("--no-ensemble", action="store_true",
@@ -401,6 +403,7 @@ def ours_arm(args, rank, world, local_rank):
                                          / measured_hbm())
     ens = None if args.no_ensemble else ensemble_bench(args, dev)
     adj = None if args.no_adjoint else adjoint_bench(args, dev, g)
+    trn = None if args.no_transport else transport_bench(args, dev, g)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, ncols, threads, el = cpu_oracle_rate(g, args.cpu_seconds)
@@ -420,6 +423,7 @@ def ours_arm(args, rank, world, local_rank):
             "baseline_fp64_plain": base,
             "speedup_vs_fp64_plain": (value / base["value"]) if base else None,
             "roofline": roof, "kernels": kernels, "batched_ensemble": ens, "deep_adjoint": adj,
+            "tracer_transport": trn,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": (1 if path == "plain" else 2) * args.steps,
             "op_rates_per_s": r}
@@ -524,6 +528,85 @@ def adjoint_bench(args, dev, g_full):
                               "adjoint_over_forward": adj2 / fwd2,
                               "value": n / (adj2 * 1e-3), "unit": UNIT}}
     return res
+
+
+def transport_bench(args, dev, g, ntr=25):
+    """Convective tracer transport of ``ntr`` tracers by the fused step's plumes
+    (mixed precision, FP32 tracers) on the benchmark grid: the transport kernel
+    timed alone with CUDA events, its algorithmic HBM bytes counted from the
+    plumes' extents (tendencies written everywhere; tracers read on the levels
+    a plume touches; mass-flux profiles, flags and levels once per column), and
+    the fused step with and without the profile outputs."""
+    import torch
+
+    from paper_1711_00289_gb300 import api
+
+    n, pver = g.n_cols, g.pver
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    T = torch.tensor(g.T, device=dev).float()
+    q = torch.tensor(g.q, device=dev).float()
+    ps = torch.tensor(g.ps, device=dev)
+    tau = None if g.tau is None else torch.tensor(g.tau, device=dev)
+    ws = api.Workspace(dev)
+    od = api.new_outputs(pver, n, "mixed", dev, flux=True)
+    os_ = api.new_outputs(pver, n, "mixed", dev, flux=True)
+    od0 = api.new_outputs(pver, n, "mixed", dev)
+    os0 = api.new_outputs(pver, n, "mixed", dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(20171106)
+    tr = torch.rand((ntr, pver, n), device=dev, generator=gen)
+    td, ts = torch.empty_like(tr), torch.empty_like(tr)
+    cur = torch.cuda.current_stream(dev)
+
+    def ev_time(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for _ in range(reps):
+            fn()
+        e1.record(cur)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    reps = max(3, args.steps)
+    step_flux = ev_time(lambda: api.deep_shallow(T, q, ps, vg, dt=g.dt, precision="mixed",
+                                                 tau=tau, out_deep=od, out_shallow=os_,
+                                                 workspace=ws), reps)
+    step_plain = ev_time(lambda: api.deep_shallow(T, q, ps, vg, dt=g.dt, precision="mixed",
+                                                  tau=tau, out_deep=od0, out_shallow=os0,
+                                                  workspace=ws), reps)
+    ms = ev_time(lambda: api.tracer_transport(tr, ps, vg, deep_out=od, shallow_out=os_, dt=g.dt,
+                                              precision="mixed", tend_deep=td, tend_shallow=ts),
+                 reps)
+    # algorithmic bytes of one launch
+    ad = (od["flags"] & 2) > 0
+    as_ = (os_["flags"] & 2) > 0
+    jt, kb = od["ktop"].long(), od["kb"].long()
+    kts = os_["ktop"].long()
+    ld_ = torch.where(ad, kb - jt + 1, torch.zeros_like(kb))
+    ls_ = torch.where(as_, pver - kts, torch.zeros_like(kts))
+    ov = torch.clamp(torch.minimum(kb, torch.full_like(kb, pver - 1)) - torch.maximum(jt, kts) + 1,
+                     min=0)
+    both = ad & as_
+    read_levels = ld_ + ls_ - torch.where(both, ov, torch.zeros_like(ov))
+    jd = od["kaux"].long()
+    dd_levels = torch.where(ad & (jd >= 0), kb - jd, torch.zeros_like(kb))
+    es = 4
+    per_col_prof = (2 * ld_ + dd_levels + 2 * ls_) * es + 7 * 4 + 8  # profiles, ints, ps
+    tracer_bytes = ntr * (2 * pver * n * es + int(read_levels.sum()) * es)
+    alg = tracer_bytes + int(per_col_prof.sum())
+    achieved = alg / (ms * 1e-3) / 1e9
+    peak = measured_hbm()
+    return {"tracers": ntr, "columns": n, "levels": pver, "precision": "mixed",
+            "ms_transport": ms, "value": ntr * n / (ms * 1e-3), "unit": "tracer-columns/s",
+            "ms_step_with_profiles": step_flux, "ms_step_without_profiles": step_plain,
+            "gpu_launches_per_call": 1,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "algorithmic_bytes": alg,
+                         "traffic": ncu_traffic(g.name + "-transport").get("k_transport"),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
 
 
 def l2_note(prec, n, pver):

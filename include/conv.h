@@ -152,6 +152,21 @@ typedef struct {
  * level indices: [ld] int32; kb = launch/source layer, klcl = LCL layer,
  * ktop = cloud-top layer (-1 unless active), kaux = deep: downdraft top layer
  * (-1 unless active) / shallow: LFC layer (-1 if none).
+ * Mass-flux profiles (kg m-2 s-1, [pver][ld], element type as T) describe the
+ * plume as a passive tracer sees it (conv_tracer_transport):
+ *   mu: updraft mass flux leaving layer k through its top interface;
+ *   du: updraft air detrained into layer k, carrying the plume value that
+ *       arrives from layer k+1;
+ *   md: downdraft mass flux leaving layer k through its bottom interface
+ *       (downward positive), all of which detrains into the layer below the
+ *       downdraft's lowest level.
+ * Deep: mu = M_b eta on ktop+1..kb, du = M_b eta(ktop+1) at ktop, md = M_b
+ * alpha eta_d on kaux..kb-1.  Shallow: mu = M_b on ktop+1..kb, du = M_b (1 -
+ * exp(-eps_s dz)) on the layers between ktop and the LCL layer and M_b at ktop,
+ * md = 0.  Every element is written (zero outside the plume and in inactive
+ * columns).  Writing them selects separate kernel instantiations, so runs
+ * without them are unaffected.  Not supported by conv_batch_* and
+ * conv_pipeline_* (CONV_ERR_UNSUPPORTED).
  * dTdt, dqdt, prec and flags are required; the rest may be NULL. */
 typedef struct {
   void* dTdt;
@@ -165,6 +180,9 @@ typedef struct {
   double* cape;
   double* mb;
   double* cons_err;
+  void* mu;
+  void* du;
+  void* md;
 } conv_out;
 
 /* Kernel variant.  CONV_PATH_PLAIN: one thread per column runs the whole scheme
@@ -295,6 +313,32 @@ conv_status conv_advance(const conv_grid* grid, void* T, void* q, const void* T_
                          const void* q_relax, double tau_relax, const conv_out* deep_out,
                          const conv_out* shallow_out, double dt, conv_precision prec,
                          conv_stream stream);
+
+/* ------------------------------------------------------------------ tracer transport
+ * Convective transport of passive tracers (a variant both cited schemes carry:
+ * ZM and UW move constituents with their plume mass fluxes, Sec. II-A; the
+ * paper times only the thermodynamic loops).  Each scheme mixes a tracer as it
+ * mixes its conserved moist static energy, with no source term, in flux form
+ * with upwind compensating subsidence, per layer
+ *   m_k dc_k/dt = mu_k (c_{k-1} - c_k) + du_k (cu_{k+1} - c_k)
+ *               + md_k (c_{k+1} - c_k) [+ md_{kb-1} (cd_{kb-1} - c_kb) at kb],
+ * with the updraft value cu (from kb upwards) and the downdraft value cd (from
+ * kaux downwards) mixed by their entrainment.
+ *
+ * deep_out / shallow_out: the conv_out of a run that wrote mu and du (deep also
+ * md), with flags, kb and ktop (deep also kaux); either may be NULL, not both.
+ * tracers: DEVICE [ntr][pver][ld] of the precision's type (tracer n at offset
+ * n*pver*ld); tend_deep / tend_shallow: the same layout, required with their
+ * scheme's outputs when ntr > 0; every element of the first n_cols columns is
+ * written.  With both schemes the shallow
+ * scheme transports max(c + dt*tend_deep, 0), the tracer after the deep update
+ * (Alg. 1 order, as conv_deep_shallow_run treats humidity).  ps: [ld] double
+ * (layer masses).  ntr >= 0; dt > 0 when both schemes are given.  Validation
+ * errors: CONV_ERR_ARG.  Asynchronous on `stream`; allocates nothing. */
+conv_status conv_tracer_transport(const conv_grid* grid, const double* ps,
+                                  const conv_out* deep_out, const conv_out* shallow_out,
+                                  double dt, int ntr, const void* tracers, void* tend_deep,
+                                  void* tend_shallow, conv_precision prec, conv_stream stream);
 
 /* ------------------------------------------------------------------ host pipeline
  * conv_deep_shallow_run on HOST buffers (no counterpart in the paper: there the

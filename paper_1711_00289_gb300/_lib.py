@@ -58,7 +58,8 @@ class Out(C.Structure):
     _fields_ = [("dTdt", C.c_void_p), ("dqdt", C.c_void_p), ("prec", C.c_void_p),
                 ("flags", C.c_void_p), ("kb", C.c_void_p), ("klcl", C.c_void_p),
                 ("ktop", C.c_void_p), ("kaux", C.c_void_p), ("cape", C.c_void_p),
-                ("mb", C.c_void_p), ("cons_err", C.c_void_p)]
+                ("mb", C.c_void_p), ("cons_err", C.c_void_p), ("mu", C.c_void_p),
+                ("du", C.c_void_p), ("md", C.c_void_p)]
 
 
 class Launch(C.Structure):
@@ -128,6 +129,8 @@ def lib(build: bool = True):
     L.conv_deep_shallow_adjoint.restype = st
     L.conv_advance.argtypes = [P(Grid), vp, vp, vp, vp, d, P(Out), P(Out), d, st, vp]
     L.conv_advance.restype = st
+    L.conv_tracer_transport.argtypes = [P(Grid), vp, P(Out), P(Out), d, st, vp, vp, vp, st, vp]
+    L.conv_tracer_transport.restype = st
     L.conv_pipeline_plan.argtypes = [P(Grid), st, st, P(vp)]
     L.conv_pipeline_plan.restype = st
     L.conv_pipeline_run.argtypes = [vp, P(In), P(DeepParams), P(ShallowParams), d, P(Out),

@@ -15,7 +15,8 @@ import torch
 from . import _lib as L
 
 _OUT_FIELDS = ("dTdt", "dqdt", "prec", "flags", "kb", "klcl", "ktop", "kaux", "cape", "mb",
-               "cons_err")
+               "cons_err", "mu", "du", "md")
+_FLUX_FIELDS = ("mu", "du", "md")
 _PREC = {"fp64": L.CONV_FP64, "mixed": L.CONV_MIXED}
 _PATH = {"auto": L.CONV_PATH_AUTO, "plain": L.CONV_PATH_PLAIN, "compact": L.CONV_PATH_COMPACT}
 
@@ -39,11 +40,14 @@ def _require_cuda(t, name, dtype, shape=None):
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
-def new_outputs(pver: int, ld: int, precision: str, device="cuda") -> dict:
-    """Allocate one scheme's output tensors."""
+def new_outputs(pver: int, ld: int, precision: str, device="cuda", flux: bool = False) -> dict:
+    """Allocate one scheme's output tensors; flux=True adds the mass-flux
+    profiles mu, du, md that tracer_transport needs."""
     rd = real_dtype(precision)
     f64, i32 = torch.float64, torch.int32
-    return dict(dTdt=torch.empty((pver, ld), dtype=rd, device=device),
+    extra = {k: torch.empty((pver, ld), dtype=rd, device=device) for k in _FLUX_FIELDS} \
+        if flux else {}
+    return dict(**extra, dTdt=torch.empty((pver, ld), dtype=rd, device=device),
                 dqdt=torch.empty((pver, ld), dtype=rd, device=device),
                 prec=torch.empty(ld, dtype=f64, device=device),
                 flags=torch.empty(ld, dtype=i32, device=device),
@@ -66,6 +70,9 @@ def _out_struct(o: dict, pver: int, ld: int, precision: str) -> L.Out:
     for k in ("flags", "kb", "klcl", "ktop", "kaux"):
         if o.get(k) is not None:
             _require_cuda(o[k], k, torch.int32, (ld,))
+    for k in _FLUX_FIELDS:
+        if o.get(k) is not None:
+            _require_cuda(o[k], k, rd, (pver, ld))
     return L.Out(*[_ptr(o.get(k)) for k in _OUT_FIELDS])
 
 
@@ -187,6 +194,64 @@ def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision
         C.byref(_out_struct(os_, pver, ld, precision)), C.byref(lc), wp, wn, _stream(stream))
     L.check(st, "conv_deep_shallow_run")
     return od, os_
+
+
+def tracer_transport(tracers, ps, vgrid: VerticalGrid, *, deep_out=None, shallow_out=None,
+                     dt: float = 1800.0, precision="fp64", n_cols=None, tend_deep=None,
+                     tend_shallow=None, stream=None):
+    """Convective transport of passive tracers ([ntr][pver][ld] tensor) by the
+    plumes of a run whose outputs hold the mass-flux profiles (new_outputs(...,
+    flux=True)).  Returns (tend_deep, tend_shallow) (None for a scheme not
+    given); with both schemes the shallow one transports the deep-updated
+    tracer max(c + dt tend_deep, 0)."""
+    rd = real_dtype(precision)
+    if tracers.dim() != 3 or not tracers.is_cuda or tracers.dtype != rd or \
+            not tracers.is_contiguous():
+        raise TypeError(f"tracers must be a contiguous CUDA {rd} tensor [ntr][pver][ld]")
+    ntr, pver, ld = tracers.shape
+    if pver != vgrid.pver:
+        raise ValueError(f"tracers have {pver} levels, the grid {vgrid.pver}")
+    n = ld if n_cols is None else int(n_cols)
+    _require_cuda(ps, "ps", torch.float64, (ld,))
+    if deep_out is None and shallow_out is None:
+        raise ValueError("give deep_out and/or shallow_out")
+    outs = []
+    for o, t in ((deep_out, tend_deep), (shallow_out, tend_shallow)):
+        if o is None:
+            outs.append((None, None))
+            continue
+        if t is None:
+            t = torch.empty_like(tracers)
+        elif t.shape != tracers.shape or t.dtype != rd or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("tendency tensors must match the tracers")
+        outs.append((_out_struct(o, pver, ld, precision), t))
+    g = vgrid.struct(n, ld)
+    (od, td), (os_, ts) = outs
+    st = L.lib().conv_tracer_transport(
+        C.byref(g), _ptr(ps), None if od is None else C.byref(od),
+        None if os_ is None else C.byref(os_), float(dt), int(ntr), _ptr(tracers), _ptr(td),
+        _ptr(ts), _PREC[precision], _stream(stream))
+    L.check(st, "conv_tracer_transport")
+    return td, ts
+
+
+def deep_shallow_tracers(T, q, ps, tracers, vgrid: VerticalGrid, *, dt: float = 1800.0,
+                         precision="fp64", lam=None, tau=None, deep_params=None,
+                         shallow_params=None, path="auto", n_cols=None, out_deep=None,
+                         out_shallow=None, workspace: Workspace | None = None, stream=None):
+    """The fused step with tracers: deep then shallow convection writing their
+    mass-flux profiles, then the transport of every tracer by both schemes.
+    Returns (deep_out, shallow_out, tend_deep, tend_shallow)."""
+    pver, ld = T.shape
+    od = out_deep if out_deep is not None else new_outputs(pver, ld, precision, T.device, True)
+    os_ = out_shallow if out_shallow is not None else new_outputs(pver, ld, precision,
+                                                                   T.device, True)
+    deep_shallow(T, q, ps, vgrid, dt=dt, precision=precision, lam=lam, tau=tau,
+                 deep_params=deep_params, shallow_params=shallow_params, path=path,
+                 n_cols=n_cols, out_deep=od, out_shallow=os_, workspace=workspace, stream=stream)
+    td, ts = tracer_transport(tracers, ps, vgrid, deep_out=od, shallow_out=os_, dt=dt,
+                              precision=precision, n_cols=n_cols, stream=stream)
+    return od, os_, td, ts
 
 
 def deep(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64", lam=None,
@@ -544,8 +609,8 @@ class HostPipeline:
 
     def __init__(self, vgrid: VerticalGrid, n_cols: int, ld: int, precision="mixed",
                  chunk_cols: int = 0):
-        # default: four chunks (measured on the 884,736-column grid: 3.66 ms per
-        # run against 3.83 with eight and 5.0 with 27; each chunk costs ~25 copies)
+        # default: four chunks (measured on the 884,736-column grid: 3.68 ms per
+        # run against 3.96 with two, 4.03 with eight and 5.4 with sixteen)
         if chunk_cols <= 0:
             chunk_cols = max(65536, -(-int(n_cols) // 4))
         if precision not in _PREC:

@@ -690,6 +690,7 @@ __device__ __forceinline__ Lcl lcl_solve(const Column<float>& c, int kstart, int
 // level by level as the scheme produces them.
 template <class R>
 struct OutCol {
+  static constexpr bool kFlux = false;
   R* dT;
   R* dq;
   size_t ld;
@@ -702,13 +703,50 @@ struct OutCol {
   __device__ __forceinline__ void zero(int k0, int k1) const {  // levels k0..k1-1
     for (int k = k0; k < k1; ++k) put(k, R(0), R(0));
   }
+  __device__ __forceinline__ void flux(int, R, R, R) const {}
+};
+
+// Tendencies plus the plume's mass-flux profiles (any of the three pointers may
+// be null): mu = updraft flux leaving layer k through its top, du = updraft air
+// detrained into layer k (carrying the plume value from layer k+1), md =
+// downdraft flux leaving layer k through its bottom.  A separate instantiation,
+// so the kernels without profile outputs are unchanged.
+template <class R>
+struct FluxCol {
+  static constexpr bool kFlux = true;
+  R* dT;
+  R* dq;
+  size_t ld;
+  int i;
+  R* mu;
+  R* du;
+  R* md;
+  __device__ __forceinline__ void put(int k, R a, R b) const {
+    const size_t o = (size_t)k * ld + i;
+    dT[o] = a;
+    dq[o] = b;
+  }
+  __device__ __forceinline__ void flux(int k, R u, R d, R m) const {
+    const size_t o = (size_t)k * ld + i;
+    if (mu) mu[o] = u;
+    if (du) du[o] = d;
+    if (md) md[o] = m;
+  }
+  __device__ __forceinline__ void zero(int k0, int k1) const {
+    for (int k = k0; k < k1; ++k) {
+      put(k, R(0), R(0));
+      flux(k, R(0), R(0), R(0));
+    }
+  }
 };
 
 // Discards tendencies (the adjoint recomputes the scheme for its tape only).
 template <class R>
 struct NoOut {
+  static constexpr bool kFlux = false;
   __device__ __forceinline__ void put(int, R, R) const {}
   __device__ __forceinline__ void zero(int, int) const {}
+  __device__ __forceinline__ void flux(int, R, R, R) const {}
 };
 
 // ---------------------------------------------------------------- deep scheme
@@ -1038,6 +1076,9 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
     const R a = mb * dT[k];
     const R b = mb * dq[k];
     out.put(k, a, b);
+    if constexpr (OUT::kFlux)  // mu = M_b eta above the top, all of it detrains at jt
+      out.flux(k, k > jt ? mb * eta[k] : R(0), k == jt ? mb * eta[jt + 1] : R(0),
+               (jd >= 0 && k >= jd && k < kb) ? mb * alpha * etad[k] : R(0));
     const R mk = c.m(k);
     sea.add(mk * a);
     swa.add(mk * b);
@@ -1052,9 +1093,9 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
 // Whole deep scheme for one column (T, q, ps set in c); writes every level of out.
 // bound (may be nullptr): set valid when the column did not trigger, the deep
 // trigger converged and the state is unchanged for the shallow scheme.
-template <class R>
+template <class R, class OUT>
 __device__ __forceinline__ void deep_column(const conv_deep_params& P, const DeepQ<R>& Q, R lam,
-                                            R tau, Column<R>& c, DeepOut& o, const OutCol<R>& out,
+                                            R tau, Column<R>& c, DeepOut& o, const OUT& out,
                                             DeepBound* bound = nullptr, bool* bound_ok = nullptr) {
   o.prec = o.cape = o.mb = o.cons = 0.0;
   o.flags = 0;
@@ -1269,11 +1310,13 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
         R hu1 = hsrc_env, qtu1 = qsrc, qp1 = qsrc, rf1 = R(0);
         R h_up = c.h(ks - 1), q_up = c.q(ks - 1);  // environment one level up
         R h_k1 = hsrc_env, q_k1 = qsrc;            // environment at k+1
-        auto emit = [&](int k, R dh, R dqv) {
+        // fu, fd: the level's mass-flux profile values (profile outputs only)
+        auto emit = [&](int k, R dh, R dqv, R fu, R fd) {
           const R rm = Mth<R>::dv(R(1), c.m(k));
           const R dqk = dqv * rm;
           const R dTk = (dh * rm - R(LV) * dqk) * R(1.0 / CP);
           out.put(k, dTk, dqk);
+          if constexpr (OUT::kFlux) out.flux(k, fu, fd, R(0));
           if constexpr (TP::kOn) tape->dT[k] = dTk;
           const R mk = c.m(k);
           sea.add(mk * dTk);
@@ -1281,7 +1324,8 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           sc += mk * Mth<R>::ab(dTk);
         };
         // the source layer's tendency (its formula does not depend on the top)
-        emit(ks, mb * (h_up - hsrc_env), mb * (q_up - qsrc));
+        emit(ks, mb * (h_up - hsrc_env), mb * (q_up - qsrc), mb, R(0));
+        R chi1 = R(0);  // mixing fraction of level k+1 (its detrainment per M_b)
         R w2 = Q.w2_0;
         const R eps = Q.eps;
         const bool drag = Q.drag;
@@ -1294,7 +1338,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
             h_up = c.h(k - 1);
             q_up = c.q(k - 1);
           }
-          R hu, qt;
+          R hu, qt, chik = R(0);
           if (k >= klcl) {
             hu = hu1;
             qt = qtu1;
@@ -1303,6 +1347,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
             const R chi = R(1) - Mth<R>::ex(-eps * dz);
             hu = hu1 + chi * (hk - hu1);
             qt = qtu1 + chi * (qk - qtu1);
+            chik = chi;
             if constexpr (TP::kOn) tape->chi[k] = chi;
           }
           const R pm = c.pm(k);
@@ -1342,7 +1387,8 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
             kts = k;
             // level k+1 (if not the source) is a regular level below the top
             if (k + 1 <= ks - 1) {
-              emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)));
+              emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)),
+                   mb, mb * chi1);
               sumr += rf1;
             }
             hu2 = hu1;
@@ -1359,9 +1405,11 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           }
           // the plume goes on above k: level k+1 is a regular level
           if (k + 1 <= ks - 1) {
-            emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)));
+            emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)),
+                 mb, mb * chi1);
             sumr += rf1;
           }
+          chi1 = chik;
           hu2 = hu1;
           qtu2 = qtu1;
           hu1 = hu;
@@ -1375,7 +1423,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
           exit_code = 4;
         } else {
           // top layer: detrainment of the plume arriving from kts+1
-          emit(kts, mb * (hu2 - h_k1), mb * (qtu2 - q_k1));
+          emit(kts, mb * (hu2 - h_k1), mb * (qtu2 - q_k1), R(0), mb);
         }
       }
     }

@@ -74,8 +74,13 @@ cvg::OutP to_outp(const conv_out* o) {
   p.cape = o->cape;
   p.mb = o->mb;
   p.cons_err = o->cons_err;
+  p.mu = o->mu;
+  p.du = o->du;
+  p.md = o->md;
   return p;
 }
+
+bool has_flux(const cvg::OutP& o) { return o.mu || o.du || o.md; }
 
 // AUTO selects the compacted path; a shallow-only run has nothing to compact
 // (no deep trigger) and always uses the plain kernel.
@@ -98,6 +103,7 @@ conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch,
     return CONV_ERR_ARG;
   if (launch && (launch->block_threads < 0 || launch->block_threads > 1024)) return CONV_ERR_ARG;
   const int path = pick_path(launch, a.mode);
+  a.flux = has_flux(a.od) || has_flux(a.os);
   a.block = launch ? launch->block_threads : 0;
   for (int i = 0; i < 3; ++i)
     a.ev[i] = (launch && launch->stage_events)
@@ -239,6 +245,49 @@ conv_status conv_deep_shallow_run(const conv_grid* grid, const conv_in* in,
   return dispatch(a, prec, launch, ws, ws_bytes);
 }
 
+conv_status conv_tracer_transport(const conv_grid* grid, const double* ps,
+                                  const conv_out* deep_out, const conv_out* shallow_out,
+                                  double dt, int ntr, const void* tracers, void* tend_deep,
+                                  void* tend_shallow, conv_precision prec, conv_stream stream) {
+  if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
+  RunArgs g;
+  std::memset(&g, 0, sizeof g);
+  conv_status s = fill_grid(grid, g);
+  if (s != CONV_OK) return s;
+  if (!ps || ntr < 0 || (!deep_out && !shallow_out)) return CONV_ERR_ARG;
+  if (ntr > 0 && !tracers) return CONV_ERR_ARG;
+  if (deep_out && shallow_out && !(std::isfinite(dt) && dt > 0.0)) return CONV_ERR_ARG;
+  if (ntr > 0 && ((deep_out && !tend_deep) || (shallow_out && !tend_shallow)))
+    return CONV_ERR_ARG;
+  cvg::TrArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.L = g.L;
+  a.n = g.n;
+  a.ld = g.ld;
+  a.pver = g.L.pver;
+  a.ntr = ntr;
+  a.tstride = (size_t)g.L.pver * (size_t)g.ld;
+  a.ps = ps;
+  a.tr = tracers;
+  a.dt = dt;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  const conv_out* outs[2] = {deep_out, shallow_out};
+  cvg::TrScheme* sch[2] = {&a.d, &a.s};
+  void* tends[2] = {tend_deep, tend_shallow};
+  for (int m = 0; m < 2; ++m) {
+    const conv_out* o = outs[m];
+    if (!o) continue;
+    if (!o->mu || !o->du || !o->flags || !o->kb || !o->ktop) return CONV_ERR_ARG;
+    const bool down = m == 0 && o->md;
+    if (down && !o->kaux) return CONV_ERR_ARG;
+    *sch[m] = cvg::TrScheme{o->mu, o->du, down ? o->md : nullptr, o->flags, o->kb, o->ktop,
+                            down ? o->kaux : nullptr, tends[m]};
+  }
+  a.has_d = deep_out != nullptr;
+  a.has_s = shallow_out != nullptr;
+  return cvg::launch_transport(a, prec == CONV_FP64) == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
+
 conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
                               const conv_deep_params* par, double dt, conv_precision prec,
                               const double* gP, const double* gH, const double* w_heat,
@@ -378,6 +427,7 @@ conv_status conv_batch_plan(const conv_member* members, int n_members, conv_prec
     a.sp = mb.shallow;
     a.od = to_outp(&mb.deep_out);
     a.os = to_outp(&mb.shallow_out);
+    if (has_flux(a.od) || has_flux(a.os)) return CONV_ERR_UNSUPPORTED;
     a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
     a.stream = nullptr;
     cvg::fill_q(a);

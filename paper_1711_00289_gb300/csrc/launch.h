@@ -24,6 +24,9 @@ struct OutP {
   double* cape;
   double* mb;
   double* cons_err;
+  void* mu;  // mass-flux profiles (optional; FluxCol instantiations only)
+  void* du;
+  void* md;
 };
 
 struct RunArgs {
@@ -43,6 +46,7 @@ struct RunArgs {
   ShalQ<float> sqf;
   ShalQ<double> sqd;
   OutP od, os;
+  bool flux;  // some mass-flux profile requested: run the FluxCol instantiations
   int mode;
   int block;
   cudaStream_t stream;
@@ -81,9 +85,22 @@ __device__ __forceinline__ Src<R> after_deep_src(const RunArgs& a, int i, bool b
                 static_cast<const R*>(a.od.dTdt), static_cast<const R*>(a.od.dqdt), (R)a.dt,
                 (size_t)a.ld, i, !bad};
 }
+template <class R, bool F>
+struct OutSel {
+  using type = OutCol<R>;
+};
 template <class R>
-__device__ __forceinline__ OutCol<R> out_col(const OutP& o, const RunArgs& a, int i) {
-  return OutCol<R>{static_cast<R*>(o.dTdt), static_cast<R*>(o.dqdt), (size_t)a.ld, i};
+struct OutSel<R, true> {
+  using type = FluxCol<R>;
+};
+template <class R, bool F = false>
+__device__ __forceinline__ typename OutSel<R, F>::type out_col(const OutP& o, const RunArgs& a,
+                                                               int i) {
+  if constexpr (F)
+    return FluxCol<R>{static_cast<R*>(o.dTdt), static_cast<R*>(o.dqdt), (size_t)a.ld, i,
+                      static_cast<R*>(o.mu), static_cast<R*>(o.du), static_cast<R*>(o.md)};
+  else
+    return OutCol<R>{static_cast<R*>(o.dTdt), static_cast<R*>(o.dqdt), (size_t)a.ld, i};
 }
 
 __device__ __forceinline__ void store_deep_scalars(const RunArgs& a, int i, const DeepOut& o) {
@@ -113,6 +130,30 @@ __device__ __forceinline__ void store_shallow_scalars(const RunArgs& a, int i, c
 
 // Plain path: one thread per column, whole scheme, no compaction.
 cudaError_t launch_plain(const RunArgs& a, bool fp64);
+
+// Tracer transport (transport.cu): one scheme's plume as a tracer sees it.
+struct TrScheme {
+  const void* mu;
+  const void* du;
+  const void* md;  // deep downdraft (nullptr: none)
+  const int32_t* flags;
+  const int32_t* kb;
+  const int32_t* ktop;
+  const int32_t* kaux;
+  void* tend;
+};
+struct TrArgs {
+  Levels L;
+  int n, ld, pver, ntr;
+  size_t tstride;  // pver * ld: offset between tracers
+  const double* ps;
+  const void* tr;
+  double dt;
+  TrScheme d, s;
+  bool has_d, has_s;
+  cudaStream_t stream;
+};
+cudaError_t launch_transport(const TrArgs& a, bool fp64);
 
 // Heating weights of the adjoint's objective, passed by value in the launch.
 struct AdjW {

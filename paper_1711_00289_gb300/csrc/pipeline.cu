@@ -152,6 +152,8 @@ conv_status conv_pipeline_run(conv_pipeline* p, const conv_in* host_in,
       !host_deep || !host_shallow || !host_deep->dTdt || !host_deep->dqdt ||
       !host_shallow->dTdt || !host_shallow->dqdt)
     return CONV_ERR_ARG;
+  for (const conv_out* h : {host_deep, host_shallow})
+    if (h->mu || h->du || h->md) return CONV_ERR_UNSUPPORTED;
   const int n = p->grid.n_cols, pver = p->grid.pver, ch = p->chunk;
   const size_t es = p->es, hp = (size_t)p->grid.ld * es, dp = (size_t)ch * es;
   const cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);

@@ -192,3 +192,46 @@ def test_pipeline_plan_validated_before_touching_a_device():
                                  C.byref(L.shallow_defaults()), 1800.0, C.byref(out),
                                  C.byref(out), None) == L.CONV_ERR_ARG
     lib.conv_pipeline_free(None)
+
+
+def test_tracer_transport_arguments_checked_on_host():
+    """conv_tracer_transport rejects bad arguments before any launch (n_cols = 0
+    throughout, so nothing would run even if a check were missing)."""
+    g, _, out, keep = _args()
+    lib = L.lib()
+    fake = C.c_void_p(0x1000)
+    flux = L.Out(fake, fake, fake, fake, fake, None, fake, fake, None, None, None, fake, fake, fake)
+
+    def call(d, s, ntr=1, tr=fake, td=fake, ts=fake, dt=1800.0, prec=L.CONV_FP64, ps=fake):
+        return lib.conv_tracer_transport(C.byref(g), ps, None if d is None else C.byref(d),
+                                         None if s is None else C.byref(s), dt, ntr, tr, td, ts,
+                                         prec, None)
+
+    assert call(flux, flux) == L.CONV_OK  # valid (nothing to do for 0 columns)
+    assert call(None, None) == L.CONV_ERR_ARG
+    assert call(flux, flux, ntr=-1) == L.CONV_ERR_ARG
+    assert call(flux, flux, tr=None) == L.CONV_ERR_ARG
+    assert call(flux, flux, ps=None) == L.CONV_ERR_ARG
+    assert call(flux, None, td=None) == L.CONV_ERR_ARG
+    assert call(None, flux, ts=None) == L.CONV_ERR_ARG
+    assert call(flux, flux, dt=0.0) == L.CONV_ERR_ARG
+    assert call(flux, flux, prec=7) == L.CONV_ERR_ARG
+    assert call(None, out) == L.CONV_ERR_ARG  # no mass-flux profiles in this output set
+    no_kaux = L.Out(fake, fake, fake, fake, fake, None, fake, None, None, None, None, fake, fake,
+                    fake)
+    assert call(no_kaux, None) == L.CONV_ERR_ARG  # deep downdraft without its top layer
+    assert call(None, no_kaux) == L.CONV_OK  # the shallow scheme has no downdraft
+
+
+def test_batch_rejects_mass_flux_outputs():
+    g, inp, out, keep = _args(n=0)
+    fake = C.c_void_p(0x1000)
+    mb = L.Member()
+    mb.grid, mb.in_ = g, inp
+    mb.deep_out = L.Out(fake, fake, fake, fake, None, None, None, None, None, None, None, fake)
+    mb.shallow_out = out
+    mb.deep, mb.shallow = L.deep_defaults(), L.shallow_defaults()
+    mb.dt = 1800.0
+    h = C.c_void_p()
+    st = L.lib().conv_batch_plan(C.byref(mb), 1, L.CONV_FP64, C.byref(h))
+    assert st == L.CONV_ERR_UNSUPPORTED
