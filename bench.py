@@ -605,7 +605,8 @@ def transport_bench(args, dev, g, ntr=25):
             "gpu_launches_per_call": 1,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "algorithmic_bytes": alg,
-                         "traffic": ncu_traffic(g.name + "-transport").get("k_transport"),
+                         "traffic": ncu_traffic(g.name + "-tracers25", "transport").get(
+                             "k_transport"),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
 
 
@@ -617,27 +618,37 @@ def l2_note(prec, n, pver):
             f"HBM-representative")
 
 
-def kernel_sources_sha256():
-    """Digest of the CUDA sources, to match an ncu capture to the kernels it measured."""
+# the sources each measured kernel is compiled from (an ncu capture stays valid
+# while none of them changes)
+KERNEL_SOURCES = {
+    "step": ("paper_1711_00289_gb300/csrc/column.cuh", "paper_1711_00289_gb300/csrc/compact.cu",
+             "paper_1711_00289_gb300/csrc/compact.h", "paper_1711_00289_gb300/csrc/launch.h",
+             "include/conv.h"),
+    "transport": ("paper_1711_00289_gb300/csrc/transport.cu", "paper_1711_00289_gb300/csrc/column.cuh",
+                  "paper_1711_00289_gb300/csrc/launch.h", "include/conv.h"),
+}
+
+
+def kernel_sources_sha256(group="step"):
+    """Digest of the CUDA sources of a kernel group, to match an ncu capture to
+    the kernels it measured."""
     import hashlib
     h = hashlib.sha256()
-    for d in (os.path.join(ROOT, "paper_1711_00289_gb300", "csrc"), os.path.join(ROOT, "include")):
-        for name in sorted(os.listdir(d)):
-            if name.endswith((".cu", ".cuh", ".h")):
-                h.update(name.encode())
-                with open(os.path.join(d, name), "rb") as fh:
-                    h.update(fh.read())
+    for rel in KERNEL_SOURCES[group]:
+        h.update(rel.encode())
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 
-def ncu_traffic(workload):
+def ncu_traffic(workload, group="step"):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each
     kernel from the ncu capture summarised under profiles/, if it was taken of
     these sources on this workload; otherwise {} (traffic is then reported null).
     Records are lines `traffic-record: sha256=<digest> workload=<name>
     <kernel>=<bytes> ...`."""
     d = os.path.join(ROOT, "profiles")
-    want = kernel_sources_sha256()
+    want = kernel_sources_sha256(group)
     out = {}
     for name in sorted(os.listdir(d)) if os.path.isdir(d) else []:
         if not name.endswith(".md"):
