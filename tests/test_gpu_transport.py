@@ -178,22 +178,25 @@ def test_profile_outputs_leave_the_step_unchanged(precision):
                 assert (np.abs(x[k] - y[k]).max(axis=0) / den)[same].max() <= 1e-5
 
 
-def test_full_resolution_properties():
-    """884,736 columns x 30 levels, mixed path with 2 tracers: every column
-    conserves tracer mass, a uniform tracer stays unchanged, and inactive columns
-    get exact zeros."""
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_full_resolution_against_oracle(oracle, precision):
+    """884,736 columns x 30 levels, the launch configuration of the benchmark
+    (compacted step, then one transport launch), 2 tracers: every column against
+    the oracle (FP64: within 1e-10 of the natural scale; mixed: 1e-3 on columns
+    whose decisions agree), plus the exact properties -- a uniform tracer stays
+    unchanged, tracer mass is conserved, inactive columns get exact zeros."""
     import torch
 
     from paper_1711_00289_gb300 import api
 
     g = S.clustered_grid(0.3)
     n = g.n_cols
-    T, q, ps, lam, tau = to_device(g, "mixed")
+    T, q, ps, lam, tau = to_device(g, precision)
     vg = api.VerticalGrid(g.hyai, g.hybi)
-    tr = torch.empty((2, g.pver, n), device="cuda")
-    tr[0] = 1.0
-    tr[1] = torch.tensor(g.q, device="cuda").float()
-    od, os_, td, ts = api.deep_shallow_tracers(T, q, ps, tr, vg, dt=g.dt, precision="mixed",
+    rd = api.real_dtype(precision)
+    tr_np = np.stack([np.ones((g.pver, n)), g.q])
+    tr = torch.tensor(tr_np, device="cuda").to(rd)
+    od, os_, td, ts = api.deep_shallow_tracers(T, q, ps, tr, vg, dt=g.dt, precision=precision,
                                               lam=lam, tau=tau)
     torch.cuda.synchronize()
     m = torch.tensor(layer_mass(g), device="cuda")
@@ -201,11 +204,44 @@ def test_full_resolution_properties():
         act = (o["flags"] & 2) > 0
         assert int(act.sum()) > 10000
         rate = ((o["mu"] + o["du"] + o["md"]).double() / m).amax(dim=0)
-        assert float((t[0].double().abs().amax(dim=0) / (rate + 1e-300))[act].max()) <= 1e-5, tag
+        uni = float((t[0].double().abs().amax(dim=0) / (rate + 1e-300))[act].max())
+        assert uni <= (1e-13 if precision == "fp64" else 1e-5), (tag, uni)
         net = (m * t[1].double()).sum(dim=0).abs()
         tot = (m * t[1].double().abs()).sum(dim=0) + 1e-300
-        assert float((net / tot)[act].max()) <= 1e-4, tag
+        assert float((net / tot)[act].max()) <= (1e-12 if precision == "fp64" else 1e-4), tag
         assert bool((t[:, :, ~act] == 0).all()), tag
+    rtd, rts, rfd, rfs = oracle.deep_shallow_tracers(g, tr_np, threads=THREADS)
+    gd = {k: v.cpu().numpy() for k, v in od.items()}
+    gs = {k: v.cpu().numpy() for k, v in os_.items()}
+    rdo, rso = oracle.deep_shallow(g, threads=THREADS)
+    if precision == "fp64":
+        same_d = np.ones(n, bool)
+        same_s = same_d
+        for k in ("flags", "kb", "ktop", "kaux"):
+            assert np.array_equal(gd[k], rdo[k]) and np.array_equal(gs[k], rso[k]), k
+        tol = 1e-10
+    else:
+        same_d = same_decisions(gd, rdo)
+        same_s = same_d & same_decisions(gs, rso)
+        assert (~same_s).sum() <= 2e-3 * n
+        tol = 1e-3
+    for got, ref, f, same, tag in ((td, rtd, rfd, same_d, "deep"),
+                                   (ts, rts, rfs, same_s, "shallow")):
+        err = (np.abs(got.double().cpu().numpy() - ref).max(axis=1) / _scale(tr_np, f, g))
+        assert err[:, same].max() <= tol, f"{tag}: {err[:, same].max():.3g}"
+
+
+@pytest.mark.parametrize("pver", [8, 32])
+def test_other_level_counts(oracle, pver):
+    """Fewest and most levels the library takes a tile of (32 = the maximum)."""
+    g = S.clustered_grid(0.4, 24, 36, pver=pver)
+    n = g.n_cols
+    tr = _tracers(g, n)
+    gd, gs, td, ts, _ = _gpu_step(g, "fp64", "compact", n, tr)
+    rtd, rts, rfd, rfs = oracle.deep_shallow_tracers(g, tr, threads=THREADS)
+    for got, ref, f, tag in ((td, rtd, rfd, "deep"), (ts, rts, rfs, "shallow")):
+        err = np.abs(got - ref).max(axis=1) / _scale(tr, f, g)
+        assert err.max() <= 1e-10, f"{tag} pver={pver}: {err.max():.3g}"
 
 
 def test_edge_cases(oracle):
