@@ -196,6 +196,52 @@ def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision
     return od, os_
 
 
+class PreparedStep:
+    """The fused deep -> shallow step with its C-ABI arguments marshalled once,
+    for launch-bound loops: each call is one library call (the library records
+    the optional stage events and launches its kernels), with no Python
+    validation or struct building on the way.  The tensors given here must stay
+    alive and in place while the object is used."""
+
+    def __init__(self, T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0,
+                 precision="fp64", lam=None, tau=None, deep_params=None, shallow_params=None,
+                 path="auto", block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
+                 workspace: Workspace | None = None, stream=None):
+        pver, ld, n, self._inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
+        self.out_deep = out_deep if out_deep is not None else new_outputs(pver, ld, precision,
+                                                                          T.device)
+        self.out_shallow = out_shallow if out_shallow is not None else new_outputs(
+            pver, ld, precision, T.device)
+        self._keep = (T, q, ps, lam, tau)
+        self._dp = deep_params or L.deep_defaults()
+        self._sp = shallow_params or L.shallow_defaults()
+        self._g = vgrid.struct(n, ld)
+        self._path, self._block = path, int(block_threads)
+        lc = _launch(path, block_threads)
+        nb = int(L.lib().conv_workspace_bytes(C.byref(self._g), _PREC[precision], C.byref(lc)))
+        self._ws = _ws_for(T.device, workspace)
+        self._wp, self._wn = self._ws.get(nb)
+        self._od = _out_struct(self.out_deep, pver, ld, precision)
+        self._os = _out_struct(self.out_shallow, pver, ld, precision)
+        self._args = (C.byref(self._g), C.byref(self._inp), C.byref(self._dp),
+                      C.byref(self._sp), float(dt), _PREC[precision], C.byref(self._od),
+                      C.byref(self._os))
+        self._tail = (self._wp, self._wn, _stream(stream))
+        self._lc = lc
+        self._fn = L.lib().conv_deep_shallow_run
+
+    def launch_struct(self, stage_events=None) -> L.Launch:
+        """A launch descriptor with stage events, to build outside a timed loop."""
+        return _launch(self._path, self._block, stage_events)
+
+    def __call__(self, launch: L.Launch | None = None):
+        st = self._fn(*self._args, C.byref(launch if launch is not None else self._lc),
+                      *self._tail)
+        if st != L.CONV_OK:
+            L.check(st, "conv_deep_shallow_run")
+        return self.out_deep, self.out_shallow
+
+
 def tracer_transport(tracers, ps, vgrid: VerticalGrid, *, deep_out=None, shallow_out=None,
                      dt: float = 1800.0, precision="fp64", n_cols=None, tend_deep=None,
                      tend_shallow=None, stream=None):

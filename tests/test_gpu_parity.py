@@ -11,7 +11,7 @@ import pytest
 
 from paper_1711_00289_gb300 import soundings as S
 from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu,
-                            same_decisions)
+                            same_decisions, to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -220,3 +220,28 @@ def test_workspace_errors():
     assert run(*args, C.c_void_p(base + 8), need, None) == L.CONV_ERR_WORKSPACE
     assert run(*args, C.c_void_p(base), need, None) == L.CONV_OK
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_prepared_step_matches_call(precision):
+    """api.PreparedStep (arguments marshalled once) gives bit-identical outputs to
+    api.deep_shallow, with and without stage events, call after call."""
+    import torch
+
+    from paper_1711_00289_gb300 import api
+
+    g = S.clustered_grid(0.3, 48, 72)
+    T, q, ps, lam, tau = to_device(g, precision)
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    a = api.deep_shallow(T, q, ps, vg, dt=g.dt, precision=precision, lam=lam, tau=tau,
+                         path="compact")
+    run = api.PreparedStep(T, q, ps, vg, dt=g.dt, precision=precision, lam=lam, tau=tau,
+                           path="compact")
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for launch in (None, run.launch_struct(evs), None):
+        b = run(launch)
+        torch.cuda.synchronize()
+        for x, y in zip(a, b):
+            for k in x:
+                assert torch.equal(x[k], y[k]), k
+    assert evs[0].elapsed_time(evs[2]) > 0.0
