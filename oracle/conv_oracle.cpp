@@ -185,6 +185,7 @@ struct DeepP {
 struct ShalP {
   double eps_s, tke, c_m, cin_scale, cin_max, a_w, b_w, ql_crit, p_lcl_min, p_lfc_min, p_top_lim;
   int n_lcl, n_h;
+  double evap_k;
 };
 DeepP to_deep(const oracle_deep_params* p) {
   return DeepP{p->capelmt, p->lambda_default, p->tau_default, p->c0, p->alpha_dd,
@@ -194,7 +195,7 @@ DeepP to_deep(const oracle_deep_params* p) {
 ShalP to_shal(const oracle_shallow_params* p) {
   return ShalP{p->eps_s, p->tke, p->c_m, p->cin_scale, p->cin_max, p->a_w, p->b_w,
                p->ql_crit, p->p_lcl_min, p->p_lfc_min, p->p_top_lim, p->n_newton_lcl,
-               p->n_newton_h};
+               p->n_newton_h, p->evap_k};
 }
 
 // ---------------------------------------------------------------- thermodynamics
@@ -751,6 +752,26 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
   R sumr(0.0);
   for (int k = ks - 1; k > kts; --k) sumr = sumr + s.rf[k];
   s.prec = mb * sumr;
+
+  // Variant (off when evap_k = 0): evaporation of the falling rain.  Rain made
+  // in plume layer k (kts < k < ks) falls through the environment layers below
+  // it; each layer j takes the fraction 1 - exp(-evap_k max(qs_j - q_j, 0) dz_j)
+  // of the flux arriving from above, which moistens and cools that layer
+  // (dq = E/m, dT = -Lv E/(cp m)); what reaches the surface is the precipitation.
+  if (P.evap_k > 0.0) {
+    R F(0.0);
+    for (int j = kts + 1; j <= ks; ++j) {
+      const R dz = s.z_int[j] - s.z_int[j + 1];
+      R def = sat_qs(T[j], s.p_mid[j]) - q[j];
+      if (val(def) < 0.0) def = R(0.0);
+      const R E = F * (1.0 - exp(-P.evap_k * def * dz));
+      F = F - E;
+      s.dq[j] = s.dq[j] + E / s.m[j];
+      s.dT[j] = s.dT[j] - LV * E / (CP * s.m[j]);
+      if (j < ks) F = F + mb * s.rf[j];
+    }
+    s.prec = F;
+  }
 
   double se = 0.0, sw = 0.0, scale = 0.0;
   for (int k = 0; k < pver; ++k) {

@@ -35,6 +35,7 @@ typedef struct {
   double eps_s, tke, c_m, cin_scale, cin_max, a_w, b_w, ql_crit;
   double p_lcl_min, p_lfc_min, p_top_lim;
   int32_t n_newton_lcl, n_newton_h;
+  double evap_k; /* rain evaporation coefficient, 1/(kg/kg)/m; 0 = off */
 } oracle_shallow_params;
 
 /* Outputs of one scheme over n_cols columns (any pointer but flags may be NULL). */

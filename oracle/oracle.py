@@ -47,7 +47,7 @@ class ShallowParams(C.Structure):
                 ("cin_scale", C.c_double), ("cin_max", C.c_double), ("a_w", C.c_double),
                 ("b_w", C.c_double), ("ql_crit", C.c_double), ("p_lcl_min", C.c_double),
                 ("p_lfc_min", C.c_double), ("p_top_lim", C.c_double),
-                ("n_newton_lcl", C.c_int32), ("n_newton_h", C.c_int32)]
+                ("n_newton_lcl", C.c_int32), ("n_newton_h", C.c_int32), ("evap_k", C.c_double)]
 
 
 def deep_params(**kw) -> DeepParams:
@@ -61,7 +61,7 @@ def deep_params(**kw) -> DeepParams:
 def shallow_params(**kw) -> ShallowParams:
     d = dict(eps_s=2e-3, tke=1.0, c_m=0.03, cin_scale=10.0, cin_max=50.0, a_w=1.0, b_w=2.0,
              ql_crit=1e-3, p_lcl_min=70000.0, p_lfc_min=50000.0, p_top_lim=4000.0,
-             n_newton_lcl=6, n_newton_h=4)
+             n_newton_lcl=6, n_newton_h=4, evap_k=0.0)
     d.update(kw)
     return ShallowParams(**d)
 
