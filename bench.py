@@ -545,9 +545,11 @@ def transport_bench(args, dev, g, ntr=25):
     timed alone with CUDA events, its algorithmic HBM bytes counted from the
     plumes' extents (tendencies written everywhere; tracers read on the levels
     a plume touches; mass-flux profiles, flags and levels once per column), and
-    the fused step with and without the profile outputs."""
+    the fused step with and without the profile outputs and with the shallow
+    rain-evaporation variant."""
     import torch
 
+    from paper_1711_00289_gb300 import _lib as L
     from paper_1711_00289_gb300 import api
 
     n, pver = g.n_cols, g.pver
@@ -580,12 +582,19 @@ def transport_bench(args, dev, g, ntr=25):
         return e0.elapsed_time(e1) / reps
 
     reps = max(3, args.steps)
-    step_flux = ev_time(lambda: api.deep_shallow(T, q, ps, vg, dt=g.dt, precision="mixed",
-                                                 tau=tau, out_deep=od, out_shallow=os_,
-                                                 workspace=ws), reps)
-    step_plain = ev_time(lambda: api.deep_shallow(T, q, ps, vg, dt=g.dt, precision="mixed",
-                                                  tau=tau, out_deep=od0, out_shallow=os0,
-                                                  workspace=ws), reps)
+    step_flux = ev_time(api.PreparedStep(T, q, ps, vg, dt=g.dt, precision="mixed", tau=tau,
+                                         out_deep=od, out_shallow=os_, workspace=ws), reps)
+    step_plain = ev_time(api.PreparedStep(T, q, ps, vg, dt=g.dt, precision="mixed", tau=tau,
+                                          out_deep=od0, out_shallow=os0, workspace=ws), reps)
+    # the shallow rain-evaporation variant (extended kernels), coefficient 0.05
+    sp = L.shallow_defaults()
+    sp.evap_k = 0.05
+    od1 = api.new_outputs(pver, n, "mixed", dev)
+    os1 = api.new_outputs(pver, n, "mixed", dev)
+    step_evap = ev_time(api.PreparedStep(T, q, ps, vg, dt=g.dt, precision="mixed", tau=tau,
+                                         shallow_params=sp, out_deep=od1, out_shallow=os1,
+                                         workspace=ws), reps)
+    p_off, p_on = float(os0["prec"].sum()), float(os1["prec"].sum())
     ms = ev_time(lambda: api.tracer_transport(tr, ps, vg, deep_out=od, shallow_out=os_, dt=g.dt,
                                               precision="mixed", tend_deep=td, tend_shallow=ts),
                  reps)
@@ -611,6 +620,8 @@ def transport_bench(args, dev, g, ntr=25):
     return {"tracers": ntr, "columns": n, "levels": pver, "precision": "mixed",
             "ms_transport": ms, "value": ntr * n / (ms * 1e-3), "unit": "tracer-columns/s",
             "ms_step_with_profiles": step_flux, "ms_step_without_profiles": step_plain,
+            "shallow_evaporation": {"evap_k": 0.05, "ms_step": step_evap,
+                                    "shallow_rain_evaporated": 1.0 - p_on / max(p_off, 1e-300)},
             "gpu_launches_per_call": 1,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "algorithmic_bytes": alg,

@@ -133,6 +133,13 @@ typedef struct {
   double p_top_lim; /* Pa [4e3]                                                */
   int32_t n_newton_lcl;
   int32_t n_newton_h;
+  double evap_k;    /* rain evaporation variant, 1/((kg/kg) m) [0 = off]: rain made
+                       in a plume layer falls through the layers below it, each
+                       taking the fraction 1 - exp(-evap_k max(qs - q, 0) dz) of
+                       the flux arriving from above (moistening and cooling it);
+                       the rest is the precipitation.  > 0 runs the extended
+                       kernel instantiations; not supported by conv_batch_* and
+                       the adjoints (CONV_ERR_UNSUPPORTED). */
 } conv_shallow_params;
 
 /* Inputs (DEVICE pointers). T,q: [pver][ld] double (FP64) or float (MIXED);

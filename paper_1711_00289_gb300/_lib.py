@@ -46,7 +46,7 @@ class ShallowParams(C.Structure):
                 ("cin_scale", C.c_double), ("cin_max", C.c_double), ("a_w", C.c_double),
                 ("b_w", C.c_double), ("ql_crit", C.c_double), ("p_lcl_min", C.c_double),
                 ("p_lfc_min", C.c_double), ("p_top_lim", C.c_double),
-                ("n_newton_lcl", C.c_int32), ("n_newton_h", C.c_int32)]
+                ("n_newton_lcl", C.c_int32), ("n_newton_h", C.c_int32), ("evap_k", C.c_double)]
 
 
 class In(C.Structure):

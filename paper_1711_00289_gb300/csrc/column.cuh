@@ -375,6 +375,7 @@ struct ShalQ {
   R p_top_lim, p_lfc_min, p_lcl_min, eps, w2_0, m2beps, aw_beps, aw2, ql_crit;
   R cm_sqrt_tke;  // c_m sqrt(tke)
   R m_inv_cin;    // -1 / (cin_scale tke)
+  R evap_k;       // rain evaporation coefficient (0: off)
   bool drag;      // b_w eps_s > 0
 };
 template <class R>
@@ -398,6 +399,7 @@ inline ShalQ<R> make_shal_q(const conv_shallow_params& P) {
   q.ql_crit = (R)P.ql_crit;
   q.cm_sqrt_tke = (R)(P.c_m * std::sqrt(P.tke));
   q.m_inv_cin = (R)(-1.0 / (P.cin_scale * P.tke));
+  q.evap_k = (R)P.evap_k;
   return q;
 }
 
@@ -691,6 +693,7 @@ __device__ __forceinline__ Lcl lcl_solve(const Column<float>& c, int kstart, int
 template <class R>
 struct OutCol {
   static constexpr bool kFlux = false;
+  static constexpr bool kExt = false;  // the extended instantiation (FluxCol)
   R* dT;
   R* dq;
   size_t ld;
@@ -706,14 +709,16 @@ struct OutCol {
   __device__ __forceinline__ void flux(int, R, R, R) const {}
 };
 
-// Tendencies plus the plume's mass-flux profiles (any of the three pointers may
-// be null): mu = updraft flux leaving layer k through its top, du = updraft air
-// detrained into layer k (carrying the plume value from layer k+1), md =
-// downdraft flux leaving layer k through its bottom.  A separate instantiation,
-// so the kernels without profile outputs are unchanged.
+// The extended instantiation's writer: tendencies plus the plume's mass-flux
+// profiles (any of the three pointers may be null): mu = updraft flux leaving
+// layer k through its top, du = updraft air detrained into layer k (carrying
+// the plume value from layer k+1), md = downdraft flux leaving layer k through
+// its bottom.  Kernels instantiated with it also run the scheme variants
+// (shallow rain evaporation); the default kernels are compiled without either.
 template <class R>
 struct FluxCol {
   static constexpr bool kFlux = true;
+  static constexpr bool kExt = true;
   R* dT;
   R* dq;
   size_t ld;
@@ -732,6 +737,13 @@ struct FluxCol {
     if (du) du[o] = d;
     if (md) md[o] = m;
   }
+  // read back and increment a level this thread has written
+  __device__ __forceinline__ R dT_at(int k) const { return dT[(size_t)k * ld + i]; }
+  __device__ __forceinline__ void add(int k, R a, R b) const {
+    const size_t o = (size_t)k * ld + i;
+    dT[o] += a;
+    dq[o] += b;
+  }
   __device__ __forceinline__ void zero(int k0, int k1) const {
     for (int k = k0; k < k1; ++k) {
       put(k, R(0), R(0));
@@ -744,6 +756,7 @@ struct FluxCol {
 template <class R>
 struct NoOut {
   static constexpr bool kFlux = false;
+  static constexpr bool kExt = false;
   __device__ __forceinline__ void put(int, R, R) const {}
   __device__ __forceinline__ void zero(int, int) const {}
   __device__ __forceinline__ void flux(int, R, R, R) const {}
@@ -1251,6 +1264,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
   const R hsrc = c.h(ks);
   Acc<R> sea, swa;
   R sc = R(0), sumr = R(0);
+  R pevap = R(-1);  // precipitation after evaporation (variant; < 0: none)
   if (pL < P.p_lcl_min || klcl < ktl) {
     exit_code = 1;
   } else {
@@ -1326,6 +1340,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
         // the source layer's tendency (its formula does not depend on the top)
         emit(ks, mb * (h_up - hsrc_env), mb * (q_up - qsrc), mb, R(0));
         R chi1 = R(0);  // mixing fraction of level k+1 (its detrainment per M_b)
+        R rfv[OUT::kExt ? MAXL : 1];  // rain made per level (evaporation variant)
         R w2 = Q.w2_0;
         const R eps = Q.eps;
         const bool drag = Q.drag;
@@ -1390,6 +1405,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
               emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)),
                    mb, mb * chi1);
               sumr += rf1;
+              if constexpr (OUT::kExt) rfv[k + 1] = rf1;
             }
             hu2 = hu1;
             qtu2 = qtu1;
@@ -1408,6 +1424,7 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
             emit(k + 1, mb * ((hu2 - hu1) + (hk - h_k1)), mb * ((qtu2 - qp1) + (qk - q_k1)),
                  mb, mb * chi1);
             sumr += rf1;
+            if constexpr (OUT::kExt) rfv[k + 1] = rf1;
           }
           chi1 = chik;
           hu2 = hu1;
@@ -1424,6 +1441,33 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
         } else {
           // top layer: detrainment of the plume arriving from kts+1
           emit(kts, mb * (hu2 - h_k1), mb * (qtu2 - q_k1), R(0), mb);
+          if constexpr (OUT::kExt) {
+            // Variant: evaporation of the falling rain (Q.evap_k > 0).  Rain made
+            // in plume layer j (kts < j < ks) falls through the layers below it;
+            // layer j takes the fraction 1 - exp(-k max(qs - q, 0) dz) of the
+            // flux arriving from above, moistening and cooling that layer; what
+            // reaches the surface is the precipitation.
+            if (Q.evap_k > R(0)) {
+              R F = R(0);
+              for (int j = kts + 1; j <= ks; ++j) {
+                const R pm = c.pm(j), qj = c.q(j);
+                R def = sat_qs(c.T(j), pm) - qj;
+                if (def < R(0)) def = R(0);
+                const R E = F * (R(1) - Mth<R>::ex(-Q.evap_k * def * c.dz(j)));
+                F -= E;
+                const R mk = c.m(j);
+                const R ddq = Mth<R>::dv(E, mk);
+                const R ddT = R(-LV / CP) * ddq;
+                const R told = out.dT_at(j);
+                out.add(j, ddT, ddq);
+                sea.add(mk * ddT);
+                swa.add(mk * ddq);
+                sc += mk * (Mth<R>::ab(told + ddT) - Mth<R>::ab(told));
+                if (j < ks) F += mb * rfv[j];
+              }
+              pevap = F;
+            }
+          }
         }
       }
     }
@@ -1439,6 +1483,8 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
   o.flags |= CONV_FLAG_ACTIVE;
   o.mb = (double)mb;
   o.prec = (double)(mb * sumr);
+  if constexpr (OUT::kExt)
+    if (pevap >= R(0)) o.prec = (double)pevap;
   o.ktop = kts;
   if constexpr (TP::kOn) {
     tape->active = true;

@@ -21,7 +21,7 @@ namespace cvg {
 // Trigger pass of one column (all lanes of the warp must call it: the queue
 // append is a warp ballot).  `tag` is what the queue records for the column
 // (the column index, or a batch-wide index), `live` false for padding lanes.
-template <class R, bool FLUX = false>
+template <class R, bool EXT = false>
 __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R>& w, int i,
                                              bool live, int tag) {
   Column<R> c;
@@ -66,11 +66,11 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     store_deep_scalars(a, i, o);  // scalars now; tendencies and the rest in the plume pass
     return;
   }
-  out_col<R, FLUX>(a.od, a, i).zero(0, c.pver);
+  out_col<R, EXT>(a.od, a, i).zero(0, c.pver);
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
   ShalOut s;
-  const auto so = out_col<R, FLUX>(a.os, a, i);
+  const auto so = out_col<R, EXT>(a.os, a, i);
   if (!valid) {
     shallow_column(a.sp, shal_q(a, R(0)), c, s, so);  // flags the column as bad input
   } else {
@@ -89,16 +89,16 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
   store_shallow_scalars(a, i, s);
 }
 
-template <class R, bool FLUX>
+template <class R, bool EXT>
 __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::trigger / kCompactBlock)
     k_trigger(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  trigger_body<R, FLUX>(a, w, i, i < a.n, i);
+  trigger_body<R, EXT>(a, w, i, i < a.n, i);
 }
 
 // Plume pass of the column in queue slot `slot`: column i of member a, queued
 // under `tag` (its index in the workspace's per-column arrays).
-template <class R, bool FLUX = false>
+template <class R, bool EXT = false>
 __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>& w, int slot,
                                            int i, int tag) {
   Column<R> c;
@@ -124,23 +124,23 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   const R lam = a.lam ? (R)a.lam[i] : Q.lambda_default;
   const R tau = a.tau ? (R)a.tau[i] : Q.tau_default;
   prologue(Q.p_top_lim, c);
-  deep_plume(c, a.dp, Q, lam, tau, t, o, out_col<R, FLUX>(a.od, a, i));
+  deep_plume(c, a.dp, Q, lam, tau, t, o, out_col<R, EXT>(a.od, a, i));
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
   c.s = after_deep_src<R>(a, i, false);  // limiter keeps q >= q_min up to rounding
   ShalOut s;
-  shallow_column(a.sp, shal_q(a, R(0)), c, s, out_col<R, FLUX>(a.os, a, i));
+  shallow_column(a.sp, shal_q(a, R(0)), c, s, out_col<R, EXT>(a.os, a, i));
   store_shallow_scalars(a, i, s);
 }
 
-template <class R, bool FLUX>
+template <class R, bool EXT>
 __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactBlock)
     k_plume(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= *w.count) return;
   const int i = w.queue[slot];
-  plume_body<R, FLUX>(a, w, slot, i, i);
+  plume_body<R, EXT>(a, w, slot, i, i);
 }
 
 size_t compact_workspace_bytes(int n, int pver, bool fp64) {
@@ -164,14 +164,14 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
   if (e != cudaSuccess) return e;
   const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
-  if (a.flux)
+  if (a.ext)
     k_trigger<R, true><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
   else
     k_trigger<R, false><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   record_stage(a, 1);
-  if (a.flux)
+  if (a.ext)
     k_plume<R, true><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
   else
     k_plume<R, false><<<grid, kCompactBlock, 0, a.stream>>>(a, w);

@@ -32,7 +32,7 @@ bool shallow_params_ok(const conv_shallow_params* p) {
          std::isfinite(p->a_w) && p->b_w >= 0.0 && std::isfinite(p->b_w) && p->ql_crit >= 0.0 &&
          finite_pos(p->p_lcl_min) && finite_pos(p->p_lfc_min) && finite_pos(p->p_top_lim) &&
          p->n_newton_lcl >= 1 && p->n_newton_lcl <= 32 && p->n_newton_h >= 0 &&
-         p->n_newton_h <= 32;
+         p->n_newton_h <= 32 && std::isfinite(p->evap_k) && p->evap_k >= 0.0;
 }
 
 conv_status fill_grid(const conv_grid* g, RunArgs& a) {
@@ -103,7 +103,7 @@ conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch,
     return CONV_ERR_ARG;
   if (launch && (launch->block_threads < 0 || launch->block_threads > 1024)) return CONV_ERR_ARG;
   const int path = pick_path(launch, a.mode);
-  a.flux = has_flux(a.od) || has_flux(a.os);
+  a.ext = has_flux(a.od) || has_flux(a.os) || ((a.mode & cvg::MODE_SHALLOW) && a.sp.evap_k > 0.0);
   a.block = launch ? launch->block_threads : 0;
   for (int i = 0; i < 3; ++i)
     a.ev[i] = (launch && launch->stage_events)
@@ -172,6 +172,7 @@ void conv_shallow_defaults(conv_shallow_params* p) {
   p->p_top_lim = 4000.0;
   p->n_newton_lcl = 6;
   p->n_newton_h = 4;
+  p->evap_k = 0.0;
 }
 
 const char* conv_status_str(conv_status s) {
@@ -329,6 +330,7 @@ conv_status conv_deep_shallow_adjoint(const conv_grid* grid, const conv_in* in,
   conv_status s = common_in(grid, in, dt, a);
   if (s != CONV_OK) return s;
   if (!deep_params_ok(dpar) || !shallow_params_ok(spar) || !gT || !gq) return CONV_ERR_ARG;
+  if (spar->evap_k > 0.0) return CONV_ERR_UNSUPPORTED;  // no adjoint of the variant
   if (gradient && (!glambda || !gtau)) return CONV_ERR_ARG;
   if (!gradient && !obj) return CONV_ERR_ARG;
   cvg::AdjW w;
@@ -427,7 +429,7 @@ conv_status conv_batch_plan(const conv_member* members, int n_members, conv_prec
     a.sp = mb.shallow;
     a.od = to_outp(&mb.deep_out);
     a.os = to_outp(&mb.shallow_out);
-    if (has_flux(a.od) || has_flux(a.os)) return CONV_ERR_UNSUPPORTED;
+    if (has_flux(a.od) || has_flux(a.os) || mb.shallow.evap_k > 0.0) return CONV_ERR_UNSUPPORTED;
     a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
     a.stream = nullptr;
     cvg::fill_q(a);

@@ -24,7 +24,7 @@ struct OutP {
   double* cape;
   double* mb;
   double* cons_err;
-  void* mu;  // mass-flux profiles (optional; FluxCol instantiations only)
+  void* mu;  // mass-flux profiles (optional; extended instantiations only)
   void* du;
   void* md;
 };
@@ -46,7 +46,7 @@ struct RunArgs {
   ShalQ<float> sqf;
   ShalQ<double> sqd;
   OutP od, os;
-  bool flux;  // some mass-flux profile requested: run the FluxCol instantiations
+  bool ext;  // profile outputs or a scheme variant requested: the extended instantiations
   int mode;
   int block;
   cudaStream_t stream;

@@ -19,7 +19,7 @@ struct PlainThreads<float> {
   static constexpr int sm = 1024;
 };
 
-template <class R, bool FLUX>
+template <class R, bool EXT>
 __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
     k_plain(const __grid_constant__ RunArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
     const DeepQ<R>& Q = deep_q(a, R(0));
     const R lam = a.lam ? (R)a.lam[i] : Q.lambda_default;
     const R tau = a.tau ? (R)a.tau[i] : Q.tau_default;
-    deep_column(a.dp, Q, lam, tau, c, o, out_col<R, FLUX>(a.od, a, i), &bound, &bound_ok);
+    deep_column(a.dp, Q, lam, tau, c, o, out_col<R, EXT>(a.od, a, i), &bound, &bound_ok);
     store_deep_scalars(a, i, o);
     // the limiter keeps q >= q_min up to rounding; a rejected column passes
     // unchanged.  A column that did not trigger has zero tendencies: the shallow
@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
   }
   if (a.mode & MODE_SHALLOW) {
     ShalOut o;
-    shallow_column(a.sp, shal_q(a, R(0)), c, o, out_col<R, FLUX>(a.os, a, i),
+    shallow_column(a.sp, shal_q(a, R(0)), c, o, out_col<R, EXT>(a.os, a, i),
                    (const ShallowSeed<R>*)nullptr, false,
                    bound_ok ? &bound : nullptr);
     store_shallow_scalars(a, i, o);
@@ -56,12 +56,12 @@ cudaError_t launch_plain(const RunArgs& a, bool fp64) {
   const int grid = (a.n + block - 1) / block;
   record_stage(a, 0);
   if (fp64) {
-    if (a.flux)
+    if (a.ext)
       k_plain<double, true><<<grid, block, 0, a.stream>>>(a);
     else
       k_plain<double, false><<<grid, block, 0, a.stream>>>(a);
   } else {
-    if (a.flux)
+    if (a.ext)
       k_plain<float, true><<<grid, block, 0, a.stream>>>(a);
     else
       k_plain<float, false><<<grid, block, 0, a.stream>>>(a);

@@ -235,3 +235,30 @@ def test_batch_rejects_mass_flux_outputs():
     h = C.c_void_p()
     st = L.lib().conv_batch_plan(C.byref(mb), 1, L.CONV_FP64, C.byref(h))
     assert st == L.CONV_ERR_UNSUPPORTED
+
+
+def test_evaporation_variant_arguments():
+    """A negative or non-finite evaporation coefficient is rejected; the variant
+    is refused by the batched runs and by the fused-step adjoint (no adjoint of
+    it), all before any device work."""
+    g, inp, out, keep = _args()
+    lib = L.lib()
+    dp, sp = L.deep_defaults(), L.shallow_defaults()
+    assert sp.evap_k == 0.0
+    for bad in (-1.0, float("nan"), float("inf")):
+        sp.evap_k = bad
+        st = lib.conv_deep_shallow_run(C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp),
+                                       1800.0, L.CONV_FP64, C.byref(out), C.byref(out), None,
+                                       None, 0, None)
+        assert st == L.CONV_ERR_ARG
+    sp.evap_k = 0.05
+    mb = L.Member()
+    mb.grid, mb.in_, mb.deep_out, mb.shallow_out = g, inp, out, out
+    mb.deep, mb.shallow, mb.dt = dp, sp, 1800.0
+    h = C.c_void_p()
+    assert lib.conv_batch_plan(C.byref(mb), 1, L.CONV_FP64, C.byref(h)) == L.CONV_ERR_UNSUPPORTED
+    fake = C.c_void_p(0x1000)
+    st = lib.conv_deep_shallow_adjoint(C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp),
+                                       1800.0, L.CONV_FP64, None, None, None, None, None, fake,
+                                       fake, fake, fake, None, 1, None)
+    assert st == L.CONV_ERR_UNSUPPORTED
