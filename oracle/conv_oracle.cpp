@@ -181,6 +181,8 @@ struct DeepP {
   double capelmt, lambda_default, tau_default, c0, alpha_dd, p_launch_min, p_top_lim, q_min,
       ent_zscale;
   int n_lcl, n_h;
+  int n_plumes;
+  double plume_spread;
 };
 struct ShalP {
   double eps_s, tke, c_m, cin_scale, cin_max, a_w, b_w, ql_crit, p_lcl_min, p_lfc_min, p_top_lim;
@@ -190,7 +192,7 @@ struct ShalP {
 DeepP to_deep(const oracle_deep_params* p) {
   return DeepP{p->capelmt, p->lambda_default, p->tau_default, p->c0, p->alpha_dd,
                p->p_launch_min, p->p_top_lim, p->q_min, p->ent_zscale, p->n_newton_lcl,
-               p->n_newton_h};
+               p->n_newton_h, p->n_plumes < 1 ? 1 : p->n_plumes, p->plume_spread};
 }
 ShalP to_shal(const oracle_shallow_params* p) {
   return ShalP{p->eps_s, p->tke, p->c_m, p->cin_scale, p->cin_max, p->a_w, p->b_w,
@@ -441,41 +443,68 @@ void deep_column(int pver, const double* hyai, const double* hybi, double p0, co
   if (!(val(cape) > P.capelmt)) return;
   s.triggered = true;
 
-  // Entraining updraft (entrainment loop).
-  s.eta[kb] = R(1.0);
-  s.hu[kb] = s.h[kb];
-  s.qtu[kb] = q[kb];
   // Shallowest admissible detrainment level: minimum h* above the LCL (ties:
-  // lowest); the plume is carried through any layer below it.
+  // lowest); a plume is carried through any layer below it.
   int khmin = -1;
   for (int k = klcl - 1; k >= ktl; --k)
     if (khmin < 0 || val(s.hs[k]) < val(s.hs[khmin])) khmin = k;
   s.khmin = khmin;
+  // Entraining updraft (entrainment loop).  Variant (n_plumes > 1): a spectrum
+  // of plumes with entrainment rates lambda * spread^(i/(n-1) - 1/2), each
+  // carrying the share 1/n of the cloud-base mass flux and detraining at its
+  // own top; a plume whose top is at or below the LCL layer drops out.  The
+  // unit tendencies of every plume are summed here; the ensemble's top (the
+  // highest plume top) starts the downdraft.  n_plumes = 1 is the bulk plume.
+  const int NP = P.n_plumes;
   int jt = -1;
   R sumR(0.0);
-  for (int k = kb - 1; k >= ktl; --k) {
-    s.eta[k] = entrain_growth(lambda, P.ent_zscale, s.z_mid[k] - s.z_mid[kb]);
-    const R deta = s.eta[k] - s.eta[k + 1];
-    s.hu[k] = (s.eta[k + 1] * s.hu[k + 1] + deta * s.h[k]) / s.eta[k];
-    if ((k <= khmin && val(s.hu[k]) <= val(s.hs[k])) || k == ktl) {
-      jt = k;
-      break;
+  for (int ip = 0; ip < NP; ++ip) {
+    R lam_i = lambda;
+    double w = 1.0;
+    if (NP > 1) {
+      lam_i = lambda * std::pow(P.plume_spread, (double)ip / (NP - 1) - 0.5);
+      w = 1.0 / NP;
     }
-    const R qt = (s.eta[k + 1] * s.qtu[k + 1] + deta * q[k]) / s.eta[k];
-    double st = 0.0;
-    const R Tsat = moist_invert(s.hu[k], GRAV * s.z_mid[k], s.p_mid[k], T[k], P.n_h, &st);
-    s.newton_max = std::max(s.newton_max, st);
-    const R qsu = sat_qs(Tsat, s.p_mid[k]);
-    R l = qt - qsu;
-    if (val(l) < 0.0) l = R(0.0);
-    const R dz = s.z_int[k] - s.z_int[k + 1];
-    s.rain[k] = s.eta[k] * P.c0 * dz * l / (1.0 + P.c0 * dz);
-    s.qtu[k] = qt - s.rain[k] / s.eta[k];
-    sumR = sumR + s.rain[k];
+    s.eta[kb] = R(1.0);
+    s.hu[kb] = s.h[kb];
+    s.qtu[kb] = q[kb];
+    int jt_i = -1;
+    R sumR_i(0.0);
+    for (int k = kb - 1; k >= ktl; --k) {
+      s.eta[k] = entrain_growth(lam_i, P.ent_zscale, s.z_mid[k] - s.z_mid[kb]);
+      const R deta = s.eta[k] - s.eta[k + 1];
+      s.hu[k] = (s.eta[k + 1] * s.hu[k + 1] + deta * s.h[k]) / s.eta[k];
+      if ((k <= khmin && val(s.hu[k]) <= val(s.hs[k])) || k == ktl) {
+        jt_i = k;
+        break;
+      }
+      const R qt = (s.eta[k + 1] * s.qtu[k + 1] + deta * q[k]) / s.eta[k];
+      double st = 0.0;
+      const R Tsat = moist_invert(s.hu[k], GRAV * s.z_mid[k], s.p_mid[k], T[k], P.n_h, &st);
+      s.newton_max = std::max(s.newton_max, st);
+      const R qsu = sat_qs(Tsat, s.p_mid[k]);
+      R l = qt - qsu;
+      if (val(l) < 0.0) l = R(0.0);
+      const R dz = s.z_int[k] - s.z_int[k + 1];
+      s.rain[k] = s.eta[k] * P.c0 * dz * l / (1.0 + P.c0 * dz);
+      s.qtu[k] = qt - s.rain[k] / s.eta[k];
+      sumR_i = sumR_i + s.rain[k];
+    }
+    if (jt_i < 0 || jt_i >= klcl) continue;  // no cloud above the LCL
+    if (jt < 0 || jt_i < jt) jt = jt_i;
+    sumR = sumR + w * sumR_i;
+    // this plume's environment tendencies per unit M_b (flux form, upwind
+    // subsidence below its top, detrainment at its top)
+    for (int k = jt_i + 1; k <= kb; ++k) {
+      s.dh[k] = s.dh[k] + (w * s.eta[k]) * (s.h[k - 1] - s.h[k]);
+      s.dq[k] = s.dq[k] + (w * s.eta[k]) * (q[k - 1] - q[k]);
+    }
+    s.dh[jt_i] = s.dh[jt_i] + (w * s.eta[jt_i + 1]) * (s.hu[jt_i + 1] - s.h[jt_i]);
+    s.dq[jt_i] = s.dq[jt_i] + (w * s.eta[jt_i + 1]) * (s.qtu[jt_i + 1] - q[jt_i]);
   }
   s.jt = jt;
   s.sumR = sumR;
-  if (jt < 0 || jt >= klcl) return;
+  if (jt < 0) return;
 
   // Downdraft (precipitation loop): starts at the minimum-h* level above the LCL.
   int jd = -1;
@@ -506,13 +535,8 @@ void deep_column(int pver, const double* hyai, const double* hybi, double p0, co
   s.sumE = sumE;
   s.alpha = alpha;
 
-  // Environment tendencies per unit M_b (flux form, upwind subsidence).
-  for (int k = jt + 1; k <= kb; ++k) {
-    s.dh[k] = s.dh[k] + s.eta[k] * (s.h[k - 1] - s.h[k]);
-    s.dq[k] = s.dq[k] + s.eta[k] * (q[k - 1] - q[k]);
-  }
-  s.dh[jt] = s.dh[jt] + s.eta[jt + 1] * (s.hu[jt + 1] - s.h[jt]);
-  s.dq[jt] = s.dq[jt] + s.eta[jt + 1] * (s.qtu[jt + 1] - q[jt]);
+  // Environment tendencies per unit M_b: the plumes' terms are in already; the
+  // downdraft's compensating ascent and its detrainment into the launch layer.
   if (jd >= 0) {
     for (int k = jd; k <= kb - 1; ++k) {
       const R D = alpha * s.etad[k];

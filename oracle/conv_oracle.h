@@ -29,6 +29,8 @@ typedef struct {
   double capelmt, lambda_default, tau_default, c0, alpha_dd;
   double p_launch_min, p_top_lim, q_min, ent_zscale;
   int32_t n_newton_lcl, n_newton_h;
+  int32_t n_plumes, reserved; /* plume spectrum: number of plumes (1 = bulk plume) */
+  double plume_spread;        /* largest / smallest entrainment rate of the spectrum */
 } oracle_deep_params;
 
 typedef struct {

@@ -39,7 +39,8 @@ class DeepParams(C.Structure):
                 ("tau_default", C.c_double), ("c0", C.c_double), ("alpha_dd", C.c_double),
                 ("p_launch_min", C.c_double), ("p_top_lim", C.c_double), ("q_min", C.c_double),
                 ("ent_zscale", C.c_double), ("n_newton_lcl", C.c_int32),
-                ("n_newton_h", C.c_int32)]
+                ("n_newton_h", C.c_int32), ("n_plumes", C.c_int32), ("reserved", C.c_int32),
+                ("plume_spread", C.c_double)]
 
 
 class ShallowParams(C.Structure):
@@ -53,7 +54,7 @@ class ShallowParams(C.Structure):
 def deep_params(**kw) -> DeepParams:
     d = dict(capelmt=70.0, lambda_default=1e-3, tau_default=3600.0, c0=2e-3, alpha_dd=0.2,
              p_launch_min=60000.0, p_top_lim=4000.0, q_min=1e-12, ent_zscale=1000.0,
-             n_newton_lcl=6, n_newton_h=4)
+             n_newton_lcl=6, n_newton_h=4, n_plumes=1, reserved=0, plume_spread=4.0)
     d.update(kw)
     return DeepParams(**d)
 

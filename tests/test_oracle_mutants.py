@@ -16,11 +16,11 @@ SRC = os.path.join(ROOT, "oracle", "conv_oracle.cpp")
 
 MUTANTS = {
     "updraft detrainment uses eta_jt": (
-        "s.dh[jt] = s.dh[jt] + s.eta[jt + 1] * (s.hu[jt + 1] - s.h[jt]);",
-        "s.dh[jt] = s.dh[jt] + s.eta[jt] * (s.hu[jt + 1] - s.h[jt]);"),
+        "s.dh[jt_i] = s.dh[jt_i] + (w * s.eta[jt_i + 1]) * (s.hu[jt_i + 1] - s.h[jt_i]);",
+        "s.dh[jt_i] = s.dh[jt_i] + (w * s.eta[jt_i]) * (s.hu[jt_i + 1] - s.h[jt_i]);"),
     "subsidence upwinds from below": (
-        "s.dh[k] = s.dh[k] + s.eta[k] * (s.h[k - 1] - s.h[k]);",
-        "s.dh[k] = s.dh[k] + s.eta[k] * (s.h[k + 1] - s.h[k]);"),
+        "s.dh[k] = s.dh[k] + (w * s.eta[k]) * (s.h[k - 1] - s.h[k]);",
+        "s.dh[k] = s.dh[k] + (w * s.eta[k]) * (s.h[k + 1] - s.h[k]);"),
     "downdraft detrains level above": (
         "s.dq[kb] = s.dq[kb] + D * (s.qd[kb - 1] - q[kb]);",
         "s.dq[kb] = s.dq[kb] + D * (s.qd[kb - 2] - q[kb]);"),
