@@ -545,8 +545,8 @@ def transport_bench(args, dev, g, ntr=25):
     timed alone with CUDA events, its algorithmic HBM bytes counted from the
     plumes' extents (tendencies written everywhere; tracers read on the levels
     a plume touches; mass-flux profiles, flags and levels once per column), and
-    the fused step with and without the profile outputs and with the shallow
-    rain-evaporation variant."""
+    the fused step with and without the profile outputs and with the scheme
+    variants (shallow rain evaporation, deep plume spectrum)."""
     import torch
 
     from paper_1711_00289_gb300 import _lib as L
@@ -595,6 +595,15 @@ def transport_bench(args, dev, g, ntr=25):
                                          shallow_params=sp, out_deep=od1, out_shallow=os1,
                                          workspace=ws), reps)
     p_off, p_on = float(os0["prec"].sum()), float(os1["prec"].sum())
+    # the deep plume-spectrum variant (extended kernels): 3 plumes, spread 4
+    dpv = L.deep_defaults()
+    dpv.n_plumes, dpv.plume_spread = 3, 4.0
+    od2 = api.new_outputs(pver, n, "mixed", dev)
+    os2 = api.new_outputs(pver, n, "mixed", dev)
+    step_spec = ev_time(api.PreparedStep(T, q, ps, vg, dt=g.dt, precision="mixed", tau=tau,
+                                         deep_params=dpv, out_deep=od2, out_shallow=os2,
+                                         workspace=ws), reps)
+    d_off, d_on = float(od0["prec"].sum()), float(od2["prec"].sum())
     ms = ev_time(lambda: api.tracer_transport(tr, ps, vg, deep_out=od, shallow_out=os_, dt=g.dt,
                                               precision="mixed", tend_deep=td, tend_shallow=ts),
                  reps)
@@ -622,6 +631,8 @@ def transport_bench(args, dev, g, ntr=25):
             "ms_step_with_profiles": step_flux, "ms_step_without_profiles": step_plain,
             "shallow_evaporation": {"evap_k": 0.05, "ms_step": step_evap,
                                     "shallow_rain_evaporated": 1.0 - p_on / max(p_off, 1e-300)},
+            "deep_plume_spectrum": {"n_plumes": 3, "plume_spread": 4.0, "ms_step": step_spec,
+                                    "deep_precip_ratio": d_on / max(d_off, 1e-300)},
             "gpu_launches_per_call": 1,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "algorithmic_bytes": alg,

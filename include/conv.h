@@ -89,6 +89,7 @@ enum {
 };
 
 #define CONV_MAX_LEVELS 32
+#define CONV_MAX_PLUMES 8
 
 /* Vertical grid.  Interface pressure p_i = hyai[i]*p0 + hybi[i]*ps for
  * i = 0 (model top) .. pver (surface); mid-layer p_k = (p_k + p_k+1)/2.
@@ -116,6 +117,18 @@ typedef struct {
   double ent_zscale;     /* entrainment decays as zscale/(dz + zscale), m [1000]   */
   int32_t n_newton_lcl;  /* LCL Newton steps [6]                                   */
   int32_t n_newton_h;    /* moist-inversion Newton steps after the first [4]       */
+  int32_t n_plumes;      /* plume-spectrum variant, 1..CONV_MAX_PLUMES [1 = bulk
+                            plume]: n plumes with entrainment rates lambda *
+                            spread^(i/(n-1) - 1/2), each carrying 1/n of the
+                            cloud-base mass flux and detraining at its own top
+                            (a plume whose top is at or below the LCL layer drops
+                            out); the highest top starts the downdraft and is
+                            reported as ktop.  > 1 runs the extended kernel
+                            instantiations; refused by conv_batch_*, the
+                            adjoints and mass-flux profile outputs
+                            (CONV_ERR_UNSUPPORTED). */
+  int32_t reserved;      /* 0 */
+  double plume_spread;   /* largest / smallest entrainment rate of the spectrum, >= 1 [4] */
 } conv_deep_params;
 
 /* Shallow scheme parameters. */

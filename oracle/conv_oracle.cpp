@@ -1114,6 +1114,7 @@ int oracle_deep_shallow_tracers(int n_cols, int pver, int ld, const double* hyai
   if (!grid_ok(n_cols, pver, ld) || !dpar || !spar || ntr < 0 || (ntr > 0 && !tracers) ||
       (ntr > 0 && (!tend_deep || !tend_shallow)))
     return 1;
+  if (dpar->n_plumes > 1) return 1;  // the transport reading covers the bulk plume
   const DeepP DP = to_deep(dpar);
   const ShalP SP = to_shal(spar);
   const size_t tstride = (size_t)pver * ld;

@@ -38,7 +38,8 @@ class DeepParams(C.Structure):
                 ("tau_default", C.c_double), ("c0", C.c_double), ("alpha_dd", C.c_double),
                 ("p_launch_min", C.c_double), ("p_top_lim", C.c_double), ("q_min", C.c_double),
                 ("ent_zscale", C.c_double), ("n_newton_lcl", C.c_int32),
-                ("n_newton_h", C.c_int32)]
+                ("n_newton_h", C.c_int32), ("n_plumes", C.c_int32), ("reserved", C.c_int32),
+                ("plume_spread", C.c_double)]
 
 
 class ShallowParams(C.Structure):

@@ -369,6 +369,8 @@ struct Acc<float> {
 template <class R>
 struct DeepQ {
   R p_launch_min, p_top_lim, ent_zscale, c0, alpha_dd, q_min, dt, lambda_default, tau_default;
+  int n_plumes;                // plume-spectrum variant (1: bulk plume)
+  R plume_f[CONV_MAX_PLUMES];  // entrainment-rate factor of each plume
 };
 template <class R>
 struct ShalQ {
@@ -380,8 +382,14 @@ struct ShalQ {
 };
 template <class R>
 inline DeepQ<R> make_deep_q(const conv_deep_params& P, double dt) {
-  return DeepQ<R>{(R)P.p_launch_min, (R)P.p_top_lim, (R)P.ent_zscale, (R)P.c0, (R)P.alpha_dd,
-                  (R)P.q_min, (R)dt, (R)P.lambda_default, (R)P.tau_default};
+  DeepQ<R> q{(R)P.p_launch_min, (R)P.p_top_lim, (R)P.ent_zscale, (R)P.c0, (R)P.alpha_dd,
+             (R)P.q_min, (R)dt, (R)P.lambda_default, (R)P.tau_default, 1, {}};
+  q.n_plumes = P.n_plumes > 1 ? P.n_plumes : 1;
+  for (int i = 0; i < CONV_MAX_PLUMES; ++i)
+    q.plume_f[i] = i < q.n_plumes && q.n_plumes > 1
+                       ? (R)std::pow(P.plume_spread, (double)i / (q.n_plumes - 1) - 0.5)
+                       : R(1);
+  return q;
 }
 template <class R>
 inline ShalQ<R> make_shal_q(const conv_shallow_params& P) {
@@ -909,7 +917,55 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   R sumR = R(0);
   MoistSeq<R> seq;
   seq.have = false;
-  for (int k = kb - 1; k >= ktl; --k) {
+  // Variant (extended instantiation, n_plumes > 1): a spectrum of plumes with
+  // entrainment rates lam * plume_f[i], each carrying 1/n of the cloud-base
+  // mass flux and detraining at its own top; a plume whose top is at or below
+  // the LCL layer drops out.  Per level: eS = the members' summed eta below
+  // their tops, dtr = their detrainment terms at their tops; jt = highest top.
+  bool ens = false;
+  R eS[OUT::kExt ? MAXL : 1], dtr_h[OUT::kExt ? MAXL : 1], dtr_q[OUT::kExt ? MAXL : 1];
+  if constexpr (OUT::kExt) {
+    if (Q.n_plumes > 1) {
+      ens = true;
+      for (int k = 0; k < pver; ++k) eS[k] = dtr_h[k] = dtr_q[k] = R(0);
+      const R w = Mth<R>::dv(R(1), (R)Q.n_plumes);
+      for (int ip = 0; ip < Q.n_plumes; ++ip) {
+        const R lam_i = lam * Q.plume_f[ip];
+        R h1 = c.h(kb), q1 = c.q(kb), sr = R(0);
+        int jt_i = -1;
+        seq.have = false;
+        for (int k = kb - 1; k >= ktl; --k) {
+          const R e = entrain_growth(lam_i, ze, c.zm[k] - zb);
+          eta[k] = e;
+          const R de = e - eta[k + 1];
+          const R re = Mth<R>::dv(R(1), e);
+          const R hu = (eta[k + 1] * h1 + de * c.h(k)) * re;
+          if ((k <= khmin && hu <= c.hs(k)) || k == ktl) {
+            jt_i = k;
+            break;
+          }
+          const R pm = c.pm(k);
+          const R qt = (eta[k + 1] * q1 + de * c.q(k)) * re;
+          const R Ts = moist_invert(hu, R(GRAV) * c.zm[k], pm, c.T(k), P.n_newton_h, seq,
+                                    t.newton, c.Tref, c.qref);
+          R l = qt - sat_qs(Ts, pm);
+          if (l < R(0)) l = R(0);
+          const R dz = c.dz(k);
+          const R rain = Mth<R>::dv(e * c0 * dz * l, R(1) + c0 * dz);
+          sr += rain;
+          h1 = hu;
+          q1 = qt - rain * re;
+        }
+        if (jt_i < 0 || jt_i >= klcl) continue;  // no cloud above the LCL
+        if (jt < 0 || jt_i < jt) jt = jt_i;
+        sumR += w * sr;
+        for (int k = jt_i + 1; k <= kb; ++k) eS[k] += w * eta[k];
+        dtr_h[jt_i] += w * eta[jt_i + 1] * (h1 - c.h(jt_i));
+        dtr_q[jt_i] += w * eta[jt_i + 1] * (q1 - c.q(jt_i));
+      }
+    }
+  }
+  for (int k = kb - 1; !ens && k >= ktl; --k) {
     const R e = entrain_growth(lam, ze, c.zm[k] - zb);
     eta[k] = e;
     const R de = e - eta[k + 1];
@@ -1004,7 +1060,20 @@ __device__ __forceinline__ void deep_plume(const Column<R>& c, const conv_deep_p
   for (int k = kb; k >= jt; --k) {
     const R hk = c.h(k), qk = c.q(k);
     R dh, dqk;
-    if (k == jt) {
+    bool done = false;
+    if constexpr (OUT::kExt) {
+      if (ens) {  // the spectrum's summed subsidence and detrainment terms
+        dh = dtr_h[k];
+        dqk = dtr_q[k];
+        if (k > jt) {
+          dh += eS[k] * (c.h(k - 1) - hk);
+          dqk += eS[k] * (c.q(k - 1) - qk);
+        }
+        done = true;
+      }
+    }
+    if (done) {
+    } else if (k == jt) {
       dh = eta[jt + 1] * (hu1 - hk);
       dqk = eta[jt + 1] * (qtu1 - qk);
     } else {

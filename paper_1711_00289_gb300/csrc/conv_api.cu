@@ -23,7 +23,9 @@ bool deep_params_ok(const conv_deep_params* p) {
          std::isfinite(p->c0) && p->alpha_dd >= 0.0 && p->alpha_dd <= 1.0 &&
          finite_pos(p->p_launch_min) && finite_pos(p->p_top_lim) && p->q_min >= 0.0 &&
          p->q_min < 1e-3 && finite_pos(p->ent_zscale) && p->n_newton_lcl >= 1 &&
-         p->n_newton_lcl <= 32 && p->n_newton_h >= 0 && p->n_newton_h <= 32;
+         p->n_newton_lcl <= 32 && p->n_newton_h >= 0 && p->n_newton_h <= 32 &&
+         p->n_plumes >= 1 && p->n_plumes <= CONV_MAX_PLUMES && std::isfinite(p->plume_spread) &&
+         p->plume_spread >= 1.0;
 }
 
 bool shallow_params_ok(const conv_shallow_params* p) {
@@ -103,7 +105,10 @@ conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch,
     return CONV_ERR_ARG;
   if (launch && (launch->block_threads < 0 || launch->block_threads > 1024)) return CONV_ERR_ARG;
   const int path = pick_path(launch, a.mode);
-  a.ext = has_flux(a.od) || has_flux(a.os) || ((a.mode & cvg::MODE_SHALLOW) && a.sp.evap_k > 0.0);
+  const bool spectrum = (a.mode & cvg::MODE_DEEP) && a.dp.n_plumes > 1;
+  if (spectrum && (has_flux(a.od) || has_flux(a.os))) return CONV_ERR_UNSUPPORTED;
+  a.ext = has_flux(a.od) || has_flux(a.os) || ((a.mode & cvg::MODE_SHALLOW) && a.sp.evap_k > 0.0) ||
+          spectrum;
   a.block = launch ? launch->block_threads : 0;
   for (int i = 0; i < 3; ++i)
     a.ev[i] = (launch && launch->stage_events)
@@ -155,6 +160,9 @@ void conv_deep_defaults(conv_deep_params* p) {
   p->ent_zscale = 1000.0;
   p->n_newton_lcl = 6;
   p->n_newton_h = 4;
+  p->n_plumes = 1;
+  p->reserved = 0;
+  p->plume_spread = 4.0;
 }
 
 void conv_shallow_defaults(conv_shallow_params* p) {
@@ -299,6 +307,7 @@ conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
   conv_status s = common_in(grid, in, dt, a);
   if (s != CONV_OK) return s;
   if (!deep_params_ok(par)) return CONV_ERR_ARG;
+  if (par->n_plumes > 1) return CONV_ERR_UNSUPPORTED;  // no adjoint of the variant
   const int n_grad = (gT != nullptr) + (gq != nullptr) + (glambda != nullptr) + (gtau != nullptr);
   if (n_grad != 0 && n_grad != 4) return CONV_ERR_ARG;
   if (n_grad == 0 && !P_out && !H_out) return CONV_ERR_ARG;
@@ -330,7 +339,7 @@ conv_status conv_deep_shallow_adjoint(const conv_grid* grid, const conv_in* in,
   conv_status s = common_in(grid, in, dt, a);
   if (s != CONV_OK) return s;
   if (!deep_params_ok(dpar) || !shallow_params_ok(spar) || !gT || !gq) return CONV_ERR_ARG;
-  if (spar->evap_k > 0.0) return CONV_ERR_UNSUPPORTED;  // no adjoint of the variant
+  if (spar->evap_k > 0.0 || dpar->n_plumes > 1) return CONV_ERR_UNSUPPORTED;  // no adjoint
   if (gradient && (!glambda || !gtau)) return CONV_ERR_ARG;
   if (!gradient && !obj) return CONV_ERR_ARG;
   cvg::AdjW w;
@@ -429,7 +438,8 @@ conv_status conv_batch_plan(const conv_member* members, int n_members, conv_prec
     a.sp = mb.shallow;
     a.od = to_outp(&mb.deep_out);
     a.os = to_outp(&mb.shallow_out);
-    if (has_flux(a.od) || has_flux(a.os) || mb.shallow.evap_k > 0.0) return CONV_ERR_UNSUPPORTED;
+    if (has_flux(a.od) || has_flux(a.os) || mb.shallow.evap_k > 0.0 || mb.deep.n_plumes > 1)
+      return CONV_ERR_UNSUPPORTED;
     a.mode = cvg::MODE_DEEP | cvg::MODE_SHALLOW;
     a.stream = nullptr;
     cvg::fill_q(a);

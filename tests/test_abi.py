@@ -262,3 +262,38 @@ def test_evaporation_variant_arguments():
                                        1800.0, L.CONV_FP64, None, None, None, None, None, fake,
                                        fake, fake, fake, None, 1, None)
     assert st == L.CONV_ERR_UNSUPPORTED
+
+
+def test_plume_spectrum_arguments():
+    """n_plumes outside 1..CONV_MAX_PLUMES or a spread below 1 is rejected; the
+    variant is refused with mass-flux profile outputs, by batched runs and by
+    both adjoints, all before any device work."""
+    g, inp, out, keep = _args()
+    lib = L.lib()
+    dp, sp = L.deep_defaults(), L.shallow_defaults()
+    assert dp.n_plumes == 1 and dp.plume_spread == 4.0
+
+    def run(d, o=out):
+        return lib.conv_deep_shallow_run(C.byref(g), C.byref(inp), C.byref(d), C.byref(sp),
+                                         1800.0, L.CONV_FP64, C.byref(o), C.byref(o), None,
+                                         None, 0, None)
+
+    for n, spread in ((0, 4.0), (9, 4.0), (3, 0.5), (3, float("nan"))):
+        dp.n_plumes, dp.plume_spread = n, spread
+        assert run(dp) == L.CONV_ERR_ARG
+    dp.n_plumes, dp.plume_spread = 3, 4.0
+    fake = C.c_void_p(0x1000)
+    flux = L.Out(fake, fake, fake, fake, None, None, None, None, None, None, None, fake)
+    assert run(dp, flux) == L.CONV_ERR_UNSUPPORTED
+    mb = L.Member()
+    mb.grid, mb.in_, mb.deep_out, mb.shallow_out = g, inp, out, out
+    mb.deep, mb.shallow, mb.dt = dp, sp, 1800.0
+    h = C.c_void_p()
+    assert lib.conv_batch_plan(C.byref(mb), 1, L.CONV_FP64, C.byref(h)) == L.CONV_ERR_UNSUPPORTED
+    st = lib.conv_deep_adjoint(C.byref(g), C.byref(inp), C.byref(dp), 1800.0, L.CONV_FP64,
+                               None, None, None, fake, fake, fake, fake, None, None, None)
+    assert st == L.CONV_ERR_UNSUPPORTED
+    st = lib.conv_deep_shallow_adjoint(C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp),
+                                       1800.0, L.CONV_FP64, None, None, None, None, None, fake,
+                                       fake, fake, fake, None, 1, None)
+    assert st == L.CONV_ERR_UNSUPPORTED
