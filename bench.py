@@ -226,6 +226,24 @@ def cpu_model():
 
 
 # ------------------------------------------------------------------ arms
+def max_over_ranks(x, world, dev):
+    """The largest of a value over all ranks (the slowest rank's time): an
+    all-reduce MAX on the process group (NCCL on GPUs, gloo on CPU)."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, n_cols, ms):
+    """Columns per second of the whole job: every rank advances its own copy of
+    the grid (replicas, weak scaling), timed by the slowest rank."""
+    return world * n_cols / (ms * 1e-3)
+
+
 def reference_arm(args, rank):
     from oracle import oracle as O  # noqa: F401  (reference arm = the oracle)
     from paper_1711_00289_gb300 import soundings as S
@@ -325,11 +343,8 @@ def ours_arm(args, rank, world, local_rank):
     time.sleep(0.3)
     ms, kern = timed(prec, path, args.steps, args.warmup, True)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms * 1e-3)
+    ms = max_over_ranks(ms, world, dev)
+    value = whole_job_value(world, n, ms)
     od = setup(prec)[3]
     act = int(((od["flags"] & 2) > 0).sum().item())
 
@@ -337,11 +352,8 @@ def ours_arm(args, rank, world, local_rank):
     base = None
     if not args.no_baseline and not (prec == "fp64" and path == "plain"):
         bms, _ = timed("fp64", "plain", max(2, min(args.steps, 5)), 2, False)
-        if world > 1:
-            t = torch.tensor([bms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            bms = float(t.item())
-        base = {"value": world * n / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms,
+        bms = max_over_ranks(bms, world, dev)
+        base = {"value": whole_job_value(world, n, bms), "unit": UNIT, "ms_per_step": bms,
                 "path": "plain", "precision": "fp64"}
 
     # end to end through the public API from pinned host buffers: the host
@@ -364,16 +376,18 @@ def ours_arm(args, rank, world, local_rank):
         for e in ev:  # materialise the events outside the timed region
             e.record(stream)
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         ev[0].record(stream)
         for s_ in range(k2):
             e2e_step()
             ev[s_ + 1].record(stream)
         torch.cuda.synchronize()
-        ms2 = ev[0].elapsed_time(ev[-1]) / k2
+        ms2 = max_over_ranks(ev[0].elapsed_time(ev[-1]) / k2, world, dev)
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(k2)]
         h2d = sum(x.numel() * x.element_size() for x in (hT, hq, hps))
         d2h = sum(v.numel() * v.element_size() for o in (hd, hs) for v in o.values())
-        e2e = {"value": world * n / (ms2 * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": whole_job_value(world, n, ms2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms2,
                "ms_min": min(per), "ms_max": max(per),
                "path": "conv_pipeline_run (host buffers, chunked copies overlapping compute)"}
