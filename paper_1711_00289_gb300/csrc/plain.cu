@@ -19,6 +19,8 @@ struct PlainThreads<float> {
   static constexpr int sm = 1024;
 };
 
+// EXT: the extended instantiation (mass-flux profile outputs, scheme variants),
+// launched only for runs that ask for them.
 template <class R, bool EXT>
 __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
     k_plain(const __grid_constant__ RunArgs a) {
