@@ -75,7 +75,7 @@ def test_ragged_sizes_and_padding_untouched(oracle, path, n, pad):
 
 
 @pytest.mark.parametrize("path", PATHS)
-@pytest.mark.parametrize("pver", [26, 32])
+@pytest.mark.parametrize("pver", [4, 8, 26, 32])
 def test_other_level_counts(oracle, path, pver):
     g = S.column_set(512, seed=99 + pver, pver=pver)
     g.lam = np.full(g.n_cols, 1.7e-3)
@@ -245,3 +245,18 @@ def test_prepared_step_matches_call(precision):
             for k in x:
                 assert torch.equal(x[k], y[k]), k
     assert evs[0].elapsed_time(evs[2]) > 0.0
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_every_column_convecting(oracle, path):
+    """The degenerate load the compaction exists for, inverted: every column
+    triggers (the queue holds the whole grid)."""
+    g = S.clustered_grid(1.0, 48, 72)
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    assert ((rd["flags"] & 1) > 0).mean() > 0.99
+    gd, gs = run_gpu(g, "fp64", path)
+    assert_fp64_parity(gd, rd, what="deep")
+    assert_fp64_parity(gs, rs, what="shallow")
+    md, ms_ = run_gpu(g, "mixed", path)
+    r = mixed_report(md, rd, layer_mass(g), None, rd["prec"] + rs["prec"])
+    assert r["decision_mismatch"] <= 2e-3 * r["n"] and r["dTdt_colint_max"] <= 1e-4, r
