@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-transport", action="store_true",
                    help="skip the tracer-transport measurement")
+    p.add_argument("--no-driver", action="store_true",
+                   help="skip the multi-step driver measurement")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the deep-adjoint timing")
     p.add_argument("--no-ensemble", action="store_true",
@@ -427,6 +429,7 @@ def ours_arm(args, rank, world, local_rank):
     ens = None if args.no_ensemble else ensemble_bench(args, dev)
     adj = None if args.no_adjoint else adjoint_bench(args, dev, g)
     trn = None if args.no_transport else transport_bench(args, dev, g)
+    drv = None if args.no_driver else driver_bench(args, dev, g)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         rate, ncols, threads, el = cpu_oracle_rate(g, args.cpu_seconds)
@@ -446,7 +449,7 @@ def ours_arm(args, rank, world, local_rank):
             "baseline_fp64_plain": base,
             "speedup_vs_fp64_plain": (value / base["value"]) if base else None,
             "roofline": roof, "kernels": kernels, "batched_ensemble": ens, "deep_adjoint": adj,
-            "tracer_transport": trn,
+            "tracer_transport": trn, "column_driver": drv,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": (1 if path == "plain" else 2) * args.steps,
             "op_rates_per_s": r}
@@ -653,6 +656,37 @@ def transport_bench(args, dev, g, ntr=25):
                          "traffic": ncu_traffic(g.name + "-tracers25", "transport").get(
                              "k_transport"),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+
+
+def driver_bench(args, dev, g):
+    """The multi-step column driver (api.ColumnModel: fused step + state advance
+    with relaxation) on the benchmark grid, mixed precision: per-step time of
+    eager steps (Python marshalling every step) and of CUDA-graph replays."""
+    import torch
+
+    from paper_1711_00289_gb300 import api
+
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    T = torch.tensor(g.T, device=dev).float()
+    q = torch.tensor(g.q, device=dev).float()
+    ps = torch.tensor(g.ps, device=dev)
+    tau = None if g.tau is None else torch.tensor(g.tau, device=dev)
+    m = api.ColumnModel(T, q, ps, vg, precision="mixed", dt=g.dt, tau=tau)
+    k = max(3, args.steps)
+    res = {}
+    for mode in ("eager", "graph"):
+        run = (lambda n: m.step(n)) if mode == "eager" else (lambda n: m.run_graph(n))
+        run(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(k)
+        e1.record()
+        torch.cuda.synchronize()
+        res[f"ms_per_step_{mode}"] = e0.elapsed_time(e1) / k
+    res.update({"columns": g.n_cols, "precision": "mixed", "steps_timed": k,
+                "gpu_launches_per_step": 4})
+    return res
 
 
 def l2_note(prec, n, pver):

@@ -618,17 +618,41 @@ class ColumnModel:
         self.out_shallow = new_outputs(pver, ld, precision, T.device)
         self.ws = Workspace(T.device)
         self.steps = 0
+        self._graph = None
+
+    def _one_step(self, stream=None):
+        deep_shallow(self.T, self.q, self.ps, self.vgrid, dt=self.dt, precision=self.precision,
+                     lam=self.lam, tau=self.tau, deep_params=self.deep_params,
+                     shallow_params=self.shallow_params, path=self.path,
+                     out_deep=self.out_deep, out_shallow=self.out_shallow, workspace=self.ws,
+                     stream=stream)
+        advance(self.T, self.q, self.vgrid, self.out_deep, self.out_shallow, dt=self.dt,
+                precision=self.precision, T_relax=self.T_ref, q_relax=self.q_ref,
+                tau_relax=self.tau_relax, stream=stream)
 
     def step(self, n: int = 1, stream=None):
         for _ in range(n):
-            deep_shallow(self.T, self.q, self.ps, self.vgrid, dt=self.dt,
-                         precision=self.precision, lam=self.lam, tau=self.tau,
-                         deep_params=self.deep_params, shallow_params=self.shallow_params,
-                         path=self.path, out_deep=self.out_deep, out_shallow=self.out_shallow,
-                         workspace=self.ws, stream=stream)
-            advance(self.T, self.q, self.vgrid, self.out_deep, self.out_shallow, dt=self.dt,
-                    precision=self.precision, T_relax=self.T_ref, q_relax=self.q_ref,
-                    tau_relax=self.tau_relax, stream=stream)
+            self._one_step(stream)
+            self.steps += 1
+        return self.T, self.q
+
+    def run_graph(self, n: int):
+        """n steps replaying a CUDA graph of one step on the current stream: the
+        kernels of step() in the same order, with no host work per step.  The
+        first call runs one step eagerly (it loads the kernels and sizes the
+        workspace) and captures the graph; later calls only replay it."""
+        if n <= 0:
+            return self.T, self.q
+        if self._graph is None:
+            self.step(1)
+            n -= 1
+            torch.cuda.synchronize(self.T.device)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                self._one_step()
+            self._graph = graph
+        for _ in range(n):
+            self._graph.replay()
             self.steps += 1
         return self.T, self.q
 

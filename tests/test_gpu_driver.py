@@ -84,3 +84,34 @@ def test_error_growth_of_mixed_path_within_induced_perturbation():
     env = np.maximum.accumulate(c32)
     assert np.all(cm <= 2.0 * env), (cm / env).max()
     assert c32.max() < 0.5 and cm.max() < 0.5  # K: no run wanders off
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replay_equals_eager_steps(precision):
+    """ColumnModel.run_graph (one step captured into a CUDA graph, replayed)
+    gives the eager steps' states bit for bit, also with the scheme variants."""
+    import torch
+
+    from paper_1711_00289_gb300 import _lib as L
+
+    g = S.latlon_grid(48, 72)
+    for dp, sp in ((None, None), ("spectrum", "evap")):
+        dpar = spar = None
+        if dp:
+            dpar = L.deep_defaults()
+            dpar.n_plumes = 3
+            spar = L.shallow_defaults()
+            spar.evap_k = 0.05
+        runs = []
+        for mode in ("eager", "graph"):
+            m = _model(g, precision)
+            m.deep_params, m.shallow_params = dpar, spar
+            if mode == "eager":
+                m.step(7)
+            else:
+                m.run_graph(3)
+                m.run_graph(4)
+            torch.cuda.synchronize()
+            assert m.steps == 7
+            runs.append((m.T.clone(), m.q.clone()))
+        assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
