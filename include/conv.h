@@ -73,7 +73,7 @@ typedef enum {
   CONV_ERR_ARG = 1,         /* invalid argument (NULL, size, range)          */
   CONV_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed          */
   CONV_ERR_WORKSPACE = 3,   /* workspace missing, too small or misaligned    */
-  CONV_ERR_UNSUPPORTED = 4, /* valid request this build does not implement   */
+  CONV_ERR_UNSUPPORTED = 4, /* valid request the library does not implement  */
   CONV_ERR_TIMEOUT = 5      /* reserved: a bounded device wait gave up       */
 } conv_status;
 
