@@ -844,9 +844,14 @@ __device__ __forceinline__ void deep_trigger(const Column<R>& c, const conv_deep
   int kel = -1;
   for (int k = klcl; k >= ktl; --k) {
     const R pm = c.pm(k), Tk = c.T(k);
+    // the parcel's qs: the scheme's definition qs(Tp) in FP64 (exact also when
+    // the iteration stops short of convergence, as with few Newton steps); the
+    // mixed path takes it from the last linearisation, qs - dqs * step, which
+    // its converged solves give to rounding (unconverged ones are flagged)
     R qsp;
     const R Tp = moist_invert(hb, R(GRAV) * c.zm[k], pm, Tk, P.n_newton_h, seq, t.newton, c.Tref,
-                              c.qref, &qsp);
+                              c.qref, sizeof(R) == 8 ? nullptr : &qsp);
+    if constexpr (sizeof(R) == 8) qsp = sat_qs(Tp, pm);
     t.Tp[(size_t)k * t.tps] = Tp;
     const R b = virt(Tp, qsp) - virt(Tk, c.q(k));
     run.add(R(RD) * b * c.dl[k]);
