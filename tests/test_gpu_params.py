@@ -55,3 +55,76 @@ def test_fp64_parity_off_default(oracle, grid, path, case):
                      shallow_params=sp)
     assert_fp64_parity(gd, rd, what=f"deep case {case} {path}")
     assert_fp64_parity(gs, rs, what=f"shallow case {case} {path}")
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_mixed_budget_off_default(oracle, grid, case):
+    """The mixed compacted path within its error budget at converged off-default
+    parameter sets (case 2 cuts the Newton counts, where the two precisions'
+    convergence flags are defined differently)."""
+    from paper_1711_00289_gb300 import _lib as L
+    from tests.gpu_util import layer_mass, mixed_report, same_decisions
+
+    dp, sp = L.deep_defaults(), L.shallow_defaults()
+    for k, v in DEEP[case].items():
+        setattr(dp, k, v)
+    for k, v in SHALLOW[case].items():
+        setattr(sp, k, v)
+    g = grid
+    rd, rs = oracle.deep_shallow(g, dpar=oracle.deep_params(**DEEP[case]),
+                                 spar=oracle.shallow_params(**SHALLOW[case]), threads=THREADS)
+    gd, gs = run_gpu(g, "mixed", "compact", deep_params=dp, shallow_params=sp)
+    m = layer_mass(g)
+    deep_same = same_decisions(gd, rd)
+    psurf = rd["prec"] + rs["prec"]
+    for tag, got, ref, up in (("deep", gd, rd, None), ("shallow", gs, rs, deep_same)):
+        r = mixed_report(got, ref, m, up, psurf)
+        assert r["decision_mismatch"] <= 2e-3 * r["n"], f"{tag} {r}"
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
+
+
+@pytest.mark.parametrize("case", [0, 1])
+def test_adjoints_off_default(oracle, grid, case):
+    """Both FP64 adjoints against the oracle's forward-mode tangent at converged
+    off-default parameter sets (gradients within 1e-10 of each column's largest)."""
+    import numpy as np
+    import torch
+
+    from paper_1711_00289_gb300 import _lib as L
+    from paper_1711_00289_gb300 import api
+    from tests.gpu_util import to_device
+
+    dp, sp = L.deep_defaults(), L.shallow_defaults()
+    for k, v in DEEP[case].items():
+        setattr(dp, k, v)
+    for k, v in SHALLOW[case].items():
+        setattr(sp, k, v)
+    g = grid
+    n = g.n_cols
+    c = np.arange(n)
+    seeds = [2.0 * S.uniform(31 + case, 0, c, j) - 1.0 for j in range(4)]
+    T, q, ps, lam, tau = to_device(g, "fp64")
+    vg = api.VerticalGrid(g.hyai, g.hybi)
+    dev = [torch.tensor(x, device="cuda") for x in seeds]
+    od = oracle.deep_params(**DEEP[case])
+    osp = oracle.shallow_params(**SHALLOW[case])
+
+    def close(got, ref, what):
+        for x, y, k in zip(got, ref, ("gT", "gq", "glambda", "gtau")):
+            x, y = np.atleast_2d(x), np.atleast_2d(y)
+            den = np.maximum(np.abs(y).max(axis=0), 1e-300)
+            err = (np.abs(x - y).max(axis=0) / den)[np.abs(y).max(axis=0) > 0]
+            assert err.size == 0 or err.max() <= 1e-10, f"{what} {k}: {err.max():.3g}"
+
+    r = api.deep_adjoint(T, q, ps, vg, gP=dev[0], gH=dev[1], dt=g.dt, lam=lam, tau=tau,
+                         params=dp)
+    torch.cuda.synchronize()
+    got = [r[k].cpu().numpy() for k in ("gT", "gq", "glambda", "gtau")]
+    close(got, oracle.deep_adjoint(g, seeds[0], seeds[1], par=od, threads=THREADS), "deep")
+    r = api.deep_shallow_adjoint(T, q, ps, vg, gPd=dev[0], gHd=dev[1], gPs=dev[2], gHs=dev[3],
+                                 dt=g.dt, lam=lam, tau=tau, deep_params=dp, shallow_params=sp)
+    torch.cuda.synchronize()
+    got = [r[k].cpu().numpy() for k in ("gT", "gq", "glambda", "gtau")]
+    ref = oracle.deep_shallow_adjoint(g, *seeds, dpar=od, spar=osp, threads=THREADS)
+    close(got, ref, "step")
