@@ -1,0 +1,71 @@
+"""Parity on physically extreme columns, where the rarely taken branches run:
+very dry air (no LCL in reach), saturated and supersaturated low levels (the
+LCL at the launch point, the q_s clamp), columns 30 K colder than the grid
+(Newton solves that stop short of convergence), mountain surface pressures of
+500-900 hPa, and hot, moist columns.  FP64 against the oracle on both paths
+(decisions bit-exact, values within 1e-10); the mixed path within its budget,
+its convergence flag left out of the decision comparison (the two precisions
+define it differently)."""
+import numpy as np
+import pytest
+
+from paper_1711_00289_gb300 import soundings as S
+from tests.gpu_util import THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def extremes(oracle):
+    g = S.latlon_grid(48, 72)
+    n = g.n_cols
+    c = np.arange(n)
+    u = S.uniform(777, 0, c, 0)
+    T, q, ps = g.T.copy(), g.q.copy(), g.ps.copy()
+    kind = c % 5
+    q[:, kind == 0] *= 0.05                                   # dry
+    p_int = g.hyai[:, None] * 1e5 + g.hybi[:, None] * ps[None, :]
+    pm = 0.5 * (p_int[1:] + p_int[:-1])
+    qs = np.vectorize(oracle.qs)(T, pm)
+    sel = kind == 1                                           # (super)saturated low levels
+    q[-4:, sel] = qs[-4:, sel] * (1.0 + 0.05 * u[sel])
+    T[:, kind == 2] -= 30.0                                   # cold
+    ps[kind == 3] = 5e4 + 4e4 * u[kind == 3]                  # mountains
+    T[:, kind == 4] += 8.0                                    # hot and moist
+    q[:, kind == 4] *= 1.3
+    return S.Columns("extremes-48x72", g.pver, T, q, ps, g.hyai, g.hybi, None, None, g.dt)
+
+
+@pytest.mark.parametrize("path", ["plain", "compact"])
+def test_fp64(oracle, extremes, path):
+    g = extremes
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    assert ((rd["flags"] & 8) > 0).sum() > 50  # unconverged solves are among them
+    gd, gs = run_gpu(g, "fp64", path, ld=S.pad_ld(g.n_cols) + 32)
+    assert_fp64_parity(gd, rd, what=f"deep {path}")
+    assert_fp64_parity(gs, rs, what=f"shallow {path}")
+
+
+def test_mixed(oracle, extremes):
+    g = extremes
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    gd, gs = run_gpu(g, "mixed", "compact")
+    for o in (rd, rs, gd, gs):
+        o["flags"] = o["flags"] & ~8
+    m = layer_mass(g)
+    from tests.gpu_util import same_decisions
+
+    deep_same = same_decisions(gd, rd)
+    psurf = rd["prec"] + rs["prec"]
+    for tag, got, ref, up in (("deep", gd, rd, None), ("shallow", gs, rs, deep_same)):
+        r = mixed_report(got, ref, m, up, psurf)
+        assert r["decision_mismatch"] <= 3e-3 * r["n"], f"{tag} {r}"
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
