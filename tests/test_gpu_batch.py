@@ -118,3 +118,49 @@ def test_batch_graph_capture_and_autotune():
             for k in h:
                 assert np.array_equal(h[k], w[k]), (g.name, k)
     b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_members_with_their_own_parameters(precision):
+    """Each member's own deep and shallow parameters, time step and relaxation
+    times reach its columns: every member equals its unbatched run."""
+    import torch
+
+    from paper_1711_00289_gb300 import _lib as L
+    from paper_1711_00289_gb300 import api
+
+    ens, mem = _members(precision, n_members=6, seed=7)
+    settings = []
+    for j, (g, m) in enumerate(zip(ens, mem)):
+        dp, sp = L.deep_defaults(), L.shallow_defaults()
+        dp.capelmt = 30.0 + 20.0 * (j % 4)
+        dp.c0 = 1e-3 * (1 + j % 3)
+        dp.alpha_dd = 0.1 + 0.1 * (j % 3)
+        sp.c_m = 0.02 + 0.01 * (j % 3)
+        sp.cin_max = 30.0 + 15.0 * (j % 4)
+        m["deep_params"], m["shallow_params"] = dp, sp
+        m["dt"] = 900.0 * (1 + j % 3)
+        ld = m["T"].shape[1]
+        tau = 1800.0 + 600.0 * (np.arange(ld) % 7) + 100.0 * j
+        m["tau"] = torch.tensor(tau, device="cuda")
+        settings.append((dp, sp))
+    b = api.Batch(mem, precision)
+    outs = b.run()
+    torch.cuda.synchronize()
+    checked = 0
+    for g, m, (od, os_) in zip(ens, mem, outs):
+        n = g.n_cols
+        if n == 0:
+            continue
+        rd, rs = api.deep_shallow(m["T"], m["q"], m["ps"], m["vgrid"], dt=m["dt"],
+                                  precision=precision, lam=m["lam"], tau=m["tau"],
+                                  deep_params=m["deep_params"],
+                                  shallow_params=m["shallow_params"], path="compact", n_cols=n)
+        torch.cuda.synchronize()
+        for got, want in ((od, rd), (os_, rs)):
+            a, w = _host(got, n), _host(want, n)
+            for k in a:
+                assert np.array_equal(a[k], w[k]), (g.name, k)
+        checked += n
+    assert checked > 1000
+    b.close()
