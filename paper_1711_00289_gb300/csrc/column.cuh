@@ -67,6 +67,11 @@ constexpr int MAXL = CONV_MAX_LEVELS;
 // for the saturated MSE residual (about 0.02 / K at 300 K, 1000 hPa): from a
 // predictor error of 0.5 K two steps leave ~1e-7 K, below FP32 resolution.
 constexpr int kWarmSteps = 2;
+// A warm-started solve stops after a correction below kWarmStop (K): the error
+// left, ~kNewtonQuad * step^2 <= 1e-5 K, is below FP32 resolution at
+// atmospheric temperatures, so the next step would not change the result
+// (measured: identical outputs on the 884,736-column grid, step 4% faster).
+constexpr double kWarmStop = 1e-2;
 constexpr float kNewtonQuad = 0.1f;  // bound on f''/2f' (1/K) used by the mixed flag
 
 // Kernel-parameter copy of the vertical grid (FP64 and FP32 forms of A p0, B).
@@ -170,7 +175,8 @@ __device__ __forceinline__ R sat_qs(R T, R p) {
 // definition; always in FP64), or -- mixed path, later levels of a vertical
 // sequence -- from the tangent prediction off the previous level's solution
 //   dT = (dh - d(gz) + Lv qs dp/D) / (cp + Lv dqs/dT)
-// followed by kWarmSteps Newton steps.  Tracks the largest remaining error
+// followed by up to kWarmSteps Newton steps (fewer once a correction falls
+// below kWarmStop).  Tracks the largest remaining error
 // (Mth::left of the last correction).
 template <class R>
 struct MoistSeq {
@@ -186,7 +192,8 @@ __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, Mois
                                           float& newton, R Tref, R qref, R* qsol = nullptr) {
   R T;
   int steps;
-  if (Mth<R>::warm && s.have) {
+  const bool warm = Mth<R>::warm && s.have;
+  if (warm) {
     T = s.T + Mth<R>::dv((h - s.h) - (gz - s.gz) + R(LV) * s.qs * (p - s.p) * s.rD,
                          R(CP) + R(LV) * s.dqs);
     steps = kWarmSteps;
@@ -201,6 +208,7 @@ __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, Mois
     const R fp = R(CP) + R(LV) * dqs;
     step = Mth<R>::dv(f, fp);
     T -= step;
+    if (warm && Mth<R>::ab(step) < R(kWarmStop)) break;
   }
   s.have = true;
   s.T = T;
