@@ -27,7 +27,15 @@
 // trigger, linearity of the closure in 1/tau, and finite differences for the
 // tangent.  Tracer transport (tests/test_oracle_transport.py): uniform tracers
 // unchanged, column tracer mass conserved, upwind monotone transport matrices,
-// the moist static energy transported as each scheme transports it.
+// the moist static energy transported as each scheme transports it, and the
+// mass-flux profiles carrying the same transport when it is written as a budget
+// of inflow and outflow.  Rain evaporation (tests/test_oracle_evaporation.py):
+// closed enthalpy and water, monotone in the coefficient, total loss into
+// unsaturated air and none into saturated air, the first-order loss.  Plume
+// spectrum (tests/test_oracle_spectrum.py): one plume and identical plumes are
+// the bulk plume, superposition without a downdraft, the least entraining
+// member's top.  tests/test_oracle_mutants.py plants plausible mistakes in a
+// copy of this file; each must fail one of these pins.
 
 #include "conv_oracle.h"
 

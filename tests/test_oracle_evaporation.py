@@ -8,9 +8,12 @@ are untouched; evaporation only moves water and heat between the rain and the
 layers (column enthalpy and water still close, per level cp dT = -Lv dq, the
 evaporated total equals the precipitation lost); precipitation falls
 monotonically with k and vanishes as k -> infinity where every layer below the
-rain is unsaturated; and for small k the loss matches the first-order
+rain is unsaturated, and no rain evaporates where every such layer is
+saturated or supersaturated; and for small k the loss matches the first-order
 expansion sum_j G_j (qs_j - q_j) dz_j, G_j the rain made above layer j (so rain
 does not evaporate in the layer that makes it)."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -136,3 +139,33 @@ def test_first_order_loss(oracle, grid):
             want += G * dfc * dz
         got = (s0["prec"][i] - s1["prec"][i]) / k
         assert got == pytest.approx(want, rel=1e-4), i
+
+
+def test_no_evaporation_into_saturated_air(oracle, grid):
+    """Deep scheme off.  In the raining columns, every layer from below the plume
+    top to the surface is moistened to 1% above saturation; where the plume top
+    stays put, the saturation deficit is clamped at zero in every layer the rain
+    falls through, so a large coefficient evaporates nothing: identical
+    tendencies, and the same precipitation up to the order of its sum."""
+    g = grid
+    dpar = oracle.deep_params(capelmt=1e30)
+    _, s0 = _run(oracle, g, 0.0, dpar=dpar)
+    rain = _act(s0, oracle) & (s0["prec"] > 0)
+    g2 = copy.deepcopy(g)
+    for i in np.flatnonzero(rain):
+        _, p_mid = oracle.levels(g.pver, g.hyai, g.hybi, g.ps[i])
+        for j in range(s0["ktop"][i] + 1, g.pver):
+            g2.q[j, i] = max(g.q[j, i], 1.01 * oracle.qs(g.T[j, i], p_mid[j]))
+    _, a = _run(oracle, g2, 0.0, dpar=dpar)
+    _, b = _run(oracle, g2, 1.0, dpar=dpar)
+    checked = 0
+    for i in np.flatnonzero(rain & _act(a, oracle) & (a["prec"] > 0)):
+        kt = a["ktop"][i]
+        _, p_mid = oracle.levels(g.pver, g.hyai, g.hybi, g.ps[i])
+        if any(g2.q[j, i] < oracle.qs(g2.T[j, i], p_mid[j]) for j in range(kt + 1, g.pver)):
+            continue  # the plume top moved up into air left unsaturated
+        assert np.array_equal(a["dqdt"][:, i], b["dqdt"][:, i]), i
+        assert np.array_equal(a["dTdt"][:, i], b["dTdt"][:, i]), i
+        assert b["prec"][i] == pytest.approx(a["prec"][i], rel=1e-14, abs=0.0), i
+        checked += 1
+    assert checked > 50

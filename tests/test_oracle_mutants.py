@@ -69,10 +69,78 @@ MUTANTS = {
 
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"]
 
+# Mistakes in the tracer transport, the mass-flux profiles and the two scheme
+# variants, each with the pin suite that covers that part.
+TRANSPORT = "tests/test_oracle_transport.py"
+EVAPORATION = "tests/test_oracle_evaporation.py"
+SPECTRUM = "tests/test_oracle_spectrum.py"
+EXT_MUTANTS = {
+    "tracer updraft entrains the layer below": (
+        "cu[k] = (s.eta[k + 1] * cu[k + 1] + (s.eta[k] - s.eta[k + 1]) * c[k]) / s.eta[k];",
+        "cu[k] = (s.eta[k + 1] * cu[k + 1] + (s.eta[k] - s.eta[k + 1]) * c[k + 1]) / s.eta[k];",
+        TRANSPORT),
+    "tracer subsidence upwinds from below": (
+        "for (int k = jt + 1; k <= kb; ++k) dc[k] = dc[k] + s.eta[k] * (c[k - 1] - c[k]);",
+        "for (int k = jt + 1; k <= kb; ++k) dc[k] = dc[k] + s.eta[k] * (c[k + 1] - c[k]);",
+        TRANSPORT),
+    "tracer downdraft detrains the level above": (
+        "dc[kb] = dc[kb] + s.alpha * s.etad[kb - 1] * (cd[kb - 1] - c[kb]);",
+        "dc[kb] = dc[kb] + s.alpha * s.etad[kb - 1] * (cd[kb - 2] - c[kb]);",
+        TRANSPORT),
+    "shallow tracer plume mixes in the LCL layer": (
+        "    if (k >= s.klcl) {\n      cu[k] = cu[k + 1];",
+        "    if (k > s.klcl) {\n      cu[k] = cu[k + 1];",
+        TRANSPORT),
+    "downdraft flux profile drops alpha": (
+        "md[k] = s.mb * s.alpha * s.etad[k];", "md[k] = s.mb * s.etad[k];", TRANSPORT),
+    "top detrainment flux from the top layer's eta": (
+        "du[s.jt] = s.mb * s.eta[s.jt + 1];", "du[s.jt] = s.mb * s.eta[s.jt];", TRANSPORT),
+    "shallow detrainment flux in the LCL layer": (
+        "for (int k = s.kts + 1; k <= s.klcl - 1 && k <= ks - 1; ++k) {",
+        "for (int k = s.kts + 1; k <= s.klcl && k <= ks - 1; ++k) {",
+        TRANSPORT),
+    "evaporated fraction without the layer depth": (
+        "const R E = F * (1.0 - exp(-P.evap_k * def * dz));",
+        "const R E = F * (1.0 - exp(-P.evap_k * def));",
+        EVAPORATION),
+    "evaporation warms the layer": (
+        "s.dT[j] = s.dT[j] - LV * E / (CP * s.m[j]);",
+        "s.dT[j] = s.dT[j] + LV * E / (CP * s.m[j]);",
+        EVAPORATION),
+    "rain evaporates in the layer that makes it": (
+        "      const R E = F * (1.0 - exp(-P.evap_k * def * dz));\n"
+        "      F = F - E;\n"
+        "      s.dq[j] = s.dq[j] + E / s.m[j];\n"
+        "      s.dT[j] = s.dT[j] - LV * E / (CP * s.m[j]);\n"
+        "      if (j < ks) F = F + mb * s.rf[j];\n",
+        "      if (j < ks) F = F + mb * s.rf[j];\n"
+        "      const R E = F * (1.0 - exp(-P.evap_k * def * dz));\n"
+        "      F = F - E;\n"
+        "      s.dq[j] = s.dq[j] + E / s.m[j];\n"
+        "      s.dT[j] = s.dT[j] - LV * E / (CP * s.m[j]);\n",
+        EVAPORATION),
+    "saturation deficit not clamped": (
+        "      if (val(def) < 0.0) def = R(0.0);\n      const R E",
+        "      const R E",
+        EVAPORATION),
+    "spectrum rates centred on the wrong member": (
+        "lambda * std::pow(P.plume_spread, (double)ip / (NP - 1) - 0.5);",
+        "lambda * std::pow(P.plume_spread, (double)ip / NP - 0.5);",
+        SPECTRUM),
+    "member share 1/(n-1)": ("w = 1.0 / NP;", "w = 1.0 / (NP - 1);", SPECTRUM),
+    "ensemble top from the most entraining member": (
+        "if (jt < 0 || jt_i < jt) jt = jt_i;", "if (jt < 0 || jt_i > jt) jt = jt_i;", SPECTRUM),
+    "member rain not weighted by its share": (
+        "sumR = sumR + w * sumR_i;", "sumR = sumR + sumR_i;", SPECTRUM),
+}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+CASES = {**{k: (o, n, PIN_FILES) for k, (o, n) in MUTANTS.items()},
+         **{k: (o, n, [f]) for k, (o, n, f) in EXT_MUTANTS.items()}}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
 def test_mutant_is_caught(name, tmp_path):
-    old, new = MUTANTS[name]
+    old, new, files = CASES[name]
     src = open(SRC).read()
     assert src.count(old) == 1, f"mutation anchor not found once: {name}"
     mpath = tmp_path / "conv_oracle.cpp"
@@ -83,6 +151,6 @@ def test_mutant_is_caught(name, tmp_path):
                     str(mpath)], check=True)
     env = dict(os.environ, CONV_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        *PIN_FILES], cwd=ROOT, env=env, capture_output=True, text=True,
+                        *files], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode != 0, f"mutant survived the pins: {name}\n{r.stdout[-2000:]}"

@@ -177,3 +177,81 @@ def test_mass_flux_profiles_close_the_plume_budget(oracle, grid, runs, off):
             want = mb * (-math.expm1(-eps * (z_int[k] - z_int[k + 1]))) if k < klcl else 0.0
             assert du[k] == pytest.approx(want, rel=1e-12, abs=1e-300)
     assert np.all(fd["md"][:, ad].sum(axis=0) >= 0.0)
+
+
+def _budget_tendency(mu, du, md, kb, kt, jd, m, c):
+    """One column's tracer tendency from its mass-flux profiles alone, as the
+    budget of what crosses each environment layer's boundaries:
+
+      subsidence    mu[k] down through the top of layer k, carrying c[k-1];
+      ascent        md[k] up through the bottom of layer k (it replaces the
+                    downdraft air leaving k), carrying c[k+1];
+      updraft       entrains e[k] = mu[k] - mu[k+1] + du[k] of c[k] and detrains
+                    du[k] of the value cu[k+1] arriving from below, its own value
+                    following from its mass budget
+                    mu[k] cu[k] = (mu[k+1] - du[k]) cu[k+1] + e[k] c[k];
+      downdraft     entrains md[k] - md[k-1] of c[k] on jd..kb-1
+                    (md[k] cd[k] = md[k-1] cd[k-1] + (md[k] - md[k-1]) c[k]) and
+                    detrains md[kb-1] of cd[kb-1] into the launch layer kb.
+
+    Written as inflow minus outflow (conservative form), not as the upwind
+    differences the schemes use."""
+    n = len(c)
+    mu_ = np.append(mu, 0.0)  # nothing rises into the lowest layer from below
+    md_up = np.concatenate(([0.0], md))  # md_up[k] = md[k-1]: crosses the top of layer k
+    cu = np.zeros(n + 1)
+    for k in range(kb, kt, -1):
+        e = mu_[k] - mu_[k + 1] + du[k]
+        cu[k] = ((mu_[k + 1] - du[k]) * cu[k + 1] + e * c[k]) / mu_[k]
+    cd = np.zeros(n)
+    if jd >= 0:
+        for k in range(jd, kb):
+            if md[k] > 0.0:
+                cd[k] = (md_up[k] * (cd[k - 1] if k > jd else 0.0) + (md[k] - md_up[k]) * c[k]) / md[k]
+    t = np.zeros(n)
+    for k in range(kt, kb + 1):
+        above = c[k - 1] if k > 0 else 0.0
+        below = c[k + 1] if k + 1 < n else 0.0
+        flow = mu_[k] * above - mu_[k + 1] * c[k]  # subsidence in, out
+        flow += md[k] * below - md_up[k] * c[k]  # compensating ascent in, out
+        e = mu_[k] - mu_[k + 1] + du[k]
+        flow += du[k] * cu[k + 1] - e * c[k]  # updraft detrainment, entrainment
+        if jd >= 0 and jd <= k <= kb - 1:
+            flow -= (md[k] - md_up[k]) * c[k]  # downdraft entrainment
+        if jd >= 0 and k == kb:
+            flow += md[kb - 1] * cd[kb - 1]  # downdraft detrainment into the launch layer
+        t[k] = flow / m[k]
+    return t
+
+
+def test_flux_profiles_reproduce_the_transport(oracle, grid, runs):
+    """The profiles mu, du, md the oracle reports carry exactly the transport its
+    schemes apply: the budget above, fed the profiles, reproduces the deep
+    tendencies and the shallow tendencies of the deep-updated tracer
+    (max(c + dt tend_deep, 0)) on every active column, and the downdraft flux
+    vanishes outside kaux..kb-1."""
+    g = grid
+    od, os_ = runs
+    rng = np.random.default_rng(5)
+    tr = rng.uniform(0.0, 1.0, (2, g.pver, g.n_cols)) * np.array([1.0, 1e-8])[:, None, None]
+    td, ts, fd, fs = oracle.deep_shallow_tracers(g, tr, threads=4)
+    m = _layer_mass(g)
+    checked = 0
+    for t_all, f, o, deep in ((td, fd, od, True), (ts, fs, os_, False)):
+        act = _active(o, oracle)
+        assert act.sum() > 20
+        for i in np.flatnonzero(act):
+            kb, kt = int(o["kb"][i]), int(o["ktop"][i])
+            jd = int(o["kaux"][i]) if deep else -1
+            md = f["md"][:, i]
+            if deep and jd >= 0:
+                assert np.all(md[:jd] == 0.0) and np.all(md[kb:] == 0.0)
+            else:
+                assert np.all(md == 0.0)
+            for n in range(tr.shape[0]):
+                c = tr[n, :, i] if deep else np.maximum(tr[n, :, i] + g.dt * td[n, :, i], 0.0)
+                want = _budget_tendency(f["mu"][:, i], f["du"][:, i], md, kb, kt, jd, m[:, i], c)
+                got = t_all[n, :, i]
+                assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), (deep, i, n)
+            checked += 1
+    assert checked > 100
