@@ -22,10 +22,12 @@
 // Discrete decisions (level scans, branches) always compare the value part.
 //
 // Parity pins (tests/test_oracle_pins.py): closed-form dry adiabat CAPE,
-// Bolton cross-checks, Newton residuals, brute-force level scans on tiny columns,
-// column energy/water conservation, non-negativity, exact zeros outside the
-// trigger, linearity of the closure in 1/tau, and finite differences for the
-// tangent.  Tracer transport (tests/test_oracle_transport.py): uniform tracers
+// Bolton cross-checks, Newton residuals, brute-force level scans on tiny columns
+// (launch level, EL, LFC also over superadiabatic surface layers, cloud and
+// downdraft tops from h* computed by its definition), column energy/water
+// conservation, non-negativity, shallow rain bounded by the plume's condensate,
+// exact zeros outside the trigger, linearity of the closure in 1/tau, and
+// finite differences for the tangent.  Tracer transport (tests/test_oracle_transport.py): uniform tracers
 // unchanged, column tracer mass conserved, upwind monotone transport matrices,
 // the moist static energy transported as each scheme transports it, and the
 // mass-flux profiles carrying the same transport when it is written as a budget

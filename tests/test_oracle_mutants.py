@@ -3,8 +3,10 @@
 Every mutant below is a plausible slip (an index off by one, a dropped factor,
 a flipped sign, a swapped operand) in one step of the column schemes.  The
 mutant is compiled from a patched copy of conv_oracle.cpp in a temporary
-directory and the pin suites are run against it in a subprocess.
+directory and the pin suites are run against it in a subprocess; the mutants
+are built and checked several at a time, each in its own directory.
 """
+import concurrent.futures as cf
 import os
 import subprocess
 import sys
@@ -65,6 +67,42 @@ MUTANTS = {
     "es constants swapped": (
         "return ES0 * exp(ESA * (T - EST0) / (T - EST1));",
         "return ES0 * exp(ESA * (T - EST1) / (T - EST0));"),
+    "moisture limiter keeps the larger flux": (
+        "if (val(ml) < val(mb)) {", "if (val(ml) > val(mb)) {"),
+    "moisture limiter ignores q_min": (
+        "const R ml = (q[k] - P.q_min) / (-dt * s.dq[k]);",
+        "const R ml = q[k] / (-dt * s.dq[k]);"),
+    "precipitation ignores downdraft evaporation": (
+        "R net = sumR - alpha * sumE;", "R net = sumR;"),
+    "closure drops tau": ("R mb = -cape / (tau * F);", "R mb = -cape / F;"),
+    "closure drops the moisture part of dTv": (
+        "const R dTv = (1.0 + ZVIR * q[k]) * s.dT[k] + ZVIR * T[k] * s.dq[k];",
+        "const R dTv = (1.0 + ZVIR * q[k]) * s.dT[k];"),
+    "shallow closure density from the dry temperature": (
+        "const R rho = psrc / (RD * s.Tv[ks]);", "const R rho = psrc / (RD * Ts);"),
+    "shallow w2 starts at tke": (
+        "const double w2_0 = 2.0 / 3.0 * P.tke;", "const double w2_0 = P.tke;"),
+    "shallow rain from total water": ("R r = l - P.ql_crit;", "R r = qt - P.ql_crit;"),
+    "unsaturated plume temperature from qs": (
+        "Tu = (s.hu[k] - gz - LV * qt) / CP;", "Tu = (s.hu[k] - gz - LV * qsu) / CP;"),
+    "shallow top at the layer where w2 runs out": (
+        "if (!(val(s.w2[k]) > 0.0)) { kts = k + 1; break; }",
+        "if (!(val(s.w2[k]) > 0.0)) { kts = k; break; }"),
+    "LFC allowed below the LCL": (
+        "if (k <= klcl && val(s.b[k]) > 0.0) { klfc = k; break; }",
+        "if (val(s.b[k]) > 0.0) { klfc = k; break; }"),
+    "mid-layer pressure at the bottom interface": (
+        "p_mid[k] = 0.5 * (p_int[k] + p_int[k + 1]);", "p_mid[k] = p_int[k + 1];"),
+    "shallow dry parcel pressure ratio inverted": (
+        "Tp = Ts * pow(s.p_mid[k] / psrc, KAPPA);", "Tp = Ts * pow(psrc / s.p_mid[k], KAPPA);"),
+    "Newton step sign": (
+        "    T = T - step;\n    if (last_step)", "    T = T + step;\n    if (last_step)"),
+    "EL scanned upwards from the LCL": (
+        "for (int k = ktl; k <= klcl; ++k)\n    if (val(s.b[k]) > 0.0) { kel = k; break; }",
+        "for (int k = klcl; k >= ktl; --k)\n    if (val(s.b[k]) > 0.0) { kel = k; break; }"),
+    "h* from the environment's own humidity": (
+        "s.hs[k] = sdry + LV * qsk;", "s.hs[k] = sdry + LV * q[k];"),
+    "CIN sign": ("R neg = -s.b[k];", "R neg = s.b[k];"),
 }
 
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"]
@@ -138,19 +176,41 @@ CASES = {**{k: (o, n, PIN_FILES) for k, (o, n) in MUTANTS.items()},
          **{k: (o, n, [f]) for k, (o, n, f) in EXT_MUTANTS.items()}}
 
 
-@pytest.mark.parametrize("name", sorted(CASES))
-def test_mutant_is_caught(name, tmp_path):
+def _check(name, d):
+    """Build mutant `name` in directory d and run its pin suites; returns the
+    pytest exit code and the end of its output."""
     old, new, files = CASES[name]
     src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not found once: {name}"
-    mpath = tmp_path / "conv_oracle.cpp"
-    mpath.write_text(src.replace(old, new))
-    lib = tmp_path / "libmutant.so"
+    if src.count(old) != 1:
+        return None, f"mutation anchor not found once: {name}"
+    mpath = os.path.join(d, "conv_oracle.cpp")
+    with open(mpath, "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(d, "libmutant.so")
     subprocess.run(["g++", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
-                    "-std=c++17", "-I", os.path.join(ROOT, "oracle"), "-o", str(lib),
-                    str(mpath)], check=True)
-    env = dict(os.environ, CONV_ORACLE_LIB=str(lib))
+                    "-std=c++17", "-I", os.path.join(ROOT, "oracle"), "-o", lib, mpath],
+                   check=True)
+    env = dict(os.environ, CONV_ORACLE_LIB=lib)
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         *files], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
-    assert r.returncode != 0, f"mutant survived the pins: {name}\n{r.stdout[-2000:]}"
+                       timeout=900)
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    workers = max(1, min(6, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        futs = {name: ex.submit(_check, name, str(tmp_path_factory.mktemp("mutant")))
+                for name in sorted(CASES)}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mutant_is_caught(name, outcomes):
+    rc, out = outcomes[name]
+    assert rc is not None, out
+    assert rc != 0, f"mutant survived the pins: {name}\n{out}"
+    # a failed pin (1) or a crash (killed by a signal), not a usage error or an
+    # empty collection
+    assert rc == 1 or rc < 0, f"pin run did not execute: {name} (exit {rc})\n{out}"

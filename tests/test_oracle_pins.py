@@ -235,19 +235,28 @@ def test_deep_plume_closed_forms(oracle, cols, active_diags):
             l = max(0.0, qt - oracle.qs(Ts, d.p_mid[k]))
             assert rain[k] / eta[k] == pytest.approx(2e-3 * dz * (l - rain[k] / eta[k]),
                                                      rel=1e-7, abs=1e-14)
-        # cloud top: first layer at/above the min-h* layer with h_u <= h*
-        hs = np.array(d.hs[: cols.pver])
+        # cloud top: first layer at/above the min-h* layer with h_u <= h*, h* the
+        # saturated moist static energy cp T + g z + Lv qs(T, p) of the environment
+        hs = _saturated_mse(oracle, T, z, d.p_mid)
+        np.testing.assert_allclose(np.array(d.hs[: cols.pver]), hs, rtol=1e-14, atol=0)
         khmin = max(range(d.k_top_lim, d.klcl), key=lambda k: (-hs[k], k))
         assert d.khmin == khmin
         cands = [k for k in range(khmin, d.k_top_lim - 1, -1) if d.hu[k] <= hs[k]]
         assert jt == (cands[0] if cands else d.k_top_lim)
 
 
-def test_deep_downdraft_closed_forms(cols, active_diags):
+def _saturated_mse(oracle, T, z, p_mid):
+    return np.array([P.CP * T[k] + P.GRAV * z[k] + P.LV * oracle.qs(T[k], p_mid[k])
+                     for k in range(len(T))])
+
+
+def test_deep_downdraft_closed_forms(oracle, cols, active_diags):
     for i, d in active_diags:
         T, q, ps = _col(cols, i)
         kb, jt, jd = d.kb, d.jt, d.jd
-        hs = np.array(d.hs[: cols.pver])
+        # the downdraft starts at the minimum of the environment's h* between
+        # the cloud top and the LCL (ties: the lower layer)
+        hs = _saturated_mse(oracle, T, np.array(d.z_mid[: cols.pver]), d.p_mid)
         rng = list(range(jt + 1, d.klcl))
         if not rng:
             assert jd == -1
@@ -409,14 +418,19 @@ def test_shallow_exit_paths_and_zero_outputs(oracle):
     assert np.bincount(codes, minlength=5)[3] > 0  # E3 occurs in this set
 
 
-def test_shallow_lfc_cin_brute_force(oracle):
+@pytest.mark.parametrize("warm", [0.0, 3.0])
+def test_shallow_lfc_cin_brute_force(oracle, warm):
+    """warm > 0 heats the source layer by that many kelvin: a superadiabatic
+    surface layer whose dry-lifted parcel is buoyant below its LCL, where the
+    LFC must still not be placed."""
     g = S.column_set(96)
-    n = 0
+    n = dry_buoyant = 0
     for i in range(g.n_cols):
-        d = _sh(oracle, g, i)
+        T, q, ps = _col(g, i)
+        T[-1] += warm
+        d = _sh(oracle, g, i, T=T)
         if d.exit_code == 1:
             continue
-        T, q, ps = _col(g, i)
         p_int, p_mid = P.levels(g.hyai, g.hybi, ps)
         ks = g.pver - 1
         z = np.array(d.z_mid[: g.pver])
@@ -435,6 +449,7 @@ def test_shallow_lfc_cin_brute_force(oracle):
             if k <= d.klcl and b[k] > 0:
                 klfc = k
                 break
+        dry_buoyant += any(b[k] > 0 for k in b if k > d.klcl)
         assert d.klfc == klfc
         if klfc >= 0:
             cin = sum(P.RD * max(0.0, -b[k]) * math.log(p_int[k + 1] / p_int[k])
@@ -442,6 +457,8 @@ def test_shallow_lfc_cin_brute_force(oracle):
             assert d.cin == pytest.approx(cin, rel=1e-9, abs=1e-9)
             n += 1
     assert n > 10
+    if warm > 0:
+        assert dry_buoyant > 10
 
 
 def test_shallow_budget_and_closure(oracle):
@@ -472,6 +489,14 @@ def test_shallow_budget_and_closure(oracle):
         np.testing.assert_allclose(np.array(d.dq[: g.pver]), dq, rtol=0,
                                    atol=1e-10 * np.abs(dq).max())
         assert d.prec == pytest.approx(d.mb * rf.sum(), rel=1e-12, abs=1e-300)
+        # rain comes out of the condensate only: never more than the liquid the
+        # plume carries (total water above saturation at its temperature), so a
+        # saturated plume stays saturated after the rain-out
+        for k in range(kts + 1, ks):
+            qs_u = oracle.qs(d.Tu[k], d.p_mid[k])
+            assert 0.0 <= rf[k] <= max(d.qtpre[k] - qs_u, 0.0) * (1 + 1e-12), k
+            if d.qtpre[k] >= qs_u:
+                assert d.qtu[k] >= qs_u * (1 - 1e-12), k
         # w2 above the LFC stays positive up to the top, fails (or hits the limit) above it
         w2 = np.array(d.w2[: g.pver])
         assert np.all(w2[kts:ks + 1] > 0)
