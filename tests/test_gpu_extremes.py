@@ -2,7 +2,10 @@
 very dry air (no LCL in reach), saturated and supersaturated low levels (the
 LCL at the launch point, the q_s clamp), columns 30 K colder than the grid
 (Newton solves that stop short of convergence), mountain surface pressures of
-500-900 hPa, and hot, moist columns.  FP64 against the oracle on both paths
+500-900 hPa, hot, moist columns, and superadiabatic surface layers (a dry-lifted
+parcel buoyant below its LCL, where the shallow LFC must not be placed).  With
+rain evaporation switched on, the (super)saturated low levels are layers the
+rain falls through without evaporating.  FP64 against the oracle on both paths
 (decisions bit-exact, values within 1e-10); the mixed path within its budget,
 its convergence flag left out of the decision comparison (the two precisions
 define it differently)."""
@@ -29,7 +32,7 @@ def extremes(oracle):
     c = np.arange(n)
     u = S.uniform(777, 0, c, 0)
     T, q, ps = g.T.copy(), g.q.copy(), g.ps.copy()
-    kind = c % 5
+    kind = c % 6
     q[:, kind == 0] *= 0.05                                   # dry
     p_int = g.hyai[:, None] * 1e5 + g.hybi[:, None] * ps[None, :]
     pm = 0.5 * (p_int[1:] + p_int[:-1])
@@ -40,6 +43,8 @@ def extremes(oracle):
     ps[kind == 3] = 5e4 + 4e4 * u[kind == 3]                  # mountains
     T[:, kind == 4] += 8.0                                    # hot and moist
     q[:, kind == 4] *= 1.3
+    sel = kind == 5                                           # superadiabatic surface layer
+    T[-1, sel] += 2.0 + 2.0 * u[sel]
     return S.Columns("extremes-48x72", g.pver, T, q, ps, g.hyai, g.hybi, None, None, g.dt)
 
 
@@ -53,10 +58,38 @@ def test_fp64(oracle, extremes, path):
     assert_fp64_parity(gs, rs, what=f"shallow {path}")
 
 
-def test_mixed(oracle, extremes):
+def test_superadiabatic_columns_reach_the_dry_branch(oracle, extremes):
     g = extremes
-    rd, rs = oracle.deep_shallow(g, threads=THREADS)
-    gd, gs = run_gpu(g, "mixed", "compact")
+    idx = np.flatnonzero(np.arange(g.n_cols) % 6 == 5)[:100]
+    dry = 0
+    for i in idx:
+        d = oracle.shallow_column_diag(g.pver, g.hyai, g.hybi, g.T[:, i], g.q[:, i],
+                                       float(g.ps[i]))
+        dry += d.exit_code != 1 and any(d.b[k] > 0 for k in range(d.klcl + 1, g.pver))
+    assert dry > 50
+
+
+def _spar_evap():
+    from paper_1711_00289_gb300 import _lib as L
+
+    sp = L.shallow_defaults()
+    sp.ql_crit, sp.evap_k = 1e-4, 0.05
+    return sp
+
+
+@pytest.mark.parametrize("path", ["plain", "compact"])
+def test_fp64_with_rain_evaporation(oracle, extremes, path):
+    g = extremes
+    rd, rs = oracle.deep_shallow(g, spar=oracle.shallow_params(ql_crit=1e-4, evap_k=0.05),
+                                 threads=THREADS)
+    sat = (np.arange(g.n_cols) % 6 == 1) & ((rs["flags"] & 2) > 0) & (rs["prec"] > 0)
+    assert sat.sum() > 100  # raining columns whose low levels are (super)saturated
+    gd, gs = run_gpu(g, "fp64", path, ld=S.pad_ld(g.n_cols) + 32, shallow_params=_spar_evap())
+    assert_fp64_parity(gd, rd, what=f"deep {path}")
+    assert_fp64_parity(gs, rs, what=f"shallow {path}")
+
+
+def _mixed_check(g, gd, gs, rd, rs):
     for o in (rd, rs, gd, gs):
         o["flags"] = o["flags"] & ~8
     m = layer_mass(g)
@@ -69,3 +102,18 @@ def test_mixed(oracle, extremes):
         assert r["decision_mismatch"] <= 3e-3 * r["n"], f"{tag} {r}"
         assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
         assert r["prec_max"] <= 1e-3, f"{tag} {r}"
+
+
+def test_mixed(oracle, extremes):
+    g = extremes
+    rd, rs = oracle.deep_shallow(g, threads=THREADS)
+    gd, gs = run_gpu(g, "mixed", "compact")
+    _mixed_check(g, gd, gs, rd, rs)
+
+
+def test_mixed_with_rain_evaporation(oracle, extremes):
+    g = extremes
+    rd, rs = oracle.deep_shallow(g, spar=oracle.shallow_params(ql_crit=1e-4, evap_k=0.05),
+                                 threads=THREADS)
+    gd, gs = run_gpu(g, "mixed", "compact", shallow_params=_spar_evap())
+    _mixed_check(g, gd, gs, rd, rs)
