@@ -6,7 +6,6 @@ import glob
 import os
 import re
 
-import numpy as np
 import pytest
 
 from paper_1711_00289_gb300 import _lib as L
