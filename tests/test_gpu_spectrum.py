@@ -49,6 +49,26 @@ def test_fp64_matches_oracle(oracle, path):
     assert (rd["ktop"][act] < r1["ktop"][act]).mean() > 0.2
 
 
+@pytest.mark.parametrize("n", [2, 8])
+def test_member_count_edges(oracle, n):
+    """Two members (the rate exponent's denominator n - 1 = 1) and the most the
+    interface allows (CONV_MAX_PLUMES = 8): FP64 on the compacted path and the
+    mixed path within its budget."""
+    g = S.latlon_grid(48, 72)
+    rd, rs = _oracle(oracle, g, n)
+    gd, gs = run_gpu(g, "fp64", "compact", ld=S.pad_ld(g.n_cols) + 32, deep_params=_dpar(n))
+    assert_fp64_parity(gd, rd, what=f"deep n={n}")
+    assert_fp64_parity(gs, rs, what=f"shallow n={n}")
+    md, ms = run_gpu(g, "mixed", "compact", deep_params=_dpar(n))
+    m = layer_mass(g)
+    psurf = rd["prec"] + rs["prec"]
+    for tag, got, ref, up in (("deep", md, rd, None), ("shallow", ms, rs, same_decisions(md, rd))):
+        r = mixed_report(got, ref, m, up, psurf)
+        assert r["decision_mismatch"] <= 3e-3 * r["n"], f"{tag} {r}"
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
+
+
 def test_one_plume_is_the_default(oracle):
     g = S.latlon_grid(48, 72)
     a = run_gpu(g, "mixed", "compact")

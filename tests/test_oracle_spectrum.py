@@ -34,7 +34,7 @@ def test_one_plume_is_the_bulk_scheme(oracle, grid):
             assert np.array_equal(x[k], y[k]), k
 
 
-@pytest.mark.parametrize("n", [2, 3, 5])
+@pytest.mark.parametrize("n", [2, 3, 5, 8])
 def test_identical_members_reproduce_the_bulk_plume(oracle, grid, n):
     a, _ = oracle.deep_shallow(grid, threads=4)
     b, _ = oracle.deep_shallow(grid, dpar=oracle.deep_params(n_plumes=n, plume_spread=1.0),
