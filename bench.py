@@ -160,25 +160,48 @@ def t_fp64_islands(c, r):
     return c["fp64_lcl_corrections"] * lcl
 
 
+# Nominal ALU peaks from unit counts and clocks: 152 SMs at the 2070 MHz maximum
+# SM clock; per SM and clock 128 FP32 FMA lanes and 2 FP64 FMA units (the
+# latter give 1.26 TFLOP/s, GB300's quoted FP64 rate).
+SMS, SM_MHZ = 152, 2070.0
+FMA_PER_SM_CLOCK = {"fp32": 128, "fp64": 2}
+
+
+def nominal_fma_rate(pipe):
+    """FMAs per second of a pipe at the maximum SM clock."""
+    return SMS * FMA_PER_SM_CLOCK[pipe] * SM_MHZ * 1e6
+
+
 def kernel_roofline(counts, precision, kernel_s, n_cols, r):
-    """Arithmetic roofline of one kernel: the time its algorithmic work needs on
-    the binding pipe at the measured per-operation throughput.  FP64 path: every
-    operation on the FP64 pipe.  Mixed path: the bulk on the FP32 pipes (fast
-    intrinsic rates, the lowest bound) and the FP64 islands on the FP64 pipe; the
-    larger of the two binds."""
+    """Arithmetic roofline of one kernel.  Its algorithmic work is weighed in
+    FMA-equivalents on the binding pipe (each operation class at its cost
+    relative to an FMA, from the measured per-operation throughputs r); the
+    achieved rate of that work is compared with the pipe's nominal FMA peak
+    (unit counts x clock), and with its measured FMA rate beside it.  FP64 path:
+    every operation on the FP64 pipe.  Mixed path: the bulk on the FP32 pipes
+    (fast intrinsic rates, the lowest bound) and the FP64 islands on the FP64
+    pipe; the larger of the two binds."""
     if precision == "fp64":
         t64, t32 = t_ops(counts, r, "fp64_") * n_cols, 0.0
     else:
         t64, t32 = t_fp64_islands(counts, r) * n_cols, t_ops(counts, r, "fp32_") * n_cols
     fp64_binds = t64 >= t32
-    t_bound = t64 if fp64_binds else t32
-    peak = 2.0 * (r["fp64_fma"] if fp64_binds else r["fp32_fma"])
-    return {"bound": "alu", "binding_pipe": "fp64" if fp64_binds else "fp32",
-            "achieved": peak * t_bound / kernel_s / 1e12, "peak": peak / 1e12,
+    pipe = "fp64" if fp64_binds else "fp32"
+    t_bound = t64 if fp64_binds else t32  # the work's time at the measured rates
+    measured = 2.0 * r[pipe + "_fma"]  # FLOP/s
+    peak = 2.0 * nominal_fma_rate(pipe)
+    achieved = measured * t_bound / kernel_s  # FMA-equivalent FLOP/s of the work
+    return {"bound": "alu", "binding_pipe": pipe,
+            "achieved": achieved / 1e12, "peak": peak / 1e12,
             "unit": "TFLOP/s (FMA-equivalent on the binding pipe)",
-            "frac": t_bound / kernel_s, "t_bound_fp64_ms": t64 * 1e3,
-            "t_bound_fp32_ms": t32 * 1e3, "kernel_ms": kernel_s * 1e3, "traffic": None,
-            "peak_source": "measured FMA rate of the binding pipe (conv_bench_op_rate)"}
+            "frac": achieved / peak, "peak_measured": measured / 1e12,
+            "frac_of_measured": t_bound / kernel_s,
+            "t_bound_fp64_ms": t64 * 1e3, "t_bound_fp32_ms": t32 * 1e3,
+            "kernel_ms": kernel_s * 1e3, "traffic": None,
+            "peak_source": (f"{SMS} SMs x {FMA_PER_SM_CLOCK[pipe]} {pipe.upper()} FMA per "
+                            f"clock x 2 FLOP x {SM_MHZ:.0f} MHz (unit counts and maximum SM "
+                            "clock); peak_measured: this device's FMA rate "
+                            "(conv_bench_op_rate)")}
 
 
 def hbm_bytes_per_column(pver, real_bytes):
@@ -424,8 +447,10 @@ def ours_arm(args, rank, world, local_rank):
     roof["op_counts_workload"] = key
     rb = 8 if prec == "fp64" else 4
     roof["hbm_algorithmic_bytes_per_column"] = hbm_bytes_per_column(pver, rb)
+    hbm_peak, hbm_src = measured_hbm()
     roof["hbm_frac_of_measured_path"] = (hbm_bytes_per_column(pver, rb) * n / (ms * 1e-3) / 1e9
-                                         / measured_hbm())
+                                         / hbm_peak)
+    roof["hbm_peak_source"] = hbm_src
     ens = None if args.no_ensemble else ensemble_bench(args, dev)
     adj = None if args.no_adjoint else adjoint_bench(args, dev, g)
     trn = None if args.no_transport else transport_bench(args, dev, g)
@@ -670,7 +695,7 @@ def transport_bench(args, dev, g, ntr=25):
     tracer_bytes = ntr * (2 * pver * n * es + int(read_levels.sum()) * es)
     alg = tracer_bytes + int(per_col_prof.sum())
     achieved = alg / (ms * 1e-3) / 1e9
-    peak = measured_hbm()
+    peak, peak_src = measured_hbm()
     return {"tracers": ntr, "columns": n, "levels": pver, "precision": "mixed",
             "ms_transport": ms, "value": ntr * n / (ms * 1e-3), "unit": "tracer-columns/s",
             "ms_step_with_profiles": step_flux, "ms_step_without_profiles": step_plain,
@@ -683,7 +708,7 @@ def transport_bench(args, dev, g, ntr=25):
                          "frac": achieved / peak, "algorithmic_bytes": alg,
                          "traffic": ncu_traffic(g.name + "-tracers25", "transport").get(
                              "k_transport"),
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+                         "peak_source": peak_src}}
 
 
 def driver_bench(args, dev, g):
@@ -772,11 +797,14 @@ def ncu_traffic(workload, group="step"):
 
 
 def measured_hbm():
+    """HBM copy bandwidth in GB/s and where it comes from: the figure measured on
+    this machine's GPUs (MEASURED_PEAKS.json), else 6.8 TB/s, one earlier copy
+    measurement on a GB300."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            return float(json.load(fh)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6800.0
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return 6800.0, "6.8 TB/s from an earlier GB300 copy measurement (of fallback)"
 
 
 def main():
