@@ -49,8 +49,9 @@ conv_status fill_grid(const conv_grid* g, RunArgs& a) {
     a.L.ap0f[i] = (float)(a.L.a[i] * g->p0);
     a.L.bf[i] = (float)a.L.b[i];
   }
-  for (int i = 0; i < g->pver; ++i) {  // interfaces must be ordered top -> surface
+  for (int i = 0; i <= g->pver; ++i)  // all pver + 1 interfaces, the surface included
     if (!std::isfinite(g->hyai[i]) || !std::isfinite(g->hybi[i])) return CONV_ERR_ARG;
+  for (int i = 0; i < g->pver; ++i) {  // interfaces must be ordered top -> surface
     if (g->hyai[i + 1] * g->p0 + g->hybi[i + 1] * 1e5 <= g->hyai[i] * g->p0 + g->hybi[i] * 1e5)
       return CONV_ERR_ARG;
   }

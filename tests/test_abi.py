@@ -296,3 +296,22 @@ def test_plume_spectrum_arguments():
                                        1800.0, L.CONV_FP64, None, None, None, None, None, fake,
                                        fake, fake, fake, None, 1, None)
     assert st == L.CONV_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("which,k,val", [("a", -1, float("nan")), ("b", -1, float("inf")),
+                                         ("a", 0, float("nan")), ("b", 12, float("nan"))])
+def test_non_finite_level_coefficients_rejected(which, k, val):
+    """Every one of the pver + 1 interface coefficients must be finite, the
+    surface interface included (a NaN there compares false in the ordering
+    check, so finiteness is checked on its own)."""
+    g, inp, out, (a, b) = _args()
+    arr = (a if which == "a" else b).copy()
+    arr[k] = val
+    dp = C.POINTER(C.c_double)
+    if which == "a":
+        g.hyai = arr.ctypes.data_as(dp)
+    else:
+        g.hybi = arr.ctypes.data_as(dp)
+    st = L.lib().conv_deep_run(C.byref(g), C.byref(inp), C.byref(L.deep_defaults()), 1800.0,
+                               L.CONV_FP64, C.byref(out), None, None, 0, None)
+    assert st == L.CONV_ERR_ARG
