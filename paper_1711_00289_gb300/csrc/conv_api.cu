@@ -10,12 +10,15 @@
 #include <vector>
 
 #include "compact.h"
+#include "validate.h"
 
 namespace {
 
-using cvg::RunArgs;
-
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+namespace cvg {
 
 bool deep_params_ok(const conv_deep_params* p) {
   return p && finite_pos(p->capelmt + 1.0) && p->capelmt >= 0.0 && p->lambda_default >= 0.0 &&
@@ -36,6 +39,14 @@ bool shallow_params_ok(const conv_shallow_params* p) {
          p->n_newton_lcl >= 1 && p->n_newton_lcl <= 32 && p->n_newton_h >= 0 &&
          p->n_newton_h <= 32 && std::isfinite(p->evap_k) && p->evap_k >= 0.0;
 }
+
+}  // namespace cvg
+
+namespace {
+
+using cvg::deep_params_ok;
+using cvg::RunArgs;
+using cvg::shallow_params_ok;
 
 conv_status fill_grid(const conv_grid* g, RunArgs& a) {
   if (!g || g->pver < 4 || g->pver > CONV_MAX_LEVELS || g->n_cols < 0 || g->ld < g->n_cols ||
@@ -145,6 +156,12 @@ conv_status common_in(const conv_grid* grid, const conv_in* in, double dt, RunAr
 }
 
 }  // namespace
+
+bool cvg::grid_ok(const conv_grid* g) {
+  RunArgs a;
+  std::memset(&a, 0, sizeof a);
+  return fill_grid(g, a) == CONV_OK;
+}
 
 extern "C" {
 

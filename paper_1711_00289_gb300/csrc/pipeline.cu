@@ -4,10 +4,12 @@
 // chunk j-1 copies out (the Grace-Blackwell host link carries both directions
 // at once).  The plan owns the device staging slots, streams and events; runs
 // allocate nothing.
+#include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "compact.h"
+#include "validate.h"
 
 namespace {
 
@@ -104,9 +106,7 @@ conv_status conv_pipeline_plan(const conv_grid* grid, conv_precision prec, int c
                                conv_pipeline** out) {
   if (!out) return CONV_ERR_ARG;
   *out = nullptr;
-  if (!grid || grid->pver < 4 || grid->pver > CONV_MAX_LEVELS || grid->n_cols < 1 ||
-      grid->ld < grid->n_cols || !grid->hyai || !grid->hybi)
-    return CONV_ERR_ARG;
+  if (!cvg::grid_ok(grid) || grid->n_cols < 1) return CONV_ERR_ARG;
   if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
   if (chunk_cols < 1) return CONV_ERR_ARG;
   conv_pipeline* p = new conv_pipeline();
@@ -148,9 +148,14 @@ conv_status conv_pipeline_run(conv_pipeline* p, const conv_in* host_in,
                               const conv_deep_params* dpar, const conv_shallow_params* spar,
                               double dt, const conv_out* host_deep, const conv_out* host_shallow,
                               conv_stream stream) {
-  if (!p || !host_in || !host_in->T || !host_in->q || !host_in->ps || !dpar || !spar ||
-      !host_deep || !host_shallow || !host_deep->dTdt || !host_deep->dqdt ||
-      !host_shallow->dTdt || !host_shallow->dqdt)
+  // Everything a chunk's run would refuse is refused here, before the first copy
+  // is enqueued: an error return never leaves copies of the caller's buffers in
+  // flight.
+  if (!p || !host_in || !host_in->T || !host_in->q || !host_in->ps || !host_deep ||
+      !host_shallow || !host_deep->dTdt || !host_deep->dqdt || !host_deep->prec ||
+      !host_deep->flags || !host_shallow->dTdt || !host_shallow->dqdt || !host_shallow->prec ||
+      !host_shallow->flags || !cvg::deep_params_ok(dpar) || !cvg::shallow_params_ok(spar) ||
+      !(std::isfinite(dt) && dt > 0.0))
     return CONV_ERR_ARG;
   for (const conv_out* h : {host_deep, host_shallow})
     if (h->mu || h->du || h->md) return CONV_ERR_UNSUPPORTED;

@@ -315,3 +315,41 @@ def test_non_finite_level_coefficients_rejected(which, k, val):
     st = L.lib().conv_deep_run(C.byref(g), C.byref(inp), C.byref(L.deep_defaults()), 1800.0,
                                L.CONV_FP64, C.byref(out), None, None, 0, None)
     assert st == L.CONV_ERR_ARG
+
+
+def test_pipeline_checks_everything_before_its_first_copy():
+    """A pipeline run refuses bad parameter blocks, dt and missing required host
+    outputs before it touches its plan or enqueues a copy, so an error return
+    never leaves copies of the caller's buffers in flight (the plan handle below
+    is never dereferenced); a plan refuses a level table a run would refuse."""
+    g, inp, out, (a, b) = _args(n=10, ld=10)
+    lib = L.lib()
+    plan = C.c_void_p(0x1000)
+    fake = C.c_void_p(0x1000)
+
+    def run(dp=None, sp=None, dt=1800.0, od=out, os_=out):
+        return lib.conv_pipeline_run(plan, C.byref(inp), C.byref(dp or L.deep_defaults()),
+                                     C.byref(sp or L.shallow_defaults()), dt, C.byref(od),
+                                     C.byref(os_), None)
+
+    bad_d = L.deep_defaults()
+    bad_d.tau_default = -1.0
+    bad_s = L.shallow_defaults()
+    bad_s.tke = 0.0
+    no_prec = L.Out(fake, fake, None, fake, None, None, None, None, None, None, None)
+    assert run(dp=bad_d) == L.CONV_ERR_ARG
+    assert run(sp=bad_s) == L.CONV_ERR_ARG
+    assert run(dt=0.0) == L.CONV_ERR_ARG
+    assert run(dt=float("nan")) == L.CONV_ERR_ARG
+    assert run(od=no_prec) == L.CONV_ERR_ARG
+    assert run(os_=no_prec) == L.CONV_ERR_ARG
+    a2 = a.copy()
+    a2[-1] = float("nan")
+    g.hyai = a2.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    assert lib.conv_pipeline_plan(C.byref(g), L.CONV_MIXED, 16, C.byref(h)) == L.CONV_ERR_ARG
+    a3, b3 = a[::-1].copy(), b[::-1].copy()  # surface first: interfaces out of order
+    g.hyai = a3.ctypes.data_as(C.POINTER(C.c_double))
+    g.hybi = b3.ctypes.data_as(C.POINTER(C.c_double))
+    assert lib.conv_pipeline_plan(C.byref(g), L.CONV_MIXED, 16, C.byref(h)) == L.CONV_ERR_ARG
+    assert not h.value
