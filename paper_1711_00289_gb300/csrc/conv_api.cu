@@ -530,9 +530,11 @@ conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_s
     return CONV_ERR_WORKSPACE;
   const bool fp64 = b->prec == CONV_FP64;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaEvent_t e0, e1;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
     return CONV_ERR_CUDA;
+  }
   cvg::BatchDev d{b->d_members, b->d_offsets, b->n_members, b->total};
   auto time_shape = [&](const cvg::BatchShape& sh, float* ms) -> cudaError_t {
     cudaError_t err = cvg::launch_batch(d, sh, fp64, ws, ws_bytes, s, nullptr);  // warm-up
