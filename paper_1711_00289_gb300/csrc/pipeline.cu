@@ -167,6 +167,10 @@ conv_status conv_pipeline_run(conv_pipeline* p, const conv_in* host_in,
     if ((x) != cudaSuccess) return CONV_ERR_CUDA; \
   } while (0)
   CK(cudaEventRecord(p->start, user));
+  // The slots are reused from the first chunk on: copies in wait for the
+  // previous run's last copy out even when that run went through another user
+  // stream (before any run, `done` has never been recorded and this is a no-op).
+  CK(cudaStreamWaitEvent(p->sh, p->done, 0));
   CK(cudaStreamWaitEvent(p->sh, p->start, 0));
   CK(cudaStreamWaitEvent(p->sc, p->start, 0));
   CK(cudaStreamWaitEvent(p->sd, p->start, 0));
