@@ -112,7 +112,23 @@ PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_adjoint.py"]
 TRANSPORT = "tests/test_oracle_transport.py"
 EVAPORATION = "tests/test_oracle_evaporation.py"
 SPECTRUM = "tests/test_oracle_spectrum.py"
+ADJOINT = "tests/test_oracle_adjoint.py"
+# The forward-mode type's rules for pow and sqrt are left out: no derivative
+# that reaches an output passes through them (pow's differentiated argument is
+# the LCL pressure, which only places levels; sqrt takes a constant), so a slip
+# there changes nothing a pin could see.
 EXT_MUTANTS = {
+    "tangent quotient rule sign": (
+        "r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;", "r.d[i] = (a.d[i] + r.v * b.d[i]) / b.v;",
+        ADJOINT),
+    "tangent product rule drops a term": (
+        "r.d[i] = a.d[i] * b.v + a.v * b.d[i];", "r.d[i] = a.d[i] * b.v;", ADJOINT),
+    "tangent of log": (
+        "for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] / a.v;",
+        "for (int i = 0; i < ND; ++i) r.d[i] = a.d[i] * a.v;", ADJOINT),
+    "tangent of exp": (
+        "for (int i = 0; i < ND; ++i) r.d[i] = r.v * a.d[i];",
+        "for (int i = 0; i < ND; ++i) r.d[i] = a.d[i];", ADJOINT),
     "tracer updraft entrains the layer below": (
         "cu[k] = (s.eta[k + 1] * cu[k + 1] + (s.eta[k] - s.eta[k + 1]) * c[k]) / s.eta[k];",
         "cu[k] = (s.eta[k + 1] * cu[k + 1] + (s.eta[k] - s.eta[k + 1]) * c[k + 1]) / s.eta[k];",
