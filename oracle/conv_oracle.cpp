@@ -234,6 +234,7 @@ void sat_qs_dqs(const R& T, const R& p, R& qs, R& dqs) {
     dqs = qs * (p / D) * dlnes;
   }
 }
+// The saturation specific humidity alone (the same clamped denominator).
 template <class R>
 R sat_qs(const R& T, const R& p) {
   const R es = sat_es(T);
@@ -326,6 +327,10 @@ int lcl_level(const R* p_mid, int kstart, const R& pL) {
   return -1;
 }
 
+// Input check of one column (flag bit 4, "bad input", of the frozen interface):
+// surface pressure within 500-1200 hPa, every temperature within 100-400 K and
+// every humidity within [0, 0.1) kg/kg, NaN failing each test.  A column that
+// fails is left with zero outputs and only that flag.
 template <class R>
 bool column_valid(int pver, const R* T, const R* q, const R& ps) {
   if (!(val(ps) > 5.0e4 && val(ps) < 1.2e5)) return false;
