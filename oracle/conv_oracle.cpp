@@ -27,7 +27,10 @@
 // downdraft tops from h* computed by its definition), column energy/water
 // conservation, non-negativity, shallow rain bounded by the plume's condensate,
 // exact zeros outside the trigger, linearity of the closure in 1/tau, and
-// finite differences for the tangent.  Tracer transport (tests/test_oracle_transport.py): uniform tracers
+// finite differences for the tangent.  Randomised columns (inversions,
+// superadiabatic, moist and dry layers; tests/test_oracle_random.py): budgets
+// closed, exact zeros off the trigger, ordered level indices, the humidity
+// limiter holding.  Tracer transport (tests/test_oracle_transport.py): uniform tracers
 // unchanged, column tracer mass conserved, upwind monotone transport matrices,
 // the moist static energy transported as each scheme transports it, and the
 // mass-flux profiles carrying the same transport when it is written as a budget
