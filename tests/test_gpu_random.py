@@ -1,0 +1,57 @@
+"""Parity on randomly perturbed soundings (inversions, superadiabatic, moist and
+dry layers, surface pressures of 600-1040 hPa, random entrainment rates and
+closure times): FP64 against the oracle on both paths, decisions bit-exact and
+values within 1e-10.  The mixed path is held to its budget here too and does not
+meet it yet (a known gap, marked as an expected failure): on 3,000 such columns
+its decisions all agree, but the deep column integrals differ by up to 9.3e-4
+(budget 1e-4) and precipitation by 1.4e-3 (budget 1e-3).  The oracle's own
+column code evaluated in plain FP32 stays within 2.8e-5 on the same columns,
+so the loss comes from the mixed path's shortcuts (warm-started Newton solves
+of two steps, whose level-to-level predictor is poor across inversions), not
+from single precision as such."""
+import numpy as np
+import pytest
+
+from paper_1711_00289_gb300 import soundings as S
+from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu,
+                            same_decisions)
+from tests.test_oracle_random import _random_columns
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def grid():
+    return _random_columns(7, n=3000)
+
+
+@pytest.mark.parametrize("path", ["plain", "compact"])
+def test_fp64(oracle, grid, path):
+    rd, rs = oracle.deep_shallow(grid, threads=THREADS)
+    gd, gs = run_gpu(grid, "fp64", path, ld=S.pad_ld(grid.n_cols) + 32)
+    assert_fp64_parity(gd, rd, what=f"deep {path}")
+    assert_fp64_parity(gs, rs, what=f"shallow {path}")
+
+
+@pytest.mark.xfail(strict=False, reason="mixed path outside its budget on rough soundings "
+                   "(deep column integrals 9.3e-4, precipitation 1.4e-3; decisions identical)")
+def test_mixed(oracle, grid):
+    rd, rs = oracle.deep_shallow(grid, threads=THREADS)
+    gd, gs = run_gpu(grid, "mixed", "compact")
+    for o in (rd, rs, gd, gs):
+        o["flags"] = o["flags"] & ~8
+    m = layer_mass(grid)
+    psurf = rd["prec"] + rs["prec"]
+    for tag, got, ref, up in (("deep", gd, rd, None), ("shallow", gs, rs, same_decisions(gd, rd))):
+        r = mixed_report(got, ref, m, up, psurf)
+        assert r["decision_mismatch"] <= 3e-3 * r["n"], f"{tag} {r}"
+        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
+    assert np.isfinite(gd["dTdt"]).all() and np.isfinite(gs["dTdt"]).all()
