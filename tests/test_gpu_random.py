@@ -6,9 +6,8 @@ meet it yet (a known gap, marked as an expected failure): on 3,000 such columns
 its decisions all agree, but the deep column integrals differ by up to 9.3e-4
 (budget 1e-4) and precipitation by 1.4e-3 (budget 1e-3).  The oracle's own
 column code evaluated in plain FP32 stays within 2.8e-5 on the same columns,
-so the loss comes from the mixed path's shortcuts (warm-started Newton solves
-of two steps, whose level-to-level predictor is poor across inversions), not
-from single precision as such."""
+so the loss comes from one of the mixed path's own arithmetic choices, not from
+single precision as such; which one is not yet isolated."""
 import numpy as np
 import pytest
 
