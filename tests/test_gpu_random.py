@@ -8,9 +8,9 @@ FP64 against the oracle on both paths: decisions bit-exact, values within
 The mixed path against a converged reference.  With the default iteration
 counts the oracle's cold-started moist inversions stop short of convergence in
 161 of the 1,787 columns the deep scheme acts on (the parcel of a 17,000 J/kg
-CAPE column lies far from the environment temperature they start from); the mixed path's
-warm-started solves do converge there, so the default oracle is not the
-solution to measure it against.  The same equations solved with 8 Newton steps
+CAPE column lies far from the environment temperature they start from); the
+mixed path's warm-started solves do converge there, so the default oracle is
+not the solution to measure it against.  The same equations solved with 8 Newton steps
 leave no solve unconverged, and against them the mixed path's tendencies are
 within the budget.  Its precipitation is not yet: two columns of trace drizzle
 (rain 1.5 times the precipitation floor, from a condensate 1.1e-5 kg/kg above
