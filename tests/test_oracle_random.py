@@ -60,3 +60,15 @@ def test_invariants_on_random_columns(oracle, seed):
             codes = (o["flags"] >> F.EXIT_SHIFT) & 7
             assert np.all(codes[act] == 0)
             assert np.all(codes[off & ~bad] > 0)
+
+
+def test_fixed_newton_counts_on_rough_columns(oracle):
+    """The premise of the mixed path's random-sounding parity test: at the
+    default iteration count the oracle's cold-started moist inversions leave some
+    solves of these columns unconverged (and flag them), and with 8 steps none."""
+    g = _random_columns(7, n=3000)
+    d4, s4 = oracle.deep_shallow(g, threads=4)
+    d8, s8 = oracle.deep_shallow(g, dpar=oracle.deep_params(n_newton_h=8),
+                                 spar=oracle.shallow_params(n_newton_h=8), threads=4)
+    assert ((d4["flags"] & oracle.F_NEWTON) > 0).sum() > 100
+    assert not ((d8["flags"] | s8["flags"]) & oracle.F_NEWTON).any()
