@@ -7,8 +7,8 @@ FP64 against the oracle on both paths: decisions bit-exact, values within
 
 The mixed path against a converged reference.  With the default iteration
 counts the oracle's cold-started moist inversions stop short of convergence in
-161 of the 1,787 columns the deep scheme acts on (the parcel of a 17,000 J/kg
-CAPE column lies far from the environment temperature they start from); the
+161 of the 1,787 columns the deep scheme acts on (with CAPE of 5,500-26,000
+J/kg the parcel lies far from the environment temperature they start from); the
 mixed path's warm-started solves do converge there, so the default oracle is
 not the solution to measure it against.  The same equations solved with 8 Newton steps
 leave no solve unconverged, and against them the mixed path's tendencies are
