@@ -72,3 +72,31 @@ def test_fixed_newton_counts_on_rough_columns(oracle):
                                  spar=oracle.shallow_params(n_newton_h=8), threads=4)
     assert ((d4["flags"] & oracle.F_NEWTON) > 0).sum() > 100
     assert not ((d8["flags"] | s8["flags"]) & oracle.F_NEWTON).any()
+
+
+def test_bad_input_columns(oracle):
+    """Columns outside the accepted input ranges (surface pressure 500-1200 hPa,
+    temperature 100-400 K, humidity [0, 0.1) kg/kg, NaN anywhere) are flagged as
+    bad input with zero outputs in both schemes; columns just inside the ranges
+    are not."""
+    g = _random_columns(11, n=12)
+    T, q, ps = g.T.copy(), g.q.copy(), g.ps.copy()
+    ps[0] = 4.99e4
+    ps[1] = 1.21e5
+    T[5, 2] = float("nan")
+    T[10, 3] = 401.0
+    q[20, 4] = -1e-9
+    q[25, 5] = 0.1
+    q[3, 6] = float("nan")
+    ps[7] = 5.01e4
+    T[0, 8] = 101.0
+    g2 = type(g)(g.name, g.pver, T, q, ps, g.hyai, g.hybi, g.lam, g.tau, g.dt)
+    d, s = oracle.deep_shallow(g2, threads=2)
+    want = np.zeros(g.n_cols, bool)
+    want[:7] = True
+    for o in (d, s):
+        got = (o["flags"] & oracle.F_BADINPUT) > 0
+        assert np.array_equal(got, want), got
+        assert np.all(o["flags"][want] == oracle.F_BADINPUT)
+        assert np.all(o["dTdt"][:, want] == 0.0) and np.all(o["dqdt"][:, want] == 0.0)
+        assert np.all(o["prec"][want] == 0.0)
