@@ -172,8 +172,10 @@ inline Cnt pow(const Cnt& a, double e) { g_count[C_POW] += 1; return Cnt(std::po
 
 // FP64-island work of the mixed-precision design, tallied by the counting
 // instantiation only: LCL solves (each ends with one FP64 Newton correction),
-// CAPE terms and CIN terms accumulated in FP64, conservation-sum terms.
-enum { I_LCL = 0, I_CAPE, I_CIN, I_CONS, I_NCAT };
+// CAPE terms and CIN terms accumulated in FP64, conservation-sum terms, and
+// saturated shallow plume layers whose rain lies within 1e-4 kg/kg of zero
+// (the mixed path refines their saturation temperature in FP64).
+enum { I_LCL = 0, I_CAPE, I_CIN, I_CONS, I_DRIZZLE, I_NCAT };
 thread_local double g_island[I_NCAT];
 // Snapshot of g_count when the deep trigger stage ends (launch level through
 // the CAPE trigger): splits the deep work between the trigger and plume passes.
@@ -187,6 +189,16 @@ inline void mark_trigger_end() {}
 template <>
 inline void mark_trigger_end<Cnt>() {
   for (int c = 0; c < C_NCAT; ++c) g_mark[c] = g_count[c];
+}
+// Snapshots of g_count around the shallow scheme's undilute-parcel LFC search
+// (begin, end): the search's work, which in a column that ends at exit E2 (no
+// LFC) an implementation may settle by cheaper bounds.
+thread_local double g_lfc0[C_NCAT], g_lfc1[C_NCAT];
+template <class R>
+inline void mark_lfc_search(bool) {}
+template <>
+inline void mark_lfc_search<Cnt>(bool end) {
+  for (int c = 0; c < C_NCAT; ++c) (end ? g_lfc1 : g_lfc0)[c] = g_count[c];
 }
 
 // ---------------------------------------------------------------- parameters
@@ -272,9 +284,36 @@ void heights(int pver, const R* T, const R* q, const R* p_int, const R* p_mid, R
 }
 
 // Newton inversion of moist static energy for a saturated parcel: find T with
-// cp T + g z + Lv qs(T, p) = h.  The first step starts from T_start (the
-// environment), then n_extra more; fixed count so every implementation takes
-// the same path.  This is the column model's analogue of `ientropy` (Alg. 2).
+// cp T + g z + Lv qs(T, p) = h.  Newton from T_start (the environment); the
+// loop tests convergence for termination, as the scheme loops the paper times
+// do (Sec. V-E): it stops after the first correction smaller than H_STOP, and
+// after at most 1 + n_extra steps.  The residual is increasing and convex in T
+// with f''/2f' <= 0.1 / K, so the error left after a correction c is about
+// 0.1 c^2: below H_STOP = 1e-7 K it is ~1e-15 K, under the rounding of T.
+// Solves far from their start (a parcel 10-50 K warmer than the environment)
+// take up to ten steps; most take three to five.  This is the column model's
+// analogue of `ientropy` (Alg. 2).  The tangent of the solution (Dual) is taken
+// by the implicit function theorem at the final iterate (ift_tangent).
+constexpr double H_STOP = 1e-7;  // K
+
+template <class R>
+inline R ift_tangent(const R&, const R&, const R&, const R& T) {
+  return T;
+}
+// dT = -(df/dtheta)/(df/dT) at the solution: one Newton correction applied to the
+// tangent part only (f's tangent carries df/dT dT_iterate + df/dtheta dtheta, so
+// the result no longer depends on how the iterate's tangent was built).
+template <>
+inline Dual ift_tangent<Dual>(const Dual& h, const Dual& gz, const Dual& p, const Dual& T) {
+  Dual qs, dqs;
+  sat_qs_dqs(T, p, qs, dqs);
+  const Dual f = CP * T + gz + LV * qs - h;
+  const double fp = CP + LV * dqs.v;
+  Dual r = T;
+  for (int i = 0; i < ND; ++i) r.d[i] = T.d[i] - f.d[i] / fp;
+  return r;
+}
+
 template <class R>
 R moist_invert(const R& h, const R& gz, const R& p, R T, int n_extra, double* last_step) {
   for (int it = 0; it <= n_extra; ++it) {
@@ -285,8 +324,9 @@ R moist_invert(const R& h, const R& gz, const R& p, R T, int n_extra, double* la
     const R step = f / fp;
     T = T - step;
     if (last_step) *last_step = std::fabs(val(step));
+    if (std::fabs(val(step)) < H_STOP) break;
   }
-  return T;
+  return ift_tangent(h, gz, p, T);
 }
 
 // Lifting condensation level of a parcel (Tb, qb, pb) lifted dry-adiabatically.
@@ -682,6 +722,7 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
 
   // Undilute parcel from the source up to the LFC search limit.
   int klfc = -1;
+  mark_lfc_search<R>(false);
   for (int k = ks; k >= ktl && val(s.p_mid[k]) >= P.p_lfc_min; --k) {
     R Tp, qp;
     if (k > klcl) {
@@ -696,6 +737,7 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
     s.b[k] = Tp * (1.0 + ZVIR * qp) - s.Tv[k];
     if (k <= klcl && val(s.b[k]) > 0.0) { klfc = k; break; }
   }
+  mark_lfc_search<R>(true);
   s.klfc = klfc;
   if (klfc < 0) { s.exit_code = 2; return; }
   R cin(0.0);
@@ -761,6 +803,7 @@ void shallow_column(int pver, const double* hyai, const double* hybi, double p0,
       if (!(val(s.w2[k]) > 0.0)) { kts = k + 1; break; }
     }
     if (k == ktl) { kts = k; break; }
+    if (val(qt) >= val(qsu) && std::fabs(val(l) - P.ql_crit) < 1e-4) island<R>(I_DRIZZLE, 1);
     R r = l - P.ql_crit;
     if (val(r) < 0.0) r = R(0.0);
     s.rf[k] = r;
@@ -937,12 +980,13 @@ void store_flux(const oracle_flux* f, int pver, int ld, int i, const double* mu,
 inline void set_i(int32_t* a, int i, int v) { if (a) a[i] = v; }
 inline void set_d(double* a, int i, double v) { if (a) a[i] = v; }
 
-void store_deep(const DeepState<double>& s, int pver, int ld, int i, const oracle_out* o) {
+template <class R>
+void store_deep(const DeepState<R>& s, int pver, int ld, int i, const oracle_out* o) {
   for (int k = 0; k < pver; ++k) {
-    set_d(o->dTdt, k * ld + i, s.dTdt[k]);
-    set_d(o->dqdt, k * ld + i, s.dqdt[k]);
+    set_d(o->dTdt, k * ld + i, val(s.dTdt[k]));
+    set_d(o->dqdt, k * ld + i, val(s.dqdt[k]));
   }
-  set_d(o->prec, i, s.prec);
+  set_d(o->prec, i, val(s.prec));
   int fl = 0;
   if (s.bad) fl |= F_BADINPUT;
   if (s.triggered) fl |= F_TRIGGERED;
@@ -954,17 +998,18 @@ void store_deep(const DeepState<double>& s, int pver, int ld, int i, const oracl
   set_i(o->klcl, i, s.klcl);
   set_i(o->ktop, i, s.active ? s.jt : -1);
   set_i(o->kaux, i, s.active ? s.jd : -1);
-  set_d(o->cape, i, s.cape);
-  set_d(o->mb, i, s.mb);
+  set_d(o->cape, i, val(s.cape));
+  set_d(o->mb, i, val(s.mb));
   set_d(o->cons_err, i, s.cons_err);
 }
 
-void store_shallow(const ShalState<double>& s, int pver, int ld, int i, const oracle_out* o) {
+template <class R>
+void store_shallow(const ShalState<R>& s, int pver, int ld, int i, const oracle_out* o) {
   for (int k = 0; k < pver; ++k) {
-    set_d(o->dTdt, k * ld + i, s.active ? s.dT[k] : 0.0);
-    set_d(o->dqdt, k * ld + i, s.active ? s.dq[k] : 0.0);
+    set_d(o->dTdt, k * ld + i, s.active ? val(s.dT[k]) : 0.0);
+    set_d(o->dqdt, k * ld + i, s.active ? val(s.dq[k]) : 0.0);
   }
-  set_d(o->prec, i, s.active ? s.prec : 0.0);
+  set_d(o->prec, i, s.active ? val(s.prec) : 0.0);
   int fl = 0;
   if (s.bad) fl |= F_BADINPUT;
   if (s.triggered) fl |= F_TRIGGERED;
@@ -976,8 +1021,8 @@ void store_shallow(const ShalState<double>& s, int pver, int ld, int i, const or
   set_i(o->klcl, i, s.klcl);
   set_i(o->ktop, i, s.active ? s.kts : -1);
   set_i(o->kaux, i, s.klfc);
-  set_d(o->cape, i, s.cin);
-  set_d(o->mb, i, s.active ? s.mb : 0.0);
+  set_d(o->cape, i, val(s.cin));
+  set_d(o->mb, i, s.active ? val(s.mb) : 0.0);
   set_d(o->cons_err, i, s.active ? s.cons_err : 0.0);
 }
 
@@ -1283,6 +1328,35 @@ int oracle_deep_shallow_adjoint(int n_cols, int pver, int ld, const double* hyai
   return 0;
 }
 
+int oracle_deep_shallow_counted(int n_cols, int pver, int ld, const double* hyai,
+                                const double* hybi, double p0, const double* T, const double* q,
+                                const double* ps, const oracle_deep_params* dpar,
+                                const oracle_shallow_params* spar, double dt,
+                                const oracle_out* deep, const oracle_out* shallow) {
+  if (!grid_ok(n_cols, pver, ld) || !dpar || !spar || !deep || !shallow) return 1;
+  const DeepP DP = to_deep(dpar);
+  const ShalP SP = to_shal(spar);
+  std::unique_ptr<DeepState<Cnt>> sp(new DeepState<Cnt>());
+  std::unique_ptr<ShalState<Cnt>> tp(new ShalState<Cnt>());
+  for (int i = 0; i < n_cols; ++i) {
+    Cnt Tc[MAXLEV], qc[MAXLEV], T2[MAXLEV], q2[MAXLEV];
+    for (int k = 0; k < pver; ++k) { Tc[k] = Cnt(T[k * ld + i]); qc[k] = Cnt(q[k * ld + i]); }
+    *sp = DeepState<Cnt>();
+    *tp = ShalState<Cnt>();
+    deep_column<Cnt>(pver, hyai, hybi, p0, Tc, qc, Cnt(ps[i]), Cnt(DP.lambda_default),
+                     Cnt(DP.tau_default), DP, dt, *sp);
+    store_deep(*sp, pver, ld, i, deep);
+    for (int k = 0; k < pver; ++k) {
+      T2[k] = Tc[k] + dt * sp->dTdt[k].v;
+      q2[k] = qc[k] + dt * sp->dqdt[k].v;
+      if (!sp->bad && q2[k].v < 0.0) q2[k] = Cnt(0.0);
+    }
+    shallow_column<Cnt>(pver, hyai, hybi, p0, T2, q2, Cnt(ps[i]), SP, *tp);
+    store_shallow(*tp, pver, ld, i, shallow);
+  }
+  return 0;
+}
+
 int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const double* hybi,
                      double p0, const double* T, const double* q, const double* ps,
                      const oracle_deep_params* dpar, const oracle_shallow_params* spar,
@@ -1320,12 +1394,14 @@ int oracle_count_ops_by_pass(int n_cols, int pver, int ld, const double* hyai,
                              const double* hybi, double p0, const double* T, const double* q,
                              const double* ps, const oracle_deep_params* dpar,
                              const oracle_shallow_params* spar, double dt, double* trigger_pass,
-                             double* plume_pass, double* n_triggered) {
+                             double* plume_pass, double* n_triggered, double* e2_search) {
   if (!grid_ok(n_cols, pver, ld) || !dpar || !spar || !trigger_pass || !plume_pass) return 1;
   const DeepP DP = to_deep(dpar);
   const ShalP SP = to_shal(spar);
   const int W = C_NCAT + I_NCAT;
   for (int c = 0; c < W; ++c) trigger_pass[c] = plume_pass[c] = 0.0;
+  if (e2_search)
+    for (int c = 0; c < C_NCAT; ++c) e2_search[c] = 0.0;
   double ntrig = 0.0;
   std::unique_ptr<DeepState<Cnt>> sp(new DeepState<Cnt>());
   std::unique_ptr<ShalState<Cnt>> tp(new ShalState<Cnt>());
@@ -1353,17 +1429,21 @@ int oracle_count_ops_by_pass(int n_cols, int pver, int ld, const double* hyai,
       if (c == I_CONS) plume_pass[C_NCAT + c] += deep_isl[c];
       else trigger_pass[C_NCAT + c] += deep_isl[c];
     }
+    // the deep-updated state the shallow scheme reads: counted with it
+    for (int c = 0; c < C_NCAT; ++c) g_count[c] = g_lfc0[c] = g_lfc1[c] = 0.0;
+    for (int c = 0; c < I_NCAT; ++c) g_island[c] = 0.0;
     for (int k = 0; k < pver; ++k) {
       T2[k] = Tc[k] + dt * s.dTdt[k].v;
       q2[k] = qc[k] + dt * s.dqdt[k].v;
       if (!s.bad && q2[k].v < 0.0) q2[k] = Cnt(0.0);
     }
-    for (int c = 0; c < C_NCAT; ++c) g_count[c] = 0.0;
-    for (int c = 0; c < I_NCAT; ++c) g_island[c] = 0.0;
     shallow_column<Cnt>(pver, hyai, hybi, p0, T2, q2, Cnt(ps[i]), SP, *tp);
     double* dst = trig ? plume_pass : trigger_pass;
     for (int c = 0; c < C_NCAT; ++c) dst[c] += g_count[c];
     for (int c = 0; c < I_NCAT; ++c) dst[C_NCAT + c] += g_island[c];
+    // the LFC search of a trigger-pass column that ends at exit E2
+    if (e2_search && !trig && tp->exit_code == 2)
+      for (int c = 0; c < C_NCAT; ++c) e2_search[c] += g_lfc1[c] - g_lfc0[c];
     ntrig += trig ? 1.0 : 0.0;
   }
   if (n_triggered) *n_triggered = ntrig;

@@ -64,7 +64,8 @@ double oracle_qs(double T, double p);
 double oracle_dqsdT(double T, double p);
 /* LCL by Newton on the vapour-pressure form; returns last |dT| step. */
 double oracle_lcl(double Tb, double qb, double pb, int n_newton, double* TL, double* pL);
-/* Moist-static-energy inversion: T with cp T + gz + Lv qs(T,p) = h, 1+n_extra Newton steps. */
+/* Moist-static-energy inversion: T with cp T + gz + Lv qs(T,p) = h by Newton from T_start,
+ * stopping after the first correction below 1e-7 K, at most 1+n_extra steps. */
 double oracle_hinv(double h, double gz, double p, double T_start, int n_extra, double* last_step);
 /* Hypsometric heights of one column (arrays of this column only). */
 void oracle_heights(int pver, const double* T, const double* q, const double* p_int,
@@ -158,22 +159,37 @@ int oracle_deep_shallow_tracers(int n_cols, int pver, int ld, const double* hyai
                                 double* tend_shallow, const oracle_flux* flux_deep,
                                 const oracle_flux* flux_shallow, int n_threads);
 
+/* Floating-point operation counts of the fused deep -> shallow step, summed over
+ * the columns, by category (add/sub, mul, div, exp, log, pow, sqrt, unused):
+ * the deep scheme alone and the whole step.  Default lambda and tau. */
 int oracle_count_ops(int n_cols, int pver, int ld, const double* hyai, const double* hybi,
                      double p0, const double* T, const double* q, const double* ps,
                      const oracle_deep_params* dpar, const oracle_shallow_params* spar,
                      double dt, double* counts_deep, double* counts_total);
 
+/* The fused step computed by the counting instantiation (default lambda and
+ * tau, serial): its outputs must equal oracle_deep_shallow's bit for bit. */
+int oracle_deep_shallow_counted(int n_cols, int pver, int ld, const double* hyai,
+                                const double* hybi, double p0, const double* T, const double* q,
+                                const double* ps, const oracle_deep_params* dpar,
+                                const oracle_shallow_params* spar, double dt,
+                                const oracle_out* deep, const oracle_out* shallow);
+
 /* The same counts split by the two passes of a compacted GPU implementation:
  * trigger_pass = deep trigger stage of every column + the shallow scheme of the
  * columns that do not trigger; plume_pass = the rest of the deep scheme and the
- * shallow scheme of the triggered columns.  Each array has 12 entries: the 8
+ * shallow scheme of the triggered columns.  Each array has 13 entries: the 8
  * operation categories, then FP64-island tallies of the mixed-precision design:
- * [8] LCL solves, [9] CAPE terms, [10] CIN terms, [11] conservation-sum terms. */
+ * [8] LCL solves, [9] CAPE terms, [10] CIN terms, [11] conservation-sum terms,
+ * [12] saturated shallow plume layers with rain within 1e-4 kg/kg of zero.
+ * e2_search (8 entries, may be NULL): the operations of the shallow scheme's
+ * undilute-parcel LFC search in trigger-pass columns that end at exit E2 (part
+ * of trigger_pass; work an implementation may settle by bounds). */
 int oracle_count_ops_by_pass(int n_cols, int pver, int ld, const double* hyai,
                              const double* hybi, double p0, const double* T, const double* q,
                              const double* ps, const oracle_deep_params* dpar,
                              const oracle_shallow_params* spar, double dt, double* trigger_pass,
-                             double* plume_pass, double* n_triggered);
+                             double* plume_pass, double* n_triggered, double* e2_search);
 
 #ifdef __cplusplus
 }

@@ -54,7 +54,7 @@ class ShallowParams(C.Structure):
 def deep_params(**kw) -> DeepParams:
     d = dict(capelmt=70.0, lambda_default=1e-3, tau_default=3600.0, c0=2e-3, alpha_dd=0.2,
              p_launch_min=60000.0, p_top_lim=4000.0, q_min=1e-12, ent_zscale=1000.0,
-             n_newton_lcl=6, n_newton_h=4, n_plumes=1, reserved=0, plume_spread=4.0)
+             n_newton_lcl=6, n_newton_h=15, n_plumes=1, reserved=0, plume_spread=4.0)
     d.update(kw)
     return DeepParams(**d)
 
@@ -62,7 +62,7 @@ def deep_params(**kw) -> DeepParams:
 def shallow_params(**kw) -> ShallowParams:
     d = dict(eps_s=2e-3, tke=1.0, c_m=0.03, cin_scale=10.0, cin_max=50.0, a_w=1.0, b_w=2.0,
              ql_crit=1e-3, p_lcl_min=70000.0, p_lfc_min=50000.0, p_top_lim=4000.0,
-             n_newton_lcl=6, n_newton_h=4, evap_k=0.0)
+             n_newton_lcl=6, n_newton_h=15, evap_k=0.0)
     d.update(kw)
     return ShallowParams(**d)
 
@@ -153,9 +153,12 @@ def lib():
         L.oracle_count_ops.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                        C.POINTER(ShallowParams), d, p, p]
         L.oracle_count_ops_by_pass.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
-                                               C.POINTER(ShallowParams), d, p, p, p]
+                                               C.POINTER(ShallowParams), d, p, p, p, p]
+        L.oracle_deep_shallow_counted.argtypes = [i, i, i, p, p, d, p, p, p,
+                                                  C.POINTER(DeepParams), C.POINTER(ShallowParams),
+                                                  d, C.POINTER(Out), C.POINTER(Out)]
         for fn in ("oracle_deep", "oracle_shallow", "oracle_deep_shallow", "oracle_deep_adjoint",
-                   "oracle_deep_shallow_tracers",
+                   "oracle_deep_shallow_tracers", "oracle_deep_shallow_counted",
                    "oracle_deep_shallow_adjoint", "oracle_count_ops", "oracle_count_ops_by_pass"):
             getattr(L, fn).restype = i
         _lib = L
@@ -357,19 +360,37 @@ def count_ops(g, dpar=None, spar=None, dt=None):
     return cd, ct
 
 
-def count_ops_by_pass(g, dpar=None, spar=None, dt=None):
-    """(trigger_pass[12], plume_pass[12], n_triggered) summed over g's columns."""
+def count_ops_by_pass(g, dpar=None, spar=None, dt=None, e2=False):
+    """(trigger_pass[13], plume_pass[13], n_triggered) summed over g's columns;
+    with e2=True also the E2 LFC-search operations (8 categories)."""
     dpar = dpar or deep_params()
     spar = spar or shallow_params()
     dt = g.dt if dt is None else dt
     T, q, ps = _c64(g.T), _c64(g.q), _c64(g.ps)
-    a, b, nt = np.zeros(12), np.zeros(12), np.zeros(1)
+    a, b, nt, e = np.zeros(13), np.zeros(13), np.zeros(1), np.zeros(8)
     hyai, hybi = _c64(g.hyai), _c64(g.hybi)
     rc = lib().oracle_count_ops_by_pass(g.n_cols, g.pver, g.n_cols, _ptr(hyai), _ptr(hybi), 1e5,
                                         _ptr(T), _ptr(q), _ptr(ps), C.byref(dpar), C.byref(spar),
-                                        dt, _ptr(a), _ptr(b), _ptr(nt))
+                                        dt, _ptr(a), _ptr(b), _ptr(nt), _ptr(e))
     assert rc == 0
-    return a, b, float(nt[0])
+    return (a, b, float(nt[0]), e) if e2 else (a, b, float(nt[0]))
+
+
+def deep_shallow_counted(g, dpar=None, spar=None, dt=None):
+    """The fused step through the counting instantiation (default lambda, tau):
+    (deep, shallow) output dicts as deep_shallow returns them."""
+    dpar = dpar or deep_params()
+    spar = spar or shallow_params()
+    dt = g.dt if dt is None else dt
+    n, pver = g.n_cols, g.pver
+    T, q, ps = _c64(g.T), _c64(g.q), _c64(g.ps)
+    hyai, hybi = _c64(g.hyai), _c64(g.hybi)
+    od, os_ = new_out(pver, n), new_out(pver, n)
+    rc = lib().oracle_deep_shallow_counted(n, pver, n, _ptr(hyai), _ptr(hybi), 1e5, _ptr(T),
+                                           _ptr(q), _ptr(ps), C.byref(dpar), C.byref(spar), dt,
+                                           C.byref(_out_struct(od)), C.byref(_out_struct(os_)))
+    assert rc == 0
+    return od, os_
 
 
 def deep_column_diag(pver, hyai, hybi, T, q, ps, lam=1e-3, tau=3600.0, par=None, dt=1800.0):
@@ -410,7 +431,7 @@ def lcl(Tb, qb, pb, n_newton=6):
     return TL.value, pL.value, last
 
 
-def hinv(h, gz, p, T_start, n_extra=4):
+def hinv(h, gz, p, T_start, n_extra=15):
     last = C.c_double()
     T = lib().oracle_hinv(float(h), float(gz), float(p), float(T_start), n_extra, C.byref(last))
     return T, last.value

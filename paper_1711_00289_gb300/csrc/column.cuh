@@ -2,8 +2,9 @@
 //
 // Device code only; included by the kernel translation units.  Every routine is
 // a template over the working precision R:
-//   R = double  the FP64 path: every operation FP64, every Newton solve with the
-//               fixed iteration counts of the scheme definition;
+//   R = double  the FP64 path: every operation FP64, every Newton solve as the
+//               scheme defines it (fixed LCL count; moist inversions stop on a
+//               1e-7 K convergence test);
 //   R = float   the mixed path: bulk FP32 with FP64 islands for the LCL Newton
 //               iteration (FP32 iterations, then one FP64 Newton correction with
 //               an FP64 residual), the CAPE integral that drives the trigger and
@@ -19,7 +20,8 @@
 //  * es      Bolton (1980) eq. 10, qs = eps es/max(p - (1-eps) es, 1e-3 p);
 //  * LCL     root of ln es(T) - ln e_b - (cp/Rd) ln(T/T_b), Newton from Bolton eq. 22;
 //  * parcel  dry adiabat below the LCL layer, saturated MSE conservation above,
-//            inverted by Newton (first step from the environment, then n_h);
+//            inverted by Newton from the environment temperature until a
+//            correction falls below 1e-7 K (at most 1 + n_h steps);
 //  * CAPE    sum of Rd (Tv_p - Tv) dln p from the LCL layer up to the highest
 //            positively buoyant layer; trigger CAPE > capelmt;
 //  * updraft eta = (1 + dz/z_e)^(lambda z_e); MSE and total water mixed per unit
@@ -94,7 +96,10 @@ template <class R>
 struct Mth;
 // newton_tol (K): a Newton solve whose remaining error exceeds it sets
 // CONV_FLAG_NEWTON.  FP64: the remaining error is taken as the last correction
-// (the scheme's fixed step counts leave it at ~1e-12 K).  Mixed: the error the
+// (below cold_stop = 1e-7 K once the convergence test has ended the loop).
+// cold_stop (K): a solve started from the environment stops after the first
+// correction below it -- FP64: the scheme's convergence test; mixed: the same
+// 0.01 K stop as the warm-started solves.  Mixed: the error the
 // last step leaves, kNewtonQuad * (last correction)^2 by quadratic convergence
 // -- the last correction itself measures the error before that step; in FP32
 // a converged residual cp T + gz + Lv qs - h still carries ~0.05 J/kg of
@@ -104,6 +109,7 @@ struct Mth<double> {
   static constexpr bool warm = false;
   static constexpr bool anomaly = false;
   static constexpr float newton_tol = 1e-4f;
+  static constexpr double cold_stop = 1e-7;
   static __device__ __forceinline__ float left(double step) { return (float)fabs(step); }
   static __device__ __forceinline__ double es(double x) { return exp(x); }
   static __device__ __forceinline__ double ex(double x) { return exp(x); }
@@ -117,6 +123,7 @@ struct Mth<float> {
   static constexpr bool warm = true;
   static constexpr bool anomaly = true;
   static constexpr float newton_tol = 1e-3f;
+  static constexpr double cold_stop = kWarmStop;
   static __device__ __forceinline__ float left(float step) { return kNewtonQuad * step * step; }
   static __device__ __forceinline__ float es(float x) { return expf(x); }
   static __device__ __forceinline__ float ex(float x) { return __expf(x); }
@@ -171,9 +178,11 @@ __device__ __forceinline__ R sat_qs(R T, R p) {
 }
 
 // Saturated MSE inversion, cp T + gz + Lv qs(T,p) = h.  A solve either starts
-// from the environment temperature with 1 + n_h Newton steps (the scheme
-// definition; always in FP64), or -- mixed path, later levels of a vertical
-// sequence -- from the tangent prediction off the previous level's solution
+// from the environment temperature and takes Newton steps until a correction
+// falls below Mth::cold_stop, at most 1 + n_h of them (the scheme definition,
+// whose loops test convergence for termination; always in FP64), or -- mixed
+// path, later levels of a vertical sequence -- from the tangent prediction off
+// the previous level's solution
 //   dT = (dh - d(gz) + Lv qs dp/D) / (cp + Lv dqs/dT)
 // followed by up to kWarmSteps Newton steps (fewer once a correction falls
 // below kWarmStop).  Tracks the largest remaining error
@@ -208,7 +217,7 @@ __device__ __forceinline__ R moist_invert(R h, R gz, R p, R T_env, int n_h, Mois
     const R fp = R(CP) + R(LV) * dqs;
     step = Mth<R>::dv(f, fp);
     T -= step;
-    if (warm && Mth<R>::ab(step) < R(kWarmStop)) break;
+    if (Mth<R>::ab(step) < (warm ? R(kWarmStop) : R(Mth<R>::cold_stop))) break;
   }
   s.have = true;
   s.T = T;
@@ -1282,6 +1291,25 @@ __device__ __forceinline__ bool certainly_no_lfc(const Column<R>& c, const DeepB
   return true;
 }
 
+// Mixed path, FP64 island for shallow rain near the autoconversion threshold.
+// The rain of a saturated plume layer, qt - qs(T_sat) - ql_crit, is a small
+// difference of quantities near ql_crit where the plume barely exceeds the
+// threshold ("drizzle"); there the FP32 saturation temperature's residual
+// rounding (~5e-5 K, i.e. ~5e-8 kg/kg of qs) would be a large part of the rain.
+// Where the FP32 rain lies within kDrizzleBand of zero, one FP64 Newton
+// correction of T_sat with an FP64 residual, and qs at the corrected
+// temperature in FP64, give the rain to the rounding of the FP32 plume state.
+constexpr float kDrizzleBand = 1e-4f;  // kg/kg
+__device__ __forceinline__ float drizzle_fp64(float hu, float gz, float pm, float Tsat, float qt,
+                                              float qlc, float Tref, float qref) {
+  const double p = pm, T0 = Tsat;
+  double qs, dqs, rD;
+  sat_qs_dqs<double>(T0, p, qs, dqs, rD);
+  const double f = CP * (T0 - (double)Tref) + (double)gz + LV * (qs - (double)qref) - (double)hu;
+  const double T = T0 - f / (CP + LV * dqs);
+  return (float)((double)qt - sat_qs<double>(T, p) - (double)qlc);
+}
+
 // Intermediate state of shallow_column, recorded only for the adjoint kernel.
 template <class R>
 struct ShalTape {
@@ -1496,6 +1524,9 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
             break;
           }
           R r = qt - qv - qlc;
+          if constexpr (sizeof(R) == 4)
+            if (qt >= qsu && fabsf(r) < kDrizzleBand)
+              r = drizzle_fp64(hu, gz, pm, Tsat, qt, qlc, c.Tref, c.qref);
           if (r < R(0)) r = R(0);
           if constexpr (TP::kOn) {
             tape->r[k] = r;

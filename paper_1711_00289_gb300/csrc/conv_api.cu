@@ -177,7 +177,7 @@ void conv_deep_defaults(conv_deep_params* p) {
   p->q_min = 1e-12;
   p->ent_zscale = 1000.0;
   p->n_newton_lcl = 6;
-  p->n_newton_h = 4;
+  p->n_newton_h = 15;
   p->n_plumes = 1;
   p->reserved = 0;
   p->plume_spread = 4.0;
@@ -197,7 +197,7 @@ void conv_shallow_defaults(conv_shallow_params* p) {
   p->p_lfc_min = 50000.0;
   p->p_top_lim = 4000.0;
   p->n_newton_lcl = 6;
-  p->n_newton_h = 4;
+  p->n_newton_h = 15;
   p->evap_k = 0.0;
 }
 

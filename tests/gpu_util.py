@@ -137,11 +137,26 @@ def mixed_report(got, ref, m, upstream_same=None, p_surface=None):
         out[k + "_colint_max"] = float(e.max()) if e.size else 0.0
     pr = ref["prec"]
     ps_ = pr if p_surface is None else p_surface
-    nz = ps_[ps_ > 0]
-    floor = 1e-3 * (np.median(nz) if nz.size else 1.0)
-    e = (np.abs(got["prec"] - pr) / np.maximum(pr, floor))[act]
-    out["prec_max"] = float(e.max()) if e.size else 0.0
+    for key, src in (("prec_max", ps_), ("prec_max_own", pr)):
+        nz = src[src > 0]
+        floor = 1e-3 * (np.median(nz) if nz.size else 1.0)
+        e = (np.abs(got["prec"] - pr) / np.maximum(pr, floor))[act]
+        out[key] = float(e.max()) if e.size else 0.0
     return out
+
+
+def check_mixed(r, tag="", mismatch=1e-3):
+    """The mixed path's error budget against the FP64 oracle (a mixed_report):
+    trigger flips on at most 0.1% of the columns; decision mismatches of any
+    kind (level indices, exit codes, flag bits) on at most `mismatch` of them;
+    on the columns whose decisions agree, tendency column integrals within 1e-4
+    and precipitation within 1e-3 (prec_max: against the floor of 1e-3 x the
+    median nonzero surface precipitation; prec_max_own, the floor from the
+    scheme's own median, is reported beside it)."""
+    assert r["trigger_flips"] <= 1e-3 * r["n"], f"{tag} {r}"
+    assert r["decision_mismatch"] <= mismatch * r["n"], f"{tag} {r}"
+    assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
+    assert r["prec_max"] <= 1e-3, f"{tag} {r}"
 
 
 def layer_mass(g):

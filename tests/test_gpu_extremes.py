@@ -1,7 +1,7 @@
 """Parity on physically extreme columns, where the rarely taken branches run:
 very dry air (no LCL in reach), saturated and supersaturated low levels (the
 LCL at the launch point, the q_s clamp), columns 30 K colder than the grid
-(Newton solves that stop short of convergence), mountain surface pressures of
+(moist inversions started far from their roots), mountain surface pressures of
 500-900 hPa, hot, moist columns, and superadiabatic surface layers (a dry-lifted
 parcel buoyant below its LCL, where the shallow LFC must not be placed).  With
 rain evaporation switched on, the (super)saturated low levels are layers the
@@ -13,7 +13,8 @@ import numpy as np
 import pytest
 
 from paper_1711_00289_gb300 import soundings as S
-from tests.gpu_util import THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu
+from tests.gpu_util import (THREADS, assert_fp64_parity, check_mixed, layer_mass, mixed_report,
+                            run_gpu)
 
 pytestmark = pytest.mark.gpu
 
@@ -52,7 +53,9 @@ def extremes(oracle):
 def test_fp64(oracle, extremes, path):
     g = extremes
     rd, rs = oracle.deep_shallow(g, threads=THREADS)
-    assert ((rd["flags"] & 8) > 0).sum() > 50  # unconverged solves are among them
+    # the cold columns' solves start far from their roots; the convergence test
+    # still ends every one of them converged
+    assert not ((rd["flags"] | rs["flags"]) & 8).any()
     gd, gs = run_gpu(g, "fp64", path, ld=S.pad_ld(g.n_cols) + 32)
     assert_fp64_parity(gd, rd, what=f"deep {path}")
     assert_fp64_parity(gs, rs, what=f"shallow {path}")
@@ -99,9 +102,7 @@ def _mixed_check(g, gd, gs, rd, rs):
     psurf = rd["prec"] + rs["prec"]
     for tag, got, ref, up in (("deep", gd, rd, None), ("shallow", gs, rs, deep_same)):
         r = mixed_report(got, ref, m, up, psurf)
-        assert r["decision_mismatch"] <= 3e-3 * r["n"], f"{tag} {r}"
-        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
-        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
+        check_mixed(r, tag, 3e-3)
 
 
 def test_mixed(oracle, extremes):

@@ -3,29 +3,24 @@ dry layers, surface pressures of 600-1040 hPa, random entrainment rates and
 closure times).
 
 FP64 against the oracle on both paths: decisions bit-exact, values within
-1e-10 (the FP64 kernels follow the oracle's fixed Newton iteration counts).
+1e-10.  On these columns a parcel can lie 10-50 K from the environment
+temperature its moist inversion starts from; the inversions test convergence
+for termination, so every solve of both sides converges.
 
-The mixed path against a converged reference.  With the default iteration
-counts the oracle's cold-started moist inversions stop short of convergence in
-161 of the 1,787 columns the deep scheme acts on (with CAPE of 5,500-26,000
-J/kg the parcel lies far from the environment temperature they start from); the
-mixed path's warm-started solves do converge there, so the default oracle is
-not the solution to measure it against.  The same equations solved with 8 Newton steps
-leave no solve unconverged, and against them the mixed path's tendencies are
-within the budget.  Its precipitation is not yet: two columns of trace drizzle
-(rain 1.5 times the precipitation floor, from a condensate 1.1e-5 kg/kg above
-the autoconversion threshold, which FP32 resolves to ~1e-8 kg/kg) are off by
-1.4e-3, an expected failure."""
+The mixed path against the same default oracle, within its full budget:
+trigger flips and decision mismatches on at most 0.1% of the columns, tendency
+column integrals within 1e-4 and precipitation within 1e-3 where decisions
+agree.  Trace drizzle -- a shallow plume barely above the autoconversion
+threshold -- is where FP32 rounding of the saturation temperature would be a
+large part of the rain; the mixed path refines it in FP64 there."""
 import pytest
 
 from paper_1711_00289_gb300 import soundings as S
-from tests.gpu_util import (THREADS, assert_fp64_parity, layer_mass, mixed_report, run_gpu,
-                            same_decisions)
+from tests.gpu_util import (THREADS, assert_fp64_parity, check_mixed, layer_mass, mixed_report,
+                            run_gpu, same_decisions)
 from tests.test_oracle_random import _random_columns
 
 pytestmark = pytest.mark.gpu
-
-NEWTON_CONVERGED = 8
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -41,38 +36,34 @@ def grid():
 
 
 @pytest.fixture(scope="module")
-def mixed_vs_converged(oracle, grid):
-    rd, rs = oracle.deep_shallow(grid, dpar=oracle.deep_params(n_newton_h=NEWTON_CONVERGED),
-                                 spar=oracle.shallow_params(n_newton_h=NEWTON_CONVERGED),
-                                 threads=THREADS)
+def reference(oracle, grid):
+    rd, rs = oracle.deep_shallow(grid, threads=THREADS)
     assert not ((rd["flags"] | rs["flags"]) & 8).any()  # every reference solve converged
+    return rd, rs
+
+
+@pytest.fixture(scope="module")
+def mixed(reference, grid):
+    rd, rs = reference
     gd, gs = run_gpu(grid, "mixed", "compact")
-    for o in (rd, rs, gd, gs):
-        o["flags"] = o["flags"] & ~8
     m = layer_mass(grid)
     psurf = rd["prec"] + rs["prec"]
-    return {tag: mixed_report(got, ref, m, up, psurf)
-            for tag, got, ref, up in (("deep", gd, rd, None),
-                                      ("shallow", gs, rs, same_decisions(gd, rd)))}
+    rep = {tag: mixed_report(got, ref, m, up, psurf)
+           for tag, got, ref, up in (("deep", gd, rd, None),
+                                     ("shallow", gs, rs, same_decisions(gd, rd)))}
+    print(rep)
+    return rep
 
 
 @pytest.mark.parametrize("path", ["plain", "compact"])
-def test_fp64(oracle, grid, path):
-    rd, rs = oracle.deep_shallow(grid, threads=THREADS)
+def test_fp64(reference, grid, path):
+    rd, rs = reference
     gd, gs = run_gpu(grid, "fp64", path, ld=S.pad_ld(grid.n_cols) + 32)
     assert_fp64_parity(gd, rd, what=f"deep {path}")
     assert_fp64_parity(gs, rs, what=f"shallow {path}")
 
 
-def test_mixed_tendencies(mixed_vs_converged):
-    for tag, r in mixed_vs_converged.items():
+def test_mixed_budget(mixed):
+    for tag, r in mixed.items():
         assert r["active"] > 300, f"{tag} {r}"
-        assert r["decision_mismatch"] <= 3e-3 * r["n"], f"{tag} {r}"
-        assert r["dTdt_colint_max"] <= 1e-4 and r["dqdt_colint_max"] <= 1e-4, f"{tag} {r}"
-
-
-@pytest.mark.xfail(strict=False, reason="two trace-drizzle columns off by 1.4e-3: FP32 "
-                   "resolution of a condensate just above the autoconversion threshold")
-def test_mixed_precipitation(mixed_vs_converged):
-    for tag, r in mixed_vs_converged.items():
-        assert r["prec_max"] <= 1e-3, f"{tag} {r}"
+        check_mixed(r, tag)

@@ -109,6 +109,28 @@ def test_moist_inversion_against_bisection(oracle, h_off, p, Tenv):
     T, last = oracle.hinv(h, gz, p, Tenv)
     assert T == pytest.approx(P.saturated_temperature(oracle, h, gz, p), abs=1e-9)
     assert abs(P.CP * T + gz + P.LV * oracle.qs(T, p) - h) < 1e-8 * h
+    assert last < 1e-7  # the loop ended on its convergence test
+
+
+@pytest.mark.parametrize("dT", [-40.0, -15.0, 20.0, 45.0])
+def test_moist_inversion_far_start_converges(oracle, dT):
+    """A start 15-45 K from the root (a parcel far warmer or colder than the
+    environment): the convergence-tested loop reaches the bisection root, while
+    a fixed 1 + 1 steps does not; a cap of 0 extra steps takes exactly one
+    Newton step from the start."""
+    p, gz = 50000.0, 5.5e4
+    Tsol = 262.0
+    h = P.CP * Tsol + gz + P.LV * oracle.qs(Tsol, p)
+    T, last = oracle.hinv(h, gz, p, Tsol + dT)
+    assert T == pytest.approx(P.saturated_temperature(oracle, h, gz, p), abs=1e-9)
+    assert last < 1e-7
+    T1, last1 = oracle.hinv(h, gz, p, Tsol + dT, n_extra=1)
+    assert abs(T1 - Tsol) > 1e-3 and last1 > 1e-4
+    T0, _ = oracle.hinv(h, gz, p, Tsol + dT, n_extra=0)
+    T00 = Tsol + dT
+    qs = oracle.qs(T00, p)
+    f = P.CP * T00 + gz + P.LV * qs - h
+    assert T0 == pytest.approx(T00 - f / (P.CP + P.LV * oracle.dqsdT(T00, p)), rel=1e-14)
 
 
 # ---------------------------------------------------------------- deep scheme
