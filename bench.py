@@ -57,6 +57,8 @@ def parse():
                    help="skip the multi-step driver measurement")
     p.add_argument("--no-adjoint", action="store_true",
                    help="skip the deep-adjoint timing")
+    p.add_argument("--no-sweep", action="store_true",
+                   help="skip the 10/30/60%% convecting-fraction sweep")
     p.add_argument("--no-ensemble", action="store_true",
                    help="skip the batched 64-member ensemble measurement")
     return p.parse_args()
@@ -151,13 +153,17 @@ def t_ops(c, r, pfx):
 # humidity and LCL pressure): 1 log, 1 exp, 4 div, 27 FMA.  It runs only for LCL
 # solves whose FP32 pressure lies within the decision band of a layer or of the
 # E1 threshold (fp64_lcl_corrections, counted from the oracle's LCL pressures by
-# oracle/count_ops.py).  The CAPE, CIN and conservation sums keep FP64 accuracy
-# as compensated FP32 sums; their terms are FP32 work, already in the oracle's
-# operation counts (one add per term; the compensation's extra adds are not
-# counted as work).
+# oracle/count_ops.py).  One FP64 drizzle correction (q_s and dq_s/dT at the FP32
+# saturation temperature, one Newton correction, q_s at the result): 2 exp,
+# 6 div, 24 FMA, on the saturated shallow plume layers whose rain lies within
+# 1e-4 kg/kg of zero (fp64_drizzle).  The CAPE, CIN and conservation sums keep
+# their accuracy as compensated FP32 sums; their terms are FP32 work, already in
+# the oracle's operation counts (one add per term; the compensation's extra adds
+# are not counted as work).
 def t_fp64_islands(c, r):
     lcl = (1 / r["fp64_log"] + 1 / r["fp64_exp"] + 4 / r["fp64_div"] + 27 / r["fp64_fma"])
-    return c["fp64_lcl_corrections"] * lcl
+    drizzle = 2 / r["fp64_exp"] + 6 / r["fp64_div"] + 24 / r["fp64_fma"]
+    return c["fp64_lcl_corrections"] * lcl + c.get("fp64_drizzle", 0.0) * drizzle
 
 
 # Nominal ALU peaks from unit counts and clocks: 152 SMs at the 2070 MHz maximum
@@ -197,7 +203,7 @@ def kernel_roofline(counts, precision, kernel_s, n_cols, r):
             "frac": achieved / peak, "peak_measured": measured / 1e12,
             "frac_of_measured": t_bound / kernel_s,
             "t_bound_fp64_ms": t64 * 1e3, "t_bound_fp32_ms": t32 * 1e3,
-            "kernel_ms": kernel_s * 1e3, "traffic": None,
+            "t_bound_ms": t_bound * 1e3, "kernel_ms": kernel_s * 1e3, "traffic": None,
             "peak_source": (f"{SMS} SMs x {FMA_PER_SM_CLOCK[pipe]} {pipe.upper()} FMA per "
                             f"clock x 2 FLOP x {SM_MHZ:.0f} MHz (unit counts and maximum SM "
                             "clock); peak_measured: this device's FMA rate "
@@ -207,6 +213,52 @@ def kernel_roofline(counts, precision, kernel_s, n_cols, r):
 def hbm_bytes_per_column(pver, real_bytes):
     # read T, q, ps; write deep and shallow dTdt, dqdt; 4 doubles + 5 int32 per scheme
     return 2 * pver * real_bytes + 8 + 4 * pver * real_bytes + 2 * (4 * 8 + 5 * 4)
+
+
+OP_CATS = ("add", "mul", "div", "exp", "log", "pow", "sqrt")
+
+
+def path_rooflines(counts, prec, path, kern_ms, n, r):
+    """Per-kernel arithmetic rooflines of one measured step.  Plain path: one
+    kernel doing the whole step.  Compacted path: the trigger pass (all columns)
+    and the plume pass (queued columns).  The trigger pass's headline work leaves
+    out the shallow LFC search of the columns that end at exit E2, which the
+    kernel settles by bounds instead (trigger_pass_e2_search_per_column); the
+    figure with that search counted is reported beside it."""
+    kernels = {}
+    if path == "plain":
+        tot = {c: counts["trigger_pass_per_column"][c] + counts["plume_pass_per_column"][c]
+               for c in counts["trigger_pass_per_column"]}
+        if prec == "fp64":
+            tot.update(counts["total_per_column"])
+        kernels["k_plain"] = kernel_roofline(tot, prec, kern_ms[0] * 1e-3, n, r)
+        kernels["k_plain"]["share"] = 1.0
+        return kernels
+    kt, kp = kern_ms
+    trig = dict(counts["trigger_pass_per_column"])
+    e2 = counts.get("trigger_pass_e2_search_per_column", {})
+    net = {c: (trig[c] - e2.get(c, 0.0)) if c in OP_CATS else trig[c] for c in trig}
+    kernels["k_trigger"] = kernel_roofline(net, prec, kt * 1e-3, n, r)
+    gross = kernel_roofline(trig, prec, kt * 1e-3, n, r)
+    kernels["k_trigger"]["with_e2_search_counted"] = {
+        k: gross[k] for k in ("frac", "frac_of_measured", "t_bound_ms")}
+    kernels["k_plume"] = kernel_roofline(counts["plume_pass_per_column"], prec, kp * 1e-3, n, r)
+    kernels["k_trigger"]["share"] = kt / (kt + kp)
+    kernels["k_plume"]["share"] = kp / (kt + kp)
+    return kernels
+
+
+def step_roofline(kernels, step_ms):
+    """The whole step against the same arithmetic roofline: the kernels' bound
+    times summed, over the measured step time (gaps and small launches between
+    the kernels included)."""
+    t_bound = sum(k["t_bound_ms"] for k in kernels.values())
+    achieved_nominal = sum(k["t_bound_ms"] * k["peak_measured"] / k["peak"]
+                           for k in kernels.values()) / step_ms
+    return {"t_bound_ms": t_bound, "step_ms": step_ms, "frac_of_measured": t_bound / step_ms,
+            "frac": achieved_nominal,
+            "note": "sum of the kernels' bound times at measured rates / step time "
+                    "(frac: the same at nominal FMA peaks)"}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -313,28 +365,32 @@ def ours_arm(args, rank, world, local_rank):
     ws = api.Workspace(dev)
     bufs = {}
 
-    def setup(prec):
-        if prec not in bufs:
+    def setup(grid, prec):
+        key = (grid.name, prec)
+        if key not in bufs:
             rd = api.real_dtype(prec)
-            bufs[prec] = (torch.tensor(g.T, device=dev).to(rd), torch.tensor(g.q, device=dev).to(rd),
-                          torch.tensor(g.ps, device=dev), api.new_outputs(pver, n, prec, dev),
-                          api.new_outputs(pver, n, prec, dev))
-        return bufs[prec]
+            bufs[key] = (torch.tensor(grid.T, device=dev).to(rd),
+                         torch.tensor(grid.q, device=dev).to(rd),
+                         torch.tensor(grid.ps, device=dev),
+                         api.new_outputs(grid.pver, grid.n_cols, prec, dev),
+                         api.new_outputs(grid.pver, grid.n_cols, prec, dev))
+        return bufs[key]
 
     preps = {}
 
-    def prepared(prec, path):
+    def prepared(grid, prec, path):
         # the step's C-ABI arguments marshalled once (api.PreparedStep): a timed
         # step is one library call, so the loop measures the GPU, not Python
-        if (prec, path) not in preps:
-            T, q, ps, od, os_ = setup(prec)
-            preps[(prec, path)] = api.PreparedStep(T, q, ps, vg, dt=g.dt, precision=prec,
-                                                   path=path, out_deep=od, out_shallow=os_,
-                                                   workspace=ws, stream=stream)
-        return preps[(prec, path)]
+        key = (grid.name, prec, path)
+        if key not in preps:
+            T, q, ps, od, os_ = setup(grid, prec)
+            preps[key] = api.PreparedStep(T, q, ps, api.VerticalGrid(grid.hyai, grid.hybi),
+                                          dt=grid.dt, precision=prec, path=path, out_deep=od,
+                                          out_shallow=os_, workspace=ws, stream=stream)
+        return preps[key]
 
-    def timed(prec, path, steps, warmup, per_kernel):
-        run = prepared(prec, path)
+    def timed(grid, prec, path, steps, warmup, per_kernel):
+        run = prepared(grid, prec, path)
         for _ in range(warmup):
             run()
         torch.cuda.synchronize()
@@ -366,27 +422,46 @@ def ours_arm(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
-    ms, kern = timed(prec, path, args.steps, args.warmup, True)
+    ms, kern = timed(g, prec, path, args.steps, args.warmup, True)
     clk = clocks.stop()
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_value(world, n, ms)
-    od = setup(prec)[3]
+    od = setup(g, prec)[3]
     act = int(((od["flags"] & 2) > 0).sum().item())
 
     # the plain FP64 kernel, the reference point of the metric
     base = None
+    bkern = None
     if not args.no_baseline and not (prec == "fp64" and path == "plain"):
-        bms, _ = timed("fp64", "plain", max(2, min(args.steps, 5)), 2, False)
+        bms, bkern = timed(g, "fp64", "plain", max(2, min(args.steps, 5)), 2, True)
         bms = max_over_ranks(bms, world, dev)
         base = {"value": whole_job_value(world, n, bms), "unit": UNIT, "ms_per_step": bms,
                 "path": "plain", "precision": "fp64"}
+
+    # the same path at the other convecting fractions of the 884,736-column
+    # workload (each its own grid; the headline value stays at args.frac)
+    sweep = []
+    if not args.no_sweep:
+        for f in (0.10, 0.30, 0.60):
+            if abs(f - args.frac) < 1e-9:
+                sweep.append({"convecting_fraction": f, "ms_per_step": ms, "kern_ms": kern,
+                              "deep_active_columns": act, "columns": n})
+                continue
+            gf = S.clustered_grid(f, args.nlat, args.nlon)
+            msf, kf = timed(gf, prec, path, args.steps, args.warmup, True)
+            msf = max_over_ranks(msf, world, dev)
+            actf = int(((setup(gf, prec)[3]["flags"] & 2) > 0).sum().item())
+            sweep.append({"convecting_fraction": f, "ms_per_step": msf, "kern_ms": kf,
+                          "deep_active_columns": actf, "columns": gf.n_cols})
+            del bufs[(gf.name, prec)], preps[(gf.name, prec, path)]
+            torch.cuda.empty_cache()
 
     # end to end through the public API from pinned host buffers: the host
     # pipeline (conv_pipeline_run) copies the inputs in, runs the fused step and
     # copies every output back, chunk by chunk with the copies overlapping
     e2e = None
     if not args.no_e2e:
-        T, q, ps, od_, os__ = setup(prec)
+        T, q, ps, od_, os__ = setup(g, prec)
         hT, hq, hps = (x.cpu().pin_memory() for x in (T, q, ps))
         hd, hs = api.new_host_outputs(pver, n, prec), api.new_host_outputs(pver, n, prec)
         pipe = api.HostPipeline(vg, n, n, prec)
@@ -414,7 +489,8 @@ def ours_arm(args, rank, world, local_rank):
         d2h = sum(v.numel() * v.element_size() for o in (hd, hs) for v in o.values())
         e2e = {"value": whole_job_value(world, n, ms2), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms2,
-               "ms_min": min(per), "ms_max": max(per),
+               "ms_median": statistics.median(per), "ms_min": min(per), "ms_max": max(per),
+               "ms_steps": per,
                "path": "conv_pipeline_run (host buffers, chunked copies overlapping compute)"}
         pipe.close()
 
@@ -422,22 +498,7 @@ def ours_arm(args, rank, world, local_rank):
         return
     counts, key = op_counts(args.frac)
     r = device_rates(L)
-    kernels = {}
-    if path == "plain":
-        tot = {c: counts["trigger_pass_per_column"][c] + counts["plume_pass_per_column"][c]
-               for c in counts["trigger_pass_per_column"]}
-        if prec == "fp64":
-            tot.update(counts["total_per_column"])
-        kernels["k_plain"] = kernel_roofline(tot, prec, kern[0] * 1e-3, n, r)
-        kernels["k_plain"]["share"] = 1.0
-    else:
-        kt, kp = kern
-        kernels["k_trigger"] = kernel_roofline(counts["trigger_pass_per_column"], prec,
-                                               kt * 1e-3, n, r)
-        kernels["k_plume"] = kernel_roofline(counts["plume_pass_per_column"], prec, kp * 1e-3,
-                                             n, r)
-        kernels["k_trigger"]["share"] = kt / (kt + kp)
-        kernels["k_plume"]["share"] = kp / (kt + kp)
+    kernels = path_rooflines(counts, prec, path, kern, n, r)
     traffic = ncu_traffic(g.name)
     for k in kernels:
         kernels[k]["traffic"] = traffic.get(k)
@@ -445,13 +506,29 @@ def ours_arm(args, rank, world, local_rank):
     roof = dict(kernels[dom])
     roof["kernel"] = dom
     roof["op_counts_workload"] = key
+    roof["step"] = step_roofline(kernels, ms)
     rb = 8 if prec == "fp64" else 4
     roof["hbm_algorithmic_bytes_per_column"] = hbm_bytes_per_column(pver, rb)
     hbm_peak, hbm_src = measured_hbm()
     roof["hbm_frac_of_measured_path"] = (hbm_bytes_per_column(pver, rb) * n / (ms * 1e-3) / 1e9
                                          / hbm_peak)
     roof["hbm_peak_source"] = hbm_src
-    ens = None if args.no_ensemble else ensemble_bench(args, dev)
+    if base is not None:
+        bk = path_rooflines(counts, "fp64", "plain", bkern, n, r)
+        base["roofline"] = dict(bk["k_plain"], kernel="k_plain", op_counts_workload=key,
+                                step=step_roofline(bk, base["ms_per_step"]))
+        base["roofline"]["traffic"] = traffic.get("k_plain_fp64")
+    for row in sweep:
+        cf, kf_ = op_counts(row["convecting_fraction"])
+        kk = path_rooflines(cf, prec, path, row.pop("kern_ms"), row["columns"], r)
+        row["value"] = whole_job_value(world, row["columns"], row["ms_per_step"])
+        row["unit"] = UNIT
+        row["op_counts_workload"] = kf_
+        row["kernels"] = {k: {x: v[x] for x in ("kernel_ms", "frac", "frac_of_measured",
+                                                 "t_bound_ms", "binding_pipe")}
+                          for k, v in kk.items()}
+        row["step"] = step_roofline(kk, row["ms_per_step"])
+    ens = None if args.no_ensemble else ensemble_bench(args, dev, r)
     adj = None if args.no_adjoint else adjoint_bench(args, dev, g)
     trn = None if args.no_transport else transport_bench(args, dev, g)
     drv = None if args.no_driver else driver_bench(args, dev, g)
@@ -473,7 +550,8 @@ def ours_arm(args, rank, world, local_rank):
                        "l2": l2_note(prec, n, pver), "parallelism": f"replicas x{world}"},
             "baseline_fp64_plain": base,
             "speedup_vs_fp64_plain": (value / base["value"]) if base else None,
-            "roofline": roof, "kernels": kernels, "batched_ensemble": ens, "deep_adjoint": adj,
+            "roofline": roof, "kernels": kernels, "convecting_fraction_sweep": sweep,
+            "batched_ensemble": ens, "deep_adjoint": adj,
             "tracer_transport": trn, "column_driver": drv,
             "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk, "gpu_launches": (1 if path == "plain" else 2) * args.steps,
@@ -481,10 +559,13 @@ def ours_arm(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
-def ensemble_bench(args, dev):
+def ensemble_bench(args, dev, rates=None):
     """64 members, log-uniform 1,000-200,000 columns, 26/30/32 levels, member
     surface-T offsets and entrainment rates: one batched run (trigger launch +
-    persistent plume launch), autotuned, captured in a CUDA graph and replayed."""
+    persistent plume launch), autotuned, captured in a CUDA graph and replayed.
+    Its arithmetic roofline: the ensemble's counted work (oracle/op_counts.json,
+    workload ensemble-64) against the two kernels' times from eager runs with
+    stage events, and against the graph-replayed step."""
     import torch
 
     from paper_1711_00289_gb300 import api
@@ -519,7 +600,31 @@ def ensemble_bench(args, dev):
     ms = e0.elapsed_time(e1) / args.steps
     total = sum(g.n_cols for g in ens)
     active = sum(int(((o[0]["flags"] & 2) > 0).sum().item()) for o in b.outputs)
+    # per-kernel times: eager runs on the same stream with stage events
+    kev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    for e3 in kev:
+        for e in e3:
+            e.record(s)
+    torch.cuda.synchronize()
+    for e3 in kev:
+        b.run(stream=s, stage_events=e3)
+    torch.cuda.synchronize()
+    kt = statistics.mean(e[0].elapsed_time(e[1]) for e in kev)
+    kp = statistics.mean(e[1].elapsed_time(e[2]) for e in kev)
     b.close()
+    roof = None
+    if rates is not None:
+        with open(os.path.join(ROOT, "oracle", "op_counts.json")) as fh:
+            cnt = json.load(fh)["workloads"].get("ensemble-64")
+        if cnt is not None:
+            kk = path_rooflines(cnt, "mixed", "compact", (kt, kp), total, rates)
+            kk = {"k_batch_trigger": kk["k_trigger"], "k_batch_plume": kk["k_plume"]}
+            dom = max(kk, key=lambda k: kk[k]["share"])
+            roof = dict(kk[dom], kernel=dom, op_counts_workload="ensemble-64",
+                        kernels={k: {x: v[x] for x in ("kernel_ms", "frac", "frac_of_measured",
+                                                        "t_bound_ms", "share")}
+                                 for k, v in kk.items()},
+                        step=step_roofline(kk, ms))
     # the same members one after another through the single-grid compacted
     # kernels (three launches each), also replayed from a CUDA graph
     runs = []
@@ -551,7 +656,7 @@ def ensemble_bench(args, dev):
             "deep_active_columns": active, "precision": "mixed", "ms_per_step": ms,
             "value": total / (ms * 1e-3), "unit": UNIT, "launch": "CUDA graph replay",
             "autotuned_shape": cfg, "gpu_launches_per_step": 2,
-            "members_one_after_another_ms": ms_sep}
+            "members_one_after_another_ms": ms_sep, "roofline": roof}
 
 
 def adjoint_bench(args, dev, g_full):

@@ -88,3 +88,45 @@ def test_hbm_peak_source_is_named(tmp_path, monkeypatch):
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6777.0}')
     v, src = bench.measured_hbm()
     assert v == 6777.0 and "measured" in src
+
+
+def _pass_counts():
+    base = dict(add=900.0, mul=700.0, div=40.0, exp=30.0, log=20.0, pow=2.0, sqrt=0.0,
+                fp64_lcl_corrections=0.001, fp64_drizzle=0.02)
+    plume = {k: v / 3 for k, v in base.items()}
+    e2 = dict(add=100.0, mul=80.0, div=10.0, exp=5.0, log=0.0, pow=0.0, sqrt=0.0)
+    return {"trigger_pass_per_column": base, "plume_pass_per_column": plume,
+            "trigger_pass_e2_search_per_column": e2,
+            "total_per_column": {k: base[k] + plume[k] for k in bench.OP_CATS}}
+
+
+def test_trigger_pass_work_leaves_out_the_e2_search():
+    c, r, n = _pass_counts(), _rates(), 884736
+    k = bench.path_rooflines(c, "mixed", "compact", (0.5, 0.4), n, r)
+    net = {x: c["trigger_pass_per_column"][x] - c["trigger_pass_e2_search_per_column"].get(x, 0)
+           for x in bench.OP_CATS}
+    net.update(fp64_lcl_corrections=0.001, fp64_drizzle=0.02)
+    ref = bench.kernel_roofline(net, "mixed", 0.5e-3, n, r)
+    gross = bench.kernel_roofline(c["trigger_pass_per_column"], "mixed", 0.5e-3, n, r)
+    assert k["k_trigger"]["frac"] == pytest.approx(ref["frac"], rel=1e-12)
+    assert k["k_trigger"]["with_e2_search_counted"]["frac"] == pytest.approx(gross["frac"])
+    assert k["k_trigger"]["frac"] < gross["frac"]
+    assert k["k_trigger"]["share"] + k["k_plume"]["share"] == pytest.approx(1.0)
+
+
+def test_step_roofline_sums_the_kernels_bound_times():
+    c, r, n = _pass_counts(), _rates(), 884736
+    k = bench.path_rooflines(c, "mixed", "compact", (0.5, 0.4), n, r)
+    st = bench.step_roofline(k, 1.0)
+    tb = k["k_trigger"]["t_bound_ms"] + k["k_plume"]["t_bound_ms"]
+    assert st["frac_of_measured"] == pytest.approx(tb / 1.0, rel=1e-12)
+    # kernels alone (0.9 ms of the 1.0 ms step): the step's fraction is lower
+    kt = bench.step_roofline(k, 0.9)
+    assert st["frac"] == pytest.approx(kt["frac"] * 0.9, rel=1e-12)
+    assert st["frac"] == pytest.approx(st["frac_of_measured"] * 2 * 35.7 / 80.5478, rel=1e-4)
+
+
+def test_drizzle_corrections_cost_fp64_work():
+    r = _rates()
+    a = bench.t_fp64_islands(dict(fp64_lcl_corrections=0.0, fp64_drizzle=1.0), r)
+    assert a == pytest.approx(2 / r["fp64_exp"] + 6 / r["fp64_div"] + 24 / r["fp64_fma"])

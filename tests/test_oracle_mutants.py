@@ -113,11 +113,28 @@ TRANSPORT = "tests/test_oracle_transport.py"
 EVAPORATION = "tests/test_oracle_evaporation.py"
 SPECTRUM = "tests/test_oracle_spectrum.py"
 ADJOINT = "tests/test_oracle_adjoint.py"
+COUNTS = "tests/test_oracle_counts.py"
 # The forward-mode type's rules for pow and sqrt are left out: no derivative
 # that reaches an output passes through them (pow's differentiated argument is
 # the LCL pressure, which only places levels; sqrt takes a constant), so a slip
 # there changes nothing a pin could see.
 EXT_MUTANTS = {
+    # the counting instantiation (numerator of the arithmetic roofline)
+    "subtraction not counted": (
+        "inline Cnt operator-(const Cnt& a, const Cnt& b) { g_count[C_ADD] += 1; return Cnt(a.v - b.v); }",
+        "inline Cnt operator-(const Cnt& a, const Cnt& b) { return Cnt(a.v - b.v); }", COUNTS),
+    "division counted as a multiplication": (
+        "inline Cnt operator/(const Cnt& a, const Cnt& b) { g_count[C_DIV] += 1;",
+        "inline Cnt operator/(const Cnt& a, const Cnt& b) { g_count[C_MUL] += 1;", COUNTS),
+    "counted power squares its base": (
+        "g_count[C_POW] += 1; return Cnt(std::pow(a.v, e));",
+        "g_count[C_POW] += 1; return Cnt(a.v * a.v);", COUNTS),
+    "trigger-pass mark before the CAPE sum": (
+        "  s.cape = cape;\n  mark_trigger_end<R>();", "  s.cape = cape;", COUNTS),
+    "LFC-search tally from the start of the column": (
+        "  mark_lfc_search<R>(false);\n", "", COUNTS),
+    "drizzle band ten times wider": (
+        "std::fabs(val(l) - P.ql_crit) < 1e-4", "std::fabs(val(l) - P.ql_crit) < 1e-3", COUNTS),
     "tangent quotient rule sign": (
         "r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v;", "r.d[i] = (a.d[i] + r.v * b.d[i]) / b.v;",
         ADJOINT),
