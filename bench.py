@@ -782,6 +782,18 @@ def transport_bench(args, dev, g, ntr=25):
     ms = ev_time(lambda: api.tracer_transport(tr, ps, vg, deep_out=od, shallow_out=os_, dt=g.dt,
                                               precision="mixed", tend_deep=td, tend_shallow=ts),
                  reps)
+    # momentum transport of (u, v) by the same plumes (pressure-gradient
+    # coefficients 0.7): one launch, timed alone
+    k = torch.arange(pver, device=dev, dtype=torch.float32)[:, None]
+    uv = torch.stack([10.0 + 20.0 * (1 - k / pver) + 3.0 * torch.rand((pver, n), device=dev,
+                                                                     generator=gen),
+                      -5.0 + 8.0 * torch.sin(k / 4.0) + 3.0 * torch.rand((pver, n), device=dev,
+                                                                         generator=gen)])
+    ud, us = torch.empty_like(uv), torch.empty_like(uv)
+    ms_mom = ev_time(lambda: api.momentum_transport(uv, ps, vg, deep_out=od, shallow_out=os_,
+                                                    dt=g.dt, precision="mixed", cp_up=0.7,
+                                                    cp_down=0.7, tend_deep=ud, tend_shallow=us),
+                     reps)
     # algorithmic bytes of one launch
     ad = (od["flags"] & 2) > 0
     as_ = (os_["flags"] & 2) > 0
@@ -801,6 +813,13 @@ def transport_bench(args, dev, g, ntr=25):
     alg = tracer_bytes + int(per_col_prof.sum())
     achieved = alg / (ms * 1e-3) / 1e9
     peak, peak_src = measured_hbm()
+    alg_mom = 2 * (2 * pver * n * es + int(read_levels.sum()) * es) + int(per_col_prof.sum())
+    mom = {"components": 2, "cp_up": 0.7, "cp_down": 0.7, "ms_transport": ms_mom,
+           "value": n / (ms_mom * 1e-3), "unit": UNIT, "gpu_launches_per_call": 1,
+           "roofline": {"bound": "hbm", "achieved": alg_mom / (ms_mom * 1e-3) / 1e9,
+                        "peak": peak, "unit": "GB/s",
+                        "frac": alg_mom / (ms_mom * 1e-3) / 1e9 / peak,
+                        "algorithmic_bytes": alg_mom, "traffic": None, "peak_source": peak_src}}
     return {"tracers": ntr, "columns": n, "levels": pver, "precision": "mixed",
             "ms_transport": ms, "value": ntr * n / (ms * 1e-3), "unit": "tracer-columns/s",
             "ms_step_with_profiles": step_flux, "ms_step_without_profiles": step_plain,
@@ -808,7 +827,7 @@ def transport_bench(args, dev, g, ntr=25):
                                     "shallow_rain_evaporated": 1.0 - p_on / max(p_off, 1e-300)},
             "deep_plume_spectrum": {"n_plumes": 3, "plume_spread": 4.0, "ms_step": step_spec,
                                     "deep_precip_ratio": d_on / max(d_off, 1e-300)},
-            "gpu_launches_per_call": 1,
+            "gpu_launches_per_call": 1, "momentum_transport": mom,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "algorithmic_bytes": alg,
                          "traffic": ncu_traffic(g.name + "-tracers25", "transport").get(

@@ -15,7 +15,7 @@
  * implicit rain, saturated downdraft, flux-form tendencies, CAPE-relaxation
  * closure with a moisture limiter, and a CIN-closed shallow plume.
  *
- * Data layout (the paper's transposed, padded layout, Sec. III-C, turned for
+ * Data layout (the paper's transposed, padded layout, Sec. IV-C, turned for
  * a GPU: columns innermost so that a warp reads 32 adjacent columns of one
  * level in one coalesced access):
  *   profile arrays  [pver][ld], element (k, i) at k*ld + i,
@@ -378,6 +378,35 @@ conv_status conv_tracer_transport(const conv_grid* grid, const double* ps,
                                   double dt, int ntr, const void* tracers, void* tend_deep,
                                   void* tend_shallow, conv_precision prec, conv_stream stream);
 
+/* ------------------------------------------------------------------ momentum transport
+ * Convective momentum transport (a variant the cited schemes carry: the ZM and
+ * UW schemes move horizontal momentum with their plumes, Sec. II-A).  A wind
+ * component is carried like a tracer (conv_tracer_transport, same mass-flux
+ * profiles and layout), except that inside each plume the convective-scale
+ * pressure gradient pushes the plume's momentum towards the environment's
+ * (Gregory, Kershaw and Inness 1997): a plume crossing layer k from its
+ * neighbour j (the layer below for the updrafts, above for the downdraft) gains
+ *   cp * (plume flux continuing from j) * (u_k - u_j),
+ * cp = cp_up for the updrafts, cp_down for the downdraft, and the layer's
+ * environment loses the same.  Per layer this is the tracer budget above with
+ * the plumes' momenta, minus those pressure forces; equivalently the divergence
+ * of the interface eddy fluxes, so the column's momentum is conserved exactly.
+ * cp_up = cp_down = 0 is the tracer transport; at 1 a plume's momentum equals
+ * the environment's at every layer it crosses.
+ *
+ * uv: DEVICE [2][pver][ld] of the precision's type, u then v (component n at
+ * offset n*pver*ld); tend_deep / tend_shallow: the same layout (m/s2), required
+ * with their scheme's outputs; every element of the first n_cols columns is
+ * written.  With both schemes the shallow scheme transports u + dt*tend_deep
+ * (no floor: a wind component takes either sign).  cp_up, cp_down in [0, 1];
+ * the other arguments as for conv_tracer_transport.  Validation errors:
+ * CONV_ERR_ARG.  Asynchronous on `stream`; allocates nothing. */
+conv_status conv_momentum_transport(const conv_grid* grid, const double* ps,
+                                    const conv_out* deep_out, const conv_out* shallow_out,
+                                    double dt, double cp_up, double cp_down, const void* uv,
+                                    void* tend_deep, void* tend_shallow, conv_precision prec,
+                                    conv_stream stream);
+
 /* ------------------------------------------------------------------ host pipeline
  * conv_deep_shallow_run on HOST buffers (no counterpart in the paper: there the
  * data never leaves the host).  A plan splits the grid's columns into chunks of
@@ -403,7 +432,7 @@ void conv_pipeline_free(conv_pipeline* p);
  * Many grids / ensemble members of uneven column counts and level counts in one
  * trigger launch over all their columns and one persistent launch over a common
  * device queue of convecting columns (the GPU answer to the load imbalance the
- * paper meets with OpenMP dynamic scheduling, Sec. III-A).  Each member is a
+ * paper meets with OpenMP dynamic scheduling, Sec. IV-A).  Each member is a
  * complete fused deep->shallow problem with its own grid, parameters and
  * buffers; results equal those of conv_deep_shallow_run on the compacted path
  * for that member alone. */
@@ -453,6 +482,38 @@ conv_status conv_batch_config(const conv_batch* b, int32_t* trigger_block, int32
 /* Release the plan and its device descriptor table (NULL is a no-op). */
 void conv_batch_free(conv_batch* b);
 
+/* ---------------------------------------------------------------- sharding
+ * One grid's columns split over several GPUs by convective work: the GPU
+ * counterpart of the paper's proportional partitioning of the column
+ * computations between devices (Sec. IV-D).  The columns are independent, so
+ * each GPU runs the fused step on its own contiguous range (the inputs and
+ * outputs offset by the range's first column, ld unchanged) with no exchange
+ * on the data path; the ranges are chosen so that each holds about the same
+ * cost  w_all * columns + w_active * triggered columns,  the triggered columns
+ * counted from the flags of a previous run (the deep scheme's trigger varies
+ * slowly from step to step, and the plume pass only runs on those columns).
+ *
+ * conv_count_triggered: counts[j] = number of columns among j*block ..
+ * min((j+1)*block, n_cols) - 1 whose deep flags have CONV_FLAG_TRIGGERED.
+ * flags: DEVICE int32[n_cols] (a deep conv_out.flags); counts: DEVICE
+ * int32[ceil(n_cols/block)], overwritten.  Asynchronous on `stream` (one memset,
+ * one kernel); CONV_ERR_ARG for n_cols < 0, block < 1 or missing pointers.
+ *
+ * conv_partition_columns: HOST function.  block_triggered: HOST
+ * int32[ceil(n_cols/block)] (each 0 .. the block's column count), e.g. the
+ * element-wise sum of every rank's counts; w_all, w_active >= 0, not both 0.
+ * Writes bounds[0 .. n_parts] (HOST int32): bounds[0] = 0, bounds[n_parts] =
+ * n_cols, non-decreasing, every inner bound a multiple of block at the block
+ * boundary closest to r/n_parts of the total cost.  Part r is columns
+ * bounds[r] .. bounds[r+1] - 1 (possibly empty).  Deterministic: every rank
+ * given the same counts computes the same bounds.  CONV_ERR_ARG on invalid
+ * arguments (bounds untouched then). */
+conv_status conv_count_triggered(const int32_t* flags, int32_t n_cols, int32_t block,
+                                 int32_t* counts, conv_stream stream);
+conv_status conv_partition_columns(int32_t n_cols, int32_t block,
+                                   const int32_t* block_triggered, double w_all,
+                                   double w_active, int32_t n_parts, int32_t* bounds);
+
 /* Largest n_cols accepted by conv_deep_shallow_run_noalloc. */
 #define CONV_NOALLOC_MAX_COLS 65536
 
@@ -469,9 +530,11 @@ void conv_batch_free(conv_batch* b);
  *   - n_cols > CONV_NOALLOC_MAX_COLS returns CONV_ERR_ARG before anything runs;
  *     all other arguments are validated as for conv_deep_shallow_run.
  *   - The first call on a device looks up that device's address of the array
- *     (once per device, for the device current at the call); make that first
- *     call before any stream capture.  The stream must belong to the current
- *     device.
+ *     (for the device current at the call) and caches it with the identity of
+ *     the device's context; make that first call before any stream capture.
+ *     After a device reset (a new context) the next call looks the address up
+ *     again, so make that call outside a capture too.  The stream must belong
+ *     to the current device.
  *   - Every call shares the one array, which keeps the last call's contents;
  *     the queue length is reset at the start of each call.  Calls that overlap
  *     on the GPU (other streams, other host threads) race on it: serialise them.

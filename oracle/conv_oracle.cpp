@@ -286,7 +286,7 @@ void heights(int pver, const R* T, const R* q, const R* p_int, const R* p_mid, R
 // Newton inversion of moist static energy for a saturated parcel: find T with
 // cp T + g z + Lv qs(T, p) = h.  Newton from T_start (the environment); the
 // loop tests convergence for termination, as the scheme loops the paper times
-// do (Sec. V-E): it stops after the first correction smaller than H_STOP, and
+// do (Sec. V-C): it stops after the first correction smaller than H_STOP, and
 // after at most 1 + n_extra steps.  The residual is increasing and convex in T
 // with f''/2f' <= 0.1 / K, so the error left after a correction c is about
 // 0.1 c^2: below H_STOP = 1e-7 K it is ~1e-15 K, under the rounding of T.
@@ -944,6 +944,78 @@ void shallow_transport(int pver, const ShalState<double>& s, const ShalP& P, con
   for (int k = kts; k <= ks; ++k) tend[k] = dc[k] / s.m[k];
 }
 
+// ---------------------------------------------------------------- momentum transport
+// Convective momentum transport (a variant the cited schemes carry, Sec. II-A:
+// the ZM and UW schemes move horizontal momentum with their plumes).  This
+// project's reading: a wind component is carried like a tracer, except that
+// inside a plume the convective-scale pressure gradient pushes the plume's
+// momentum towards the environment's by a fraction of the environmental wind
+// change it rises (or sinks) through -- the pressure-gradient term of Gregory,
+// Kershaw and Inness (1997, Q. J. R. Meteorol. Soc. 123), with coefficients
+// c_up (updrafts) and c_down (downdraft); with both 0 this is the tracer
+// transport.  Discretely, per unit cloud-base flux: a plume crossing layer k from
+// its neighbour j (k+1 for updrafts, k-1 for the downdraft) gains
+// c (flux continuing from j) (u_k - u_j) on top of the mixing of the tracer
+// recurrence.  The environment's tendency is the divergence of the eddy fluxes
+// through the layer interfaces, with the upwind values of the tracer transport:
+//   updraft, interface k (top of layer k):  F_k = eta_k (u_u,k - u_k-1), jt < k <= kb,
+//   downdraft, interface k+1 (bottom of k): G_k+1 = alpha etad_k (u_d,k - u_k+1), jd <= k < kb,
+//   m_k du_k/dt = M_b [(F_k+1 - F_k) + (G_k - G_k+1)],
+// zero through the top of the cloud-top layer, the bottom of the launch layer
+// and the top of the downdraft's first layer; so the column's momentum is
+// conserved exactly, whatever the coefficients.  Equivalently: the tracer
+// tendency with the plumes' momenta, minus the pressure force each plume exerts
+// in each layer it crosses.
+
+// Deep momentum tendency of one column for one wind component c.
+void deep_momentum(int pver, const DeepState<double>& s, const double* c, double c_up,
+                   double c_down, double* tend) {
+  for (int k = 0; k < pver; ++k) tend[k] = 0.0;
+  if (!s.active) return;
+  const int kb = s.kb, jt = s.jt, jd = s.jd;
+  double cu[MAXLEV], cd[MAXLEV], F[MAXLEV + 1], G[MAXLEV + 1];
+  for (int k = 0; k <= pver; ++k) F[k] = G[k] = 0.0;
+  for (int k = 0; k < pver; ++k) cu[k] = cd[k] = 0.0;
+  cu[kb] = c[kb];
+  for (int k = kb - 1; k > jt; --k)
+    cu[k] = (s.eta[k + 1] * (cu[k + 1] + c_up * (c[k] - c[k + 1])) +
+             (s.eta[k] - s.eta[k + 1]) * c[k]) / s.eta[k];
+  for (int k = jt + 1; k <= kb; ++k) F[k] = s.eta[k] * (cu[k] - c[k - 1]);
+  if (jd >= 0) {
+    cd[jd] = c[jd];
+    for (int k = jd + 1; k <= kb - 1; ++k)
+      cd[k] = (s.etad[k - 1] * (cd[k - 1] + c_down * (c[k] - c[k - 1])) +
+               (s.etad[k] - s.etad[k - 1]) * c[k]) / s.etad[k];
+    for (int k = jd; k <= kb - 1; ++k) G[k + 1] = s.alpha * s.etad[k] * (cd[k] - c[k + 1]);
+  }
+  for (int k = jt; k <= kb; ++k)
+    tend[k] = s.mb * (((F[k + 1] - F[k]) + (G[k] - G[k + 1])) / s.m[k]);
+}
+
+// Shallow momentum tendency of one column (s from shallow_column on the state
+// the shallow scheme saw; c the wind component it sees).
+void shallow_momentum(int pver, const ShalState<double>& s, const ShalP& P, const double* c,
+                      double c_up, double* tend) {
+  for (int k = 0; k < pver; ++k) tend[k] = 0.0;
+  if (!s.active) return;
+  const int ks = pver - 1, kts = s.kts;
+  double cu[MAXLEV], F[MAXLEV + 1];
+  for (int k = 0; k <= pver; ++k) F[k] = 0.0;
+  cu[ks] = c[ks];
+  for (int k = ks - 1; k > kts; --k) {
+    const double ustar = cu[k + 1] + c_up * (c[k] - c[k + 1]);
+    if (k >= s.klcl) {
+      cu[k] = ustar;
+    } else {
+      const double dz = s.z_int[k] - s.z_int[k + 1];
+      const double chi = 1.0 - std::exp(-P.eps_s * dz);
+      cu[k] = ustar + chi * (c[k] - ustar);
+    }
+  }
+  for (int k = kts + 1; k <= ks; ++k) F[k] = s.mb * (cu[k] - c[k - 1]);
+  for (int k = kts; k <= ks; ++k) tend[k] = (F[k + 1] - F[k]) / s.m[k];
+}
+
 void deep_fluxes(int pver, const DeepState<double>& s, double* mu, double* du, double* md) {
   for (int k = 0; k < pver; ++k) mu[k] = du[k] = md[k] = 0.0;
   if (!s.active) return;
@@ -1215,6 +1287,51 @@ int oracle_deep_shallow_tracers(int n_cols, int pver, int ld, const double* hyai
       for (int k = 0; k < pver; ++k) {
         tend_deep[n * tstride + k * ld + i] = td[k];
         tend_shallow[n * tstride + k * ld + i] = ts[k];
+      }
+    }
+  }
+  return 0;
+}
+
+int oracle_deep_shallow_momentum(int n_cols, int pver, int ld, const double* hyai,
+                                 const double* hybi, double p0, const double* T,
+                                 const double* q, const double* ps, const double* lambda,
+                                 const double* tau, const oracle_deep_params* dpar,
+                                 const oracle_shallow_params* spar, double dt, double c_up,
+                                 double c_down, const double* uv, double* tend_deep,
+                                 double* tend_shallow, int n_threads) {
+  if (!grid_ok(n_cols, pver, ld) || !dpar || !spar || !uv || !tend_deep || !tend_shallow)
+    return 1;
+  if (dpar->n_plumes > 1) return 1;  // the transport reading covers the bulk plume
+  const DeepP DP = to_deep(dpar);
+  const ShalP SP = to_shal(spar);
+  const size_t cstride = (size_t)pver * ld;
+#pragma omp parallel for schedule(dynamic, 8) num_threads(threads_for(n_threads))
+  for (int i = 0; i < n_cols; ++i) {
+    double Tc[MAXLEV], qc[MAXLEV], T2[MAXLEV], q2[MAXLEV];
+    for (int k = 0; k < pver; ++k) { Tc[k] = T[k * ld + i]; qc[k] = q[k * ld + i]; }
+    DeepState<double> s;
+    deep_column<double>(pver, hyai, hybi, p0, Tc, qc, ps[i],
+                        lambda ? lambda[i] : DP.lambda_default, tau ? tau[i] : DP.tau_default,
+                        DP, dt, s);
+    for (int k = 0; k < pver; ++k) {
+      T2[k] = Tc[k] + dt * s.dTdt[k];
+      q2[k] = qc[k] + dt * s.dqdt[k];
+      if (!s.bad && q2[k] < 0.0) q2[k] = 0.0;
+    }
+    ShalState<double> t;
+    shallow_column<double>(pver, hyai, hybi, p0, T2, q2, ps[i], SP, t);
+    // each component: deep transport, then the shallow transport of the
+    // deep-updated wind (no floor: a wind component may take either sign)
+    for (int n = 0; n < 2; ++n) {
+      double c[MAXLEV], c2[MAXLEV], td[MAXLEV], ts[MAXLEV];
+      for (int k = 0; k < pver; ++k) c[k] = uv[n * cstride + k * ld + i];
+      deep_momentum(pver, s, c, c_up, c_down, td);
+      for (int k = 0; k < pver; ++k) c2[k] = c[k] + dt * td[k];
+      shallow_momentum(pver, t, SP, c2, c_up, ts);
+      for (int k = 0; k < pver; ++k) {
+        tend_deep[n * cstride + k * ld + i] = td[k];
+        tend_shallow[n * cstride + k * ld + i] = ts[k];
       }
     }
   }

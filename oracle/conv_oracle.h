@@ -101,7 +101,7 @@ void oracle_shallow_column_diag(int pver, const double* hyai, const double* hybi
 
 /* Whole-grid drivers.  n_threads <= 1 runs serially; otherwise OpenMP
  * schedule(dynamic,8) over columns (the paper's load-balancing device,
- * Sec. III-A).  lambda/tau may be NULL (defaults).  Return 0 on success. */
+ * Sec. IV-A).  lambda/tau may be NULL (defaults).  Return 0 on success. */
 int oracle_deep(int n_cols, int pver, int ld, const double* hyai, const double* hybi, double p0,
                 const double* T, const double* q, const double* ps, const double* lambda,
                 const double* tau, const oracle_deep_params* par, double dt,
@@ -158,6 +158,21 @@ int oracle_deep_shallow_tracers(int n_cols, int pver, int ld, const double* hyai
                                 double dt, int ntr, const double* tracers, double* tend_deep,
                                 double* tend_shallow, const oracle_flux* flux_deep,
                                 const oracle_flux* flux_shallow, int n_threads);
+
+/* Convective momentum transport of the fused step: the two wind components
+ * uv [2][pver][ld] (u then v) carried by the plumes like tracers, plus the
+ * pressure-gradient term of Gregory et al. (1997) inside each plume (c_up for
+ * the updrafts, c_down for the downdraft; 0 gives the tracer transport), the
+ * environment's tendency the divergence of the interface eddy fluxes (column
+ * momentum conserved).  tend_deep, tend_shallow: [2][pver][ld] m/s2; the
+ * shallow scheme transports u + dt tend_deep (no floor). */
+int oracle_deep_shallow_momentum(int n_cols, int pver, int ld, const double* hyai,
+                                 const double* hybi, double p0, const double* T,
+                                 const double* q, const double* ps, const double* lambda,
+                                 const double* tau, const oracle_deep_params* dpar,
+                                 const oracle_shallow_params* spar, double dt, double c_up,
+                                 double c_down, const double* uv, double* tend_deep,
+                                 double* tend_shallow, int n_threads);
 
 /* Floating-point operation counts of the fused deep -> shallow step, summed over
  * the columns, by category (add/sub, mul, div, exp, log, pow, sqrt, unused):

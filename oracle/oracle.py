@@ -154,11 +154,16 @@ def lib():
                                        C.POINTER(ShallowParams), d, p, p]
         L.oracle_count_ops_by_pass.argtypes = [i, i, i, p, p, d, p, p, p, C.POINTER(DeepParams),
                                                C.POINTER(ShallowParams), d, p, p, p, p]
+        L.oracle_deep_shallow_momentum.argtypes = [i, i, i, p, p, d, p, p, p, p, p,
+                                                   C.POINTER(DeepParams),
+                                                   C.POINTER(ShallowParams), d, d, d, p, p, p,
+                                                   i]
         L.oracle_deep_shallow_counted.argtypes = [i, i, i, p, p, d, p, p, p,
                                                   C.POINTER(DeepParams), C.POINTER(ShallowParams),
                                                   d, C.POINTER(Out), C.POINTER(Out)]
         for fn in ("oracle_deep", "oracle_shallow", "oracle_deep_shallow", "oracle_deep_adjoint",
                    "oracle_deep_shallow_tracers", "oracle_deep_shallow_counted",
+                   "oracle_deep_shallow_momentum",
                    "oracle_deep_shallow_adjoint", "oracle_count_ops", "oracle_count_ops_by_pass"):
             getattr(L, fn).restype = i
         _lib = L
@@ -270,6 +275,30 @@ def deep_shallow_tracers(g, tracers, dpar=None, spar=None, dt=None, threads: int
         C.byref(Flux(*[fs[k].ctypes.data for k in ("mu", "du", "md")])), threads)
     assert rc == 0
     return td, ts, fd, fs
+
+
+def deep_shallow_momentum(g, uv, c_up=0.7, c_down=0.7, dpar=None, spar=None, dt=None,
+                          threads: int = 1, lam=None, tau=None):
+    """Convective momentum transport of the wind components uv ([2][pver][n], u
+    then v) by the fused step, with the plumes' pressure-gradient coefficients.
+    Returns (tend_deep, tend_shallow), each [2][pver][n]."""
+    dpar = dpar or deep_params()
+    spar = spar or shallow_params()
+    dt = g.dt if dt is None else dt
+    T, q, ps = _c64(g.T), _c64(g.q), _c64(g.ps)
+    lam = _c64(lam if lam is not None else g.lam)
+    tau = _c64(tau if tau is not None else g.tau)
+    n, pver = g.n_cols, g.pver
+    w = _c64(uv)
+    assert w.shape == (2, pver, n), w.shape
+    td, ts = np.zeros_like(w), np.zeros_like(w)
+    hyai, hybi = _c64(g.hyai), _c64(g.hybi)
+    rc = lib().oracle_deep_shallow_momentum(
+        n, pver, n, _ptr(hyai), _ptr(hybi), 1e5, _ptr(T), _ptr(q), _ptr(ps), _ptr(lam), _ptr(tau),
+        C.byref(dpar), C.byref(spar), dt, float(c_up), float(c_down), _ptr(w), _ptr(td),
+        _ptr(ts), threads)
+    assert rc == 0
+    return td, ts
 
 
 def deep_adjoint(g, gP, gH, w_heat=None, par=None, dt=None, threads: int = 1, lam=None,

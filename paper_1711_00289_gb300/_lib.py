@@ -132,12 +132,19 @@ def lib(build: bool = True):
     L.conv_advance.restype = st
     L.conv_tracer_transport.argtypes = [P(Grid), vp, P(Out), P(Out), d, st, vp, vp, vp, st, vp]
     L.conv_tracer_transport.restype = st
+    L.conv_momentum_transport.argtypes = [P(Grid), vp, P(Out), P(Out), d, d, d, vp, vp, vp, st,
+                                          vp]
+    L.conv_momentum_transport.restype = st
     L.conv_pipeline_plan.argtypes = [P(Grid), st, st, P(vp)]
     L.conv_pipeline_plan.restype = st
     L.conv_pipeline_run.argtypes = [vp, P(In), P(DeepParams), P(ShallowParams), d, P(Out),
                                     P(Out), vp]
     L.conv_pipeline_run.restype = st
     L.conv_pipeline_free.argtypes = [vp]
+    L.conv_count_triggered.argtypes = [vp, C.c_int32, C.c_int32, vp, vp]
+    L.conv_count_triggered.restype = st
+    L.conv_partition_columns.argtypes = [C.c_int32, C.c_int32, vp, d, d, C.c_int32, vp]
+    L.conv_partition_columns.restype = st
     L.conv_pipeline_free.restype = None
     _lib = L
     return L

@@ -171,15 +171,47 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def _shift(struct, col0: int, sizes: dict):
+    """Offset the column pointers of a conv_in / conv_out struct by col0 columns
+    (element sizes by field); the leading dimension stays that of the arrays."""
+    for name, size in sizes.items():
+        v = getattr(struct, name)
+        if v:
+            setattr(struct, name, v + col0 * size)
+    return struct
+
+
+def _in_sizes(precision):
+    rb = 8 if precision == "fp64" else 4
+    return {"T": rb, "q": rb, "ps": 8, "lam": 8, "tau": 8}
+
+
+def _out_sizes(precision):
+    rb = 8 if precision == "fp64" else 4
+    d = {k: rb for k in ("dTdt", "dqdt", "mu", "du", "md")}
+    d.update({k: 8 for k in ("prec", "cape", "mb", "cons_err")})
+    d.update({k: 4 for k in ("flags", "kb", "klcl", "ktop", "kaux")})
+    return d
+
+
 def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision="fp64",
                  lam=None, tau=None, deep_params=None, shallow_params=None, path="auto",
                  block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
-                 workspace: Workspace | None = None, stream=None, stage_events=None):
+                 workspace: Workspace | None = None, stream=None, stage_events=None,
+                 col0: int = 0):
     """Deep then shallow convection (Alg. 1 order) in one fused call.
 
     Returns ``(deep_out, shallow_out)`` dicts of output tensors.  stage_events:
-    optional three torch.cuda.Event the library records around its passes."""
+    optional three torch.cuda.Event the library records around its passes.
+    col0: first column of the range processed (columns col0 .. col0 + n_cols - 1
+    of every [pver, ld] / [ld] tensor; n_cols defaults to the rest of ld); the
+    other columns of the outputs are left untouched."""
     pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
+    col0 = int(col0)
+    if n_cols is None:
+        n = ld - col0
+    if col0 < 0 or n < 0 or col0 + n > ld:
+        raise ValueError(f"columns {col0}..{col0 + n - 1} outside ld = {ld}")
     od = out_deep if out_deep is not None else new_outputs(pver, ld, precision, T.device)
     os_ = out_shallow if out_shallow is not None else new_outputs(pver, ld, precision, T.device)
     dp = deep_params or L.deep_defaults()
@@ -188,10 +220,15 @@ def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision
     lc = _launch(path, block_threads, stage_events)
     nb = int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
     wp, wn = _ws_for(T.device, workspace).get(nb)
+    so_d = _out_struct(od, pver, ld, precision)
+    so_s = _out_struct(os_, pver, ld, precision)
+    if col0:
+        _shift(inp, col0, _in_sizes(precision))
+        _shift(so_d, col0, _out_sizes(precision))
+        _shift(so_s, col0, _out_sizes(precision))
     st = L.lib().conv_deep_shallow_run(
         C.byref(g), C.byref(inp), C.byref(dp), C.byref(sp), float(dt), _PREC[precision],
-        C.byref(_out_struct(od, pver, ld, precision)),
-        C.byref(_out_struct(os_, pver, ld, precision)), C.byref(lc), wp, wn, _stream(stream))
+        C.byref(so_d), C.byref(so_s), C.byref(lc), wp, wn, _stream(stream))
     L.check(st, "conv_deep_shallow_run")
     return od, os_
 
@@ -278,6 +315,47 @@ def tracer_transport(tracers, ps, vgrid: VerticalGrid, *, deep_out=None, shallow
         None if os_ is None else C.byref(os_), float(dt), int(ntr), _ptr(tracers), _ptr(td),
         _ptr(ts), _PREC[precision], _stream(stream))
     L.check(st, "conv_tracer_transport")
+    return td, ts
+
+
+def momentum_transport(uv, ps, vgrid: VerticalGrid, *, deep_out=None, shallow_out=None,
+                       dt: float = 1800.0, precision="fp64", cp_up: float = 0.7,
+                       cp_down: float = 0.7, n_cols=None, tend_deep=None, tend_shallow=None,
+                       stream=None):
+    """Convective momentum transport of the wind components uv ([2][pver][ld]
+    tensor, u then v) by the plumes of a run whose outputs hold the mass-flux
+    profiles (new_outputs(..., flux=True)), with the plumes' pressure-gradient
+    coefficients cp_up (updrafts) and cp_down (downdraft).  Returns (tend_deep,
+    tend_shallow) (None for a scheme not given); with both schemes the shallow
+    one transports the deep-updated wind u + dt tend_deep."""
+    rd = real_dtype(precision)
+    if uv.dim() != 3 or uv.shape[0] != 2 or not uv.is_cuda or uv.dtype != rd or \
+            not uv.is_contiguous():
+        raise TypeError(f"uv must be a contiguous CUDA {rd} tensor [2][pver][ld]")
+    _, pver, ld = uv.shape
+    if pver != vgrid.pver:
+        raise ValueError(f"uv has {pver} levels, the grid {vgrid.pver}")
+    n = ld if n_cols is None else int(n_cols)
+    _require_cuda(ps, "ps", torch.float64, (ld,))
+    if deep_out is None and shallow_out is None:
+        raise ValueError("give deep_out and/or shallow_out")
+    outs = []
+    for o, t in ((deep_out, tend_deep), (shallow_out, tend_shallow)):
+        if o is None:
+            outs.append((None, None))
+            continue
+        if t is None:
+            t = torch.empty_like(uv)
+        elif t.shape != uv.shape or t.dtype != rd or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("tendency tensors must match uv")
+        outs.append((_out_struct(o, pver, ld, precision), t))
+    g = vgrid.struct(n, ld)
+    (od, td), (os_, ts) = outs
+    st = L.lib().conv_momentum_transport(
+        C.byref(g), _ptr(ps), None if od is None else C.byref(od),
+        None if os_ is None else C.byref(os_), float(dt), float(cp_up), float(cp_down), _ptr(uv),
+        _ptr(td), _ptr(ts), _PREC[precision], _stream(stream))
+    L.check(st, "conv_momentum_transport")
     return td, ts
 
 

@@ -163,6 +163,54 @@ bool cvg::grid_ok(const conv_grid* g) {
   return fill_grid(g, a) == CONV_OK;
 }
 
+namespace {
+conv_status transport_run(const conv_grid* grid, const double* ps, const conv_out* deep_out,
+                          const conv_out* shallow_out, double dt, int ntr, const void* tracers,
+                          void* tend_deep, void* tend_shallow, conv_precision prec,
+                          conv_stream stream, bool mom, double cp_up, double cp_down) {
+  if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
+  RunArgs g;
+  std::memset(&g, 0, sizeof g);
+  conv_status s = fill_grid(grid, g);
+  if (s != CONV_OK) return s;
+  if (!ps || ntr < 0 || (!deep_out && !shallow_out)) return CONV_ERR_ARG;
+  if (ntr > 0 && !tracers) return CONV_ERR_ARG;
+  if (deep_out && shallow_out && !(std::isfinite(dt) && dt > 0.0)) return CONV_ERR_ARG;
+  if (ntr > 0 && ((deep_out && !tend_deep) || (shallow_out && !tend_shallow)))
+    return CONV_ERR_ARG;
+  cvg::TrArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.L = g.L;
+  a.n = g.n;
+  a.ld = g.ld;
+  a.pver = g.L.pver;
+  a.ntr = ntr;
+  a.tstride = (size_t)g.L.pver * (size_t)g.ld;
+  a.ps = ps;
+  a.tr = tracers;
+  a.dt = dt;
+  a.stream = reinterpret_cast<cudaStream_t>(stream);
+  const conv_out* outs[2] = {deep_out, shallow_out};
+  cvg::TrScheme* sch[2] = {&a.d, &a.s};
+  void* tends[2] = {tend_deep, tend_shallow};
+  for (int m = 0; m < 2; ++m) {
+    const conv_out* o = outs[m];
+    if (!o) continue;
+    if (!o->mu || !o->du || !o->flags || !o->kb || !o->ktop) return CONV_ERR_ARG;
+    const bool down = m == 0 && o->md;
+    if (down && !o->kaux) return CONV_ERR_ARG;
+    *sch[m] = cvg::TrScheme{o->mu, o->du, down ? o->md : nullptr, o->flags, o->kb, o->ktop,
+                            down ? o->kaux : nullptr, tends[m]};
+  }
+  a.has_d = deep_out != nullptr;
+  a.has_s = shallow_out != nullptr;
+  a.mom = mom;
+  a.cp_up = cp_up;
+  a.cp_down = cp_down;
+  return cvg::launch_transport(a, prec == CONV_FP64) == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
+}  // namespace
+
 extern "C" {
 
 void conv_deep_defaults(conv_deep_params* p) {
@@ -276,44 +324,23 @@ conv_status conv_tracer_transport(const conv_grid* grid, const double* ps,
                                   const conv_out* deep_out, const conv_out* shallow_out,
                                   double dt, int ntr, const void* tracers, void* tend_deep,
                                   void* tend_shallow, conv_precision prec, conv_stream stream) {
-  if (prec != CONV_FP64 && prec != CONV_MIXED) return CONV_ERR_ARG;
-  RunArgs g;
-  std::memset(&g, 0, sizeof g);
-  conv_status s = fill_grid(grid, g);
-  if (s != CONV_OK) return s;
-  if (!ps || ntr < 0 || (!deep_out && !shallow_out)) return CONV_ERR_ARG;
-  if (ntr > 0 && !tracers) return CONV_ERR_ARG;
-  if (deep_out && shallow_out && !(std::isfinite(dt) && dt > 0.0)) return CONV_ERR_ARG;
-  if (ntr > 0 && ((deep_out && !tend_deep) || (shallow_out && !tend_shallow)))
-    return CONV_ERR_ARG;
-  cvg::TrArgs a;
-  std::memset(&a, 0, sizeof a);
-  a.L = g.L;
-  a.n = g.n;
-  a.ld = g.ld;
-  a.pver = g.L.pver;
-  a.ntr = ntr;
-  a.tstride = (size_t)g.L.pver * (size_t)g.ld;
-  a.ps = ps;
-  a.tr = tracers;
-  a.dt = dt;
-  a.stream = reinterpret_cast<cudaStream_t>(stream);
-  const conv_out* outs[2] = {deep_out, shallow_out};
-  cvg::TrScheme* sch[2] = {&a.d, &a.s};
-  void* tends[2] = {tend_deep, tend_shallow};
-  for (int m = 0; m < 2; ++m) {
-    const conv_out* o = outs[m];
-    if (!o) continue;
-    if (!o->mu || !o->du || !o->flags || !o->kb || !o->ktop) return CONV_ERR_ARG;
-    const bool down = m == 0 && o->md;
-    if (down && !o->kaux) return CONV_ERR_ARG;
-    *sch[m] = cvg::TrScheme{o->mu, o->du, down ? o->md : nullptr, o->flags, o->kb, o->ktop,
-                            down ? o->kaux : nullptr, tends[m]};
-  }
-  a.has_d = deep_out != nullptr;
-  a.has_s = shallow_out != nullptr;
-  return cvg::launch_transport(a, prec == CONV_FP64) == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+  return transport_run(grid, ps, deep_out, shallow_out, dt, ntr, tracers, tend_deep,
+                       tend_shallow, prec, stream, false, 0.0, 0.0);
 }
+
+conv_status conv_momentum_transport(const conv_grid* grid, const double* ps,
+                                    const conv_out* deep_out, const conv_out* shallow_out,
+                                    double dt, double cp_up, double cp_down, const void* uv,
+                                    void* tend_deep, void* tend_shallow, conv_precision prec,
+                                    conv_stream stream) {
+  if (!(cp_up >= 0.0 && cp_up <= 1.0) || !(cp_down >= 0.0 && cp_down <= 1.0))
+    return CONV_ERR_ARG;
+  if (!uv) return CONV_ERR_ARG;
+  return transport_run(grid, ps, deep_out, shallow_out, dt, 2, uv, tend_deep, tend_shallow,
+                       prec, stream, true, cp_up, cp_down);
+}
+
+
 
 conv_status conv_deep_adjoint(const conv_grid* grid, const conv_in* in,
                               const conv_deep_params* par, double dt, conv_precision prec,
@@ -427,7 +454,7 @@ cvg::BatchShape default_shape(bool fp64, int max_pver, int sms) {
   sh.max_pver = max_pver;
   sh.trigger_block = 128;
   sh.plume_block = 128;
-  sh.plume_grid = sms * cvg::batch_plume_occupancy(fp64, 128);
+  sh.plume_grid = sms * cvg::batch_plume_occupancy(fp64, 128, max_pver);
   return sh;
 }
 
@@ -563,7 +590,7 @@ conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_s
     if (err != cudaSuccess) break;
     cvg::BatchShape sh = best;
     sh.plume_block = pb;
-    sh.plume_grid = b->sms * cvg::batch_plume_occupancy(fp64, pb);
+    sh.plume_grid = b->sms * cvg::batch_plume_occupancy(fp64, pb, best.max_pver);
     float ms = 0.f;
     err = time_shape(sh, &ms);
     if (err != cudaSuccess) break;

@@ -151,6 +151,8 @@ struct TrArgs {
   double dt;
   TrScheme d, s;
   bool has_d, has_s;
+  bool mom;               // momentum transport: ntr = 2 (u, v), pressure-gradient terms
+  double cp_up, cp_down;  // their coefficients (updrafts, downdraft)
   cudaStream_t stream;
 };
 cudaError_t launch_transport(const TrArgs& a, bool fp64);

@@ -83,10 +83,16 @@ struct TrSrc {
 // column, level by level: the level's mass fluxes, layer mass and mixing ratios
 // are loaded and divided once for all G tracers, whose recurrences then run side
 // by side (G independent loads per level in flight).
-template <class R, int G>
+// MOM: the momentum variant (conv_momentum_transport): a plume crossing layer k
+// from its neighbour j gains cp (flux continuing from j) (c_k - c_j) -- the
+// convective-scale pressure gradient, coefficient cp_up for the updraft and
+// cp_down for the downdraft -- and the environment of layer k loses the same
+// (the pressure force the plume exerts), so column momentum is conserved.
+template <class R, int G, bool MOM = false>
 __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLevels<R>& L, R ps,
                                       int pver, size_t ld, size_t tstr, int i, const Plume& p,
-                                      const TrSrc<R>& C, R* __restrict__ out, int ng) {
+                                      const TrSrc<R>& C, R* __restrict__ out, int ng,
+                                      R cp_up = R(0), R cp_down = R(0)) {
   auto put = [&](int g, int k, R v) { out[(size_t)g * tstr + (size_t)k * ld] = v; };
   if (!p.active) {
     for (int k = 0; k < pver; ++k)
@@ -113,8 +119,12 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
   // downdraft values arriving at the launch layer: mixed from jd down to kb-1,
   // entraining md[k] - md[k-1] at layer k
   R cd[G];
+  R cpv[MOM ? G : 1];  // momentum: the tracer one level up the downdraft
 #pragma unroll
   for (int g = 0; g < G; ++g) cd[g] = R(0);
+  if constexpr (MOM)
+#pragma unroll
+    for (int g = 0; g < G; ++g) cpv[g] = R(0);
   R mdl = R(0);
   if (dd) {
     R mprev = R(0);
@@ -135,8 +145,15 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
         if (mk > R(0)) {
           const R r = Mth<R>::dv(mk - mprev, mk);
 #pragma unroll
-          for (int g = 0; g < G; ++g) cd[g] = cd[g] + r * (cv[g][j] - cd[g]);
+          for (int g = 0; g < G; ++g) {
+            cd[g] = cd[g] + r * (cv[g][j] - cd[g]);
+            if constexpr (MOM)
+              if (mprev > R(0)) cd[g] = cd[g] + (R(1) - r) * cp_down * (cv[g][j] - cpv[g]);
+          }
         }
+        if constexpr (MOM)
+#pragma unroll
+          for (int g = 0; g < G; ++g) cpv[g] = cv[g][j];
         mprev = mk;
       }
     }
@@ -153,7 +170,7 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
   }
   R mu1 = R(0);
   for (int k0 = kb; k0 >= kt; k0 -= D) {
-    R muv[D], duv[D], mdv[D], cv[G][D];
+    R muv[D], duv[D], mdv[D], mdu[MOM ? D : 1], cv[G][D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       const int k = k0 - j;
@@ -162,6 +179,8 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
       muv[j] = ok ? mu[o] : R(0);
       duv[j] = ok ? du[o] : R(0);
       mdv[j] = (ok && dd && k >= jd && k <= kb - 1) ? md[o] : R(0);
+      // the downdraft flux arriving from the layer above (momentum only)
+      if constexpr (MOM) mdu[j] = (ok && dd && k > jd && k <= kb - 1) ? md[o - ld] : R(0);
 #pragma unroll
       for (int g = 0; g < G; ++g) cv[g][j] = (k > kt && g < ng) ? C(g, k - 1) : R(0);
     }
@@ -181,8 +200,17 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
           t += mdk * (cb[g] - ck[g]);
           if (k == kb) t += mdl * (cd[g] - ck[g]);
         }
-        put(g, k, t * rm);
-        cu[g] = muk > R(0) ? cu[g] + ru * (ck[g] - cu[g]) : R(0);
+        if constexpr (MOM) {
+          // pressure forces of the updraft (from below) and the downdraft (from
+          // above) in this layer; the updraft carries its own away
+          const R pu = cp_up * (mu1 - duk) * (ck[g] - cb[g]);
+          t -= pu + cp_down * mdu[j] * (ck[g] - cup);
+          put(g, k, t * rm);
+          cu[g] = muk > R(0) ? cu[g] + ru * (ck[g] - cu[g]) + Mth<R>::dv(pu, muk) : R(0);
+        } else {
+          put(g, k, t * rm);
+          cu[g] = muk > R(0) ? cu[g] + ru * (ck[g] - cu[g]) : R(0);
+        }
         cb[g] = ck[g];
         ck[g] = cup;
       }
@@ -191,7 +219,7 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
   }
 }
 
-template <class R, int G>
+template <class R, int G, bool MOM = false>
 __global__ void __launch_bounds__(kTrBlock) k_transport(const __grid_constant__ TrArgs a) {
   __shared__ ShLevels<R> L;
   for (int k = threadIdx.x; k <= a.pver; k += blockDim.x) {
@@ -216,17 +244,21 @@ __global__ void __launch_bounds__(kTrBlock) k_transport(const __grid_constant__ 
     const R ps = (R)a.ps[i];
     R* td = a.has_d ? static_cast<R*>(a.d.tend) + base : nullptr;
     bool deep_active = false;
+    const R cpu = (R)a.cp_up, cpd = (R)a.cp_down;
     if (a.has_d) {
       const Plume p = plume_of(a.d, i, pver);
       deep_active = p.active;
-      stage<R, G>(a.d, a.d.md != nullptr, L, ps, pver, ld, tstr, i, p,
-                  TrSrc<R>{c, nullptr, R(0), false, ld, tstr}, td, ng);
+      stage<R, G, MOM>(a.d, a.d.md != nullptr, L, ps, pver, ld, tstr, i, p,
+                       TrSrc<R>{c, nullptr, R(0), false, ld, tstr}, td, ng, cpu, cpd);
     }
     if (a.has_s) {
+      // the shallow scheme sees the deep-updated field: a tracer floored at 0,
+      // a wind component as it is
       const Plume p = plume_of(a.s, i, pver);
-      stage<R, G>(a.s, false, L, ps, pver, ld, tstr, i, p,
-                  TrSrc<R>{c, deep_active ? td : nullptr, (R)a.dt, a.has_d, ld, tstr},
-                  static_cast<R*>(a.s.tend) + base, ng);
+      stage<R, G, MOM>(a.s, false, L, ps, pver, ld, tstr, i, p,
+                       TrSrc<R>{c, deep_active ? td : nullptr, (R)a.dt, a.has_d && !MOM, ld,
+                                tstr},
+                       static_cast<R*>(a.s.tend) + base, ng, cpu, cpd);
     }
   }
 }
@@ -238,10 +270,17 @@ cudaError_t launch_transport(const TrArgs& a, bool fp64) {
   const int blocks = (a.n + kTrBlock - 1) / kTrBlock;
   const dim3 grid((unsigned)((a.ntr + kTrGroup - 1) / kTrGroup),
                   (unsigned)(blocks < 65535 ? blocks : 65535));
-  if (fp64)
+  if (a.mom) {  // the two wind components as one group
+    const dim3 g2(1, grid.y);
+    if (fp64)
+      k_transport<double, 2, true><<<g2, kTrBlock, 0, a.stream>>>(a);
+    else
+      k_transport<float, 2, true><<<g2, kTrBlock, 0, a.stream>>>(a);
+  } else if (fp64) {
     k_transport<double, kTrGroup><<<grid, kTrBlock, 0, a.stream>>>(a);
-  else
+  } else {
     k_transport<float, kTrGroup><<<grid, kTrBlock, 0, a.stream>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -114,6 +114,7 @@ EVAPORATION = "tests/test_oracle_evaporation.py"
 SPECTRUM = "tests/test_oracle_spectrum.py"
 ADJOINT = "tests/test_oracle_adjoint.py"
 COUNTS = "tests/test_oracle_counts.py"
+MOMENTUM = "tests/test_oracle_momentum.py"
 # The forward-mode type's rules for pow and sqrt are left out: no derivative
 # that reaches an output passes through them (pow's differentiated argument is
 # the LCL pressure, which only places levels; sqrt takes a constant), so a slip
@@ -133,6 +134,24 @@ EXT_MUTANTS = {
         "  s.cape = cape;\n  mark_trigger_end<R>();", "  s.cape = cape;", COUNTS),
     "LFC-search tally from the start of the column": (
         "  mark_lfc_search<R>(false);\n", "", COUNTS),
+    # the momentum transport
+    "updraft pressure term pushes away from the environment": (
+        "cu[k] = (s.eta[k + 1] * (cu[k + 1] + c_up * (c[k] - c[k + 1])) +",
+        "cu[k] = (s.eta[k + 1] * (cu[k + 1] - c_up * (c[k] - c[k + 1])) +", MOMENTUM),
+    "downdraft pressure term from the layer below": (
+        "cd[k] = (s.etad[k - 1] * (cd[k - 1] + c_down * (c[k] - c[k - 1])) +",
+        "cd[k] = (s.etad[k - 1] * (cd[k - 1] + c_down * (c[k] - c[k + 1])) +", MOMENTUM),
+    "shallow plume skips the pressure term below its LCL": (
+        "      cu[k] = ustar;\n", "      cu[k] = cu[k + 1];\n", MOMENTUM),
+    "updraft eddy flux upwinded from its own layer": (
+        "for (int k = jt + 1; k <= kb; ++k) F[k] = s.eta[k] * (cu[k] - c[k - 1]);",
+        "for (int k = jt + 1; k <= kb; ++k) F[k] = s.eta[k] * (cu[k] - c[k]);", MOMENTUM),
+    "downdraft eddy flux without its limiter": (
+        "G[k + 1] = s.alpha * s.etad[k] * (cd[k] - c[k + 1]);",
+        "G[k + 1] = s.etad[k] * (cd[k] - c[k + 1]);", MOMENTUM),
+    "shallow eddy flux through the wrong interface": (
+        "for (int k = kts + 1; k <= ks; ++k) F[k] = s.mb * (cu[k] - c[k - 1]);",
+        "for (int k = kts + 1; k <= ks; ++k) F[k] = s.mb * (cu[k - 1] - c[k - 1]);", MOMENTUM),
     "drizzle band ten times wider": (
         "std::fabs(val(l) - P.ql_crit) < 1e-4", "std::fabs(val(l) - P.ql_crit) < 1e-3", COUNTS),
     "tangent quotient rule sign": (
