@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(64) k_deep_adjoint(const __grid_constant__ Adj
   if (i >= a.n) return;
   const int pver = a.L.pver, ld = a.ld;
   Column<double> c;
-  init_column(c, a.L, input_src<double>(a, i), a.ps[i]);
+  LevelBuf<double> cbuf;
+  init_column(c, a.L, input_src<double>(a, i), a.ps[i], cbuf);
   const double lam = a.lam ? a.lam[i] : a.dp.lambda_default;
   const double tau = a.tau ? a.tau[i] : a.dp.tau_default;
   const double gP = A.gP ? A.gP[i] : 0.0, gH = A.gH ? A.gH[i] : 0.0;
@@ -63,11 +64,12 @@ __global__ void __launch_bounds__(64) k_step_adjoint(const __grid_constant__ Ste
   if (i >= a.n) return;
   const int pver = a.L.pver, ld = a.ld;
   Column<double> c, c2;
-  init_column(c, a.L, input_src<double>(a, i), a.ps[i]);
+  LevelBuf<double> cbuf, cbuf2;
+  init_column(c, a.L, input_src<double>(a, i), a.ps[i], cbuf);
   init_column(c2, a.L,
               Src<double>{static_cast<const double*>(a.T), static_cast<const double*>(a.q), A.gT,
                           A.gq, a.dt, (size_t)ld, i, true},
-              a.ps[i]);
+              a.ps[i], cbuf2);
   const double lam = a.lam ? a.lam[i] : a.dp.lambda_default;
   const double tau = a.tau ? a.tau[i] : a.dp.tau_default;
   double g[4];

@@ -537,12 +537,31 @@ struct ColCache<double> {
   double T[MAXL], q[MAXL], pm[MAXL], m[MAXL], Tv[MAXL], h[MAXL];
 };
 
+// A per-thread array over levels, element k at p[k * stride]: either the
+// thread's own local array (stride 1) or the thread's slice of a shared-memory
+// array of its block, level-major with the thread index innermost (stride =
+// block size), where the 32 threads of a warp reading one level touch 32
+// consecutive words -- one access, no bank conflict.
+template <class R>
+struct LevelArr {
+  R* p;
+  int stride;
+  __device__ __forceinline__ R& operator[](int k) const { return p[k * stride]; }
+};
+
+// A thread's own storage for a column's level arrays (kept outside Column, so
+// that stores through the views cannot alias the views themselves).
+template <class R>
+struct LevelBuf {
+  R v[2 * MAXL];
+};
+
 template <class R>
 struct Column {
   using Pr = typename PressOf<R>::type;
   Src<R> s;
   const Levels* L;
-  R zm[MAXL], dl[MAXL];
+  LevelArr<R> zm, dl;  // mid-layer heights and layer log-thicknesses
   ColCache<R> cc;
   R Tref, qref;
   R psR;  // ps in the working precision
@@ -590,14 +609,25 @@ struct Column {
   __device__ __forceinline__ R dz(int k) const { return R(RD / GRAV) * Tv(k) * dl[k]; }
 };
 
+// buf: the thread's own storage for zm and dl.
 template <class R>
 __device__ __forceinline__ void init_column(Column<R>& c, const Levels& L, const Src<R>& s,
-                                            double ps) {
+                                            double ps, LevelBuf<R>& buf) {
   c.s = s;
   c.L = &L;
   c.pver = L.pver;
   c.ps = ps;
   c.psR = (R)ps;
+  c.zm = LevelArr<R>{buf.v, 1};
+  c.dl = LevelArr<R>{buf.v + MAXL, 1};
+}
+
+// Keep zm and dl in a block-shared array instead: lv = this thread's first word
+// of 2 pver levels x stride words (zm on levels 0..pver-1, then dl).
+template <class R>
+__device__ __forceinline__ void bind_levels(Column<R>& c, R* lv, int stride) {
+  c.zm = LevelArr<R>{lv, stride};
+  c.dl = LevelArr<R>{lv + c.pver * stride, stride};
 }
 
 __device__ __forceinline__ bool in_range(double T, double q) {

@@ -1,7 +1,7 @@
 // compact.cu -- the compacted path: the GPU answer to the load imbalance the
-// paper fights with OpenMP dynamic scheduling (Sec. III-A): "at grid points
-// where there is no deep clouding, the corresponding column iterations ... are
-// skipped".  Instead of letting a warp carry idle lanes through the plume code:
+// paper fights with OpenMP dynamic scheduling (Sec. IV-A), which arises because
+// the deep scheme's column work is skipped wherever no deep cloud forms.
+// Instead of letting a warp carry idle lanes through the plume code:
 //
 //  k_trigger (all columns, one thread each): prologue, launch level, LCL,
 //    undilute parcel and CAPE.  A column that does not trigger deep convection
@@ -18,13 +18,27 @@
 
 namespace cvg {
 
+// This thread's slice of the block's shared level arrays (nullptr: none).
+template <class R>
+__device__ __forceinline__ R* smem_levels() {
+  if constexpr (SmemLevels<R>::on) {
+    extern __shared__ __align__(16) unsigned char cvg_smem[];
+    return reinterpret_cast<R*>(cvg_smem) + threadIdx.x;
+  } else {
+    return nullptr;
+  }
+}
+
 // Trigger pass of one column (all lanes of the warp must call it: the queue
 // append is a warp ballot).  `tag` is what the queue records for the column
 // (the column index, or a batch-wide index), `live` false for padding lanes.
-template <class R, bool EXT = false>
+// SMEM: the column's level arrays live in the block's shared memory
+// (smem_levels), not in the thread's local arrays.
+template <class R, bool EXT = false, bool SMEM = false>
 __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R>& w, int i,
                                              bool live, int tag) {
   Column<R> c;
+  LevelBuf<R> cbuf;
   DeepOut o;
   DeepTrig<R> t;
   t.triggered = false;
@@ -32,7 +46,8 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
   t.tps = (size_t)w.cap;
   bool valid = false;
   if (live) {
-    init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
+    init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
+    if constexpr (SMEM) bind_levels(c, smem_levels<R>(), blockDim.x);
     o.prec = o.cape = o.mb = o.cons = 0.0;
     o.flags = 0;
     o.kb = o.klcl = o.ktop = o.kaux = -1;
@@ -93,21 +108,23 @@ template <class R, bool EXT>
 __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::trigger / kCompactBlock)
     k_trigger(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  trigger_body<R, EXT>(a, w, i, i < a.n, i);
+  trigger_body<R, EXT, SmemLevels<R>::on>(a, w, i, i < a.n, i);
 }
 
 // Plume pass of the column in queue slot `slot`: column i of member a, queued
 // under `tag` (its index in the workspace's per-column arrays).
-template <class R, bool EXT = false>
+template <class R, bool EXT = false, bool SMEM = false>
 __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>& w, int slot,
                                            int i, int tag) {
   Column<R> c;
-  init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
+  LevelBuf<R> cbuf;
+  init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
+  if constexpr (SMEM) bind_levels(c, smem_levels<R>(), blockDim.x);
   DeepTrig<R> t;
-  const int lv = w.levels[slot];
-  t.kb = lv & 0xff;
-  t.klcl = (lv >> 8) & 0xff;
-  t.kel = (lv >> 16) & 0xff;
+  const int lvl = w.levels[slot];
+  t.kb = lvl & 0xff;
+  t.klcl = (lvl >> 8) & 0xff;
+  t.kel = (lvl >> 16) & 0xff;
   t.cape = w.cape[slot];
   t.triggered = true;
   t.newton = 0.f;
@@ -140,7 +157,28 @@ __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactB
   const int slot = blockIdx.x * blockDim.x + threadIdx.x;
   if (slot >= *w.count) return;
   const int i = w.queue[slot];
-  plume_body<R, EXT>(a, w, slot, i, i);
+  plume_body<R, EXT, SmemLevels<R>::on>(a, w, slot, i, i);
+}
+
+// The compacted kernels that keep level arrays in shared memory ask for the
+// largest shared-memory carve-out, so that their resident blocks fit (set once
+// per kernel, before its first launch).
+template <class R>
+static void prefer_shared() {
+  if constexpr (SmemLevels<R>::on) {
+    static const bool done = [] {
+      cudaFuncSetAttribute(k_trigger<R, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+      cudaFuncSetAttribute(k_trigger<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+      cudaFuncSetAttribute(k_plume<R, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+      cudaFuncSetAttribute(k_plume<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+      return true;
+    }();
+    (void)done;
+  }
 }
 
 size_t compact_workspace_bytes(int n, int pver, bool fp64) {
@@ -164,17 +202,19 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
   if (e != cudaSuccess) return e;
   const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
+  const size_t sm = smem_levels_bytes<R>(a.L.pver, kCompactBlock);
+  prefer_shared<R>();
   if (a.ext)
-    k_trigger<R, true><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+    k_trigger<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
   else
-    k_trigger<R, false><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+    k_trigger<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   record_stage(a, 1);
   if (a.ext)
-    k_plume<R, true><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+    k_plume<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
   else
-    k_plume<R, false><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+    k_plume<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
   e = cudaGetLastError();
   record_stage(a, 2);
   return e;
@@ -213,7 +253,7 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::trigger / BLOCK)
     m = find_member(b.offsets, b.n_members, g);
     i = g - b.offsets[m];
   }
-  trigger_body(b.members[m], w, i, live, g);
+  trigger_body<R, false, SmemLevels<R>::on>(b.members[m], w, i, live, g);
 }
 
 template <class R, int BLOCK>
@@ -223,34 +263,66 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
   for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
     const int g = w.queue[slot];
     const int m = find_member(b.offsets, b.n_members, g);
-    plume_body(b.members[m], w, slot, g - b.offsets[m], g);
+    plume_body<R, false, SmemLevels<R>::on>(b.members[m], w, slot, g - b.offsets[m], g);
+  }
+}
+
+// Shared-memory set-up of the batch kernels at one block size: the largest
+// carve-out, and the dynamic size of the largest level count (a 256-thread
+// block of 32-level columns needs 64 KB, above the default 48 KB limit).
+template <class R, int BLOCK>
+static void batch_smem_setup() {
+  if constexpr (SmemLevels<R>::on) {
+    static const bool done = [] {
+      const int most = (int)smem_levels_bytes<R>(CONV_MAX_LEVELS, BLOCK);
+      for (const void* f : {(const void*)k_batch_trigger<R, BLOCK>,
+                            (const void*)k_batch_plume<R, BLOCK>}) {
+        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+      }
+      return true;
+    }();
+    (void)done;
   }
 }
 
 template <class R, int BLOCK>
-static int plume_occupancy() {
+static int plume_occupancy(int max_pver) {
+  batch_smem_setup<R, BLOCK>();
   int blocks = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_plume<R, BLOCK>, BLOCK, 0) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_plume<R, BLOCK>, BLOCK,
+                                                    smem_levels_bytes<R>(max_pver, BLOCK)) !=
       cudaSuccess)
     return 1;
   return blocks < 1 ? 1 : blocks;
 }
 
-int batch_plume_occupancy(bool fp64, int block) {
+int batch_plume_occupancy(bool fp64, int block, int max_pver) {
   switch (block) {
-    case 64: return fp64 ? plume_occupancy<double, 64>() : plume_occupancy<float, 64>();
-    case 256: return fp64 ? plume_occupancy<double, 256>() : plume_occupancy<float, 256>();
-    default: return fp64 ? plume_occupancy<double, 128>() : plume_occupancy<float, 128>();
+    case 64:
+      return fp64 ? plume_occupancy<double, 64>(max_pver) : plume_occupancy<float, 64>(max_pver);
+    case 256:
+      return fp64 ? plume_occupancy<double, 256>(max_pver)
+                  : plume_occupancy<float, 256>(max_pver);
+    default:
+      return fp64 ? plume_occupancy<double, 128>(max_pver)
+                  : plume_occupancy<float, 128>(max_pver);
   }
 }
 
 template <class R, int BLOCK>
-static void launch_trig(const BatchDev& b, const CompactWs<R>& w, cudaStream_t s) {
-  k_batch_trigger<R, BLOCK><<<(b.total + BLOCK - 1) / BLOCK, BLOCK, 0, s>>>(b, w);
+static void launch_trig(const BatchDev& b, const CompactWs<R>& w, int max_pver,
+                        cudaStream_t s) {
+  batch_smem_setup<R, BLOCK>();
+  k_batch_trigger<R, BLOCK><<<(b.total + BLOCK - 1) / BLOCK, BLOCK,
+                              smem_levels_bytes<R>(max_pver, BLOCK), s>>>(b, w);
 }
 template <class R, int BLOCK>
-static void launch_plume(const BatchDev& b, const CompactWs<R>& w, int grid, cudaStream_t s) {
-  k_batch_plume<R, BLOCK><<<grid, BLOCK, 0, s>>>(b, w);
+static void launch_plume(const BatchDev& b, const CompactWs<R>& w, int grid, int max_pver,
+                         cudaStream_t s) {
+  batch_smem_setup<R, BLOCK>();
+  k_batch_plume<R, BLOCK><<<grid, BLOCK, smem_levels_bytes<R>(max_pver, BLOCK), s>>>(b, w);
 }
 
 template <class R>
@@ -270,17 +342,17 @@ static cudaError_t batch_t(const BatchDev& b, const BatchShape& sh, void* ws, si
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   switch (sh.trigger_block) {
-    case 64: launch_trig<R, 64>(b, w, s); break;
-    case 256: launch_trig<R, 256>(b, w, s); break;
-    default: launch_trig<R, 128>(b, w, s); break;
+    case 64: launch_trig<R, 64>(b, w, sh.max_pver, s); break;
+    case 256: launch_trig<R, 256>(b, w, sh.max_pver, s); break;
+    default: launch_trig<R, 128>(b, w, sh.max_pver, s); break;
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (ev && ev[1]) cudaEventRecord(ev[1], s);
   switch (sh.plume_block) {
-    case 64: launch_plume<R, 64>(b, w, sh.plume_grid, s); break;
-    case 256: launch_plume<R, 256>(b, w, sh.plume_grid, s); break;
-    default: launch_plume<R, 128>(b, w, sh.plume_grid, s); break;
+    case 64: launch_plume<R, 64>(b, w, sh.plume_grid, sh.max_pver, s); break;
+    case 256: launch_plume<R, 256>(b, w, sh.plume_grid, sh.max_pver, s); break;
+    default: launch_plume<R, 128>(b, w, sh.plume_grid, sh.max_pver, s); break;
   }
   e = cudaGetLastError();
   if (ev && ev[2]) cudaEventRecord(ev[2], s);

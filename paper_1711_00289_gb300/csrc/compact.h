@@ -12,17 +12,50 @@ constexpr int kCompactBlock = 128;
 // FP32 operations: more resident warps hide more of that latency, until the
 // spills of a tighter cap cost more.  Measured sweeps of the caps put the
 // trigger pass at 1408 threads per SM (40 registers; 1664 threads, 32
-// registers, was 21% slower) and the plume pass at 896 (72 registers; 768 was
-// 18% slower, 1024 2% slower).  The FP64 kernels are bound by the FP64 pipe and
-// need enough warps in flight to keep it fed: 896 threads (72 registers).
+// registers, was 21% slower; 1024 threads, 64 registers, 50% slower) and the
+// plume pass at 896 (72 registers; 768 was 18% slower, 1024 2% slower).  The
+// FP64 kernels are bound by the FP64 pipe and need enough warps in flight to
+// keep it fed: 896 threads (72 registers).  (Build-time overrides, for sweeps.)
+#ifndef CVG_TRIGGER_SM_THREADS
+#define CVG_TRIGGER_SM_THREADS 1408
+#endif
+#ifndef CVG_PLUME_SM_THREADS
+#define CVG_PLUME_SM_THREADS 896
+#endif
+// Level arrays in shared memory (1) or in each thread's local memory (0, the
+// default): measured on the 884,736-column step, shared memory limits the
+// trigger pass to 896 resident threads per SM (7 blocks of 30 KB) and made it
+// 9% slower (0.544 against 0.498 ms); the plume pass gained 3% (0.444 against
+// 0.459 ms) and the batched ensemble lost 13%.
+#ifndef CVG_SMEM_LEVELS
+#define CVG_SMEM_LEVELS 0
+#endif
 template <class R>
 struct SmThreads {
   static constexpr int trigger = 896, plume = 896;
 };
 template <>
 struct SmThreads<float> {
-  static constexpr int trigger = 1408, plume = 896;
+  static constexpr int trigger = CVG_TRIGGER_SM_THREADS, plume = CVG_PLUME_SM_THREADS;
 };
+
+// Where the compacted kernels keep each column's mid-layer heights and layer
+// log-thicknesses (Column::zm, dl): in shared memory, 2 pver levels x block
+// words per block (level-major, thread innermost), for the mixed path; in the
+// threads' own local arrays for FP64, where the 8-byte words would leave room
+// for too few blocks per SM.
+template <class R>
+struct SmemLevels {
+  static constexpr bool on = false;
+};
+template <>
+struct SmemLevels<float> {
+  static constexpr bool on = CVG_SMEM_LEVELS != 0;
+};
+template <class R>
+inline size_t smem_levels_bytes(int pver, int block) {
+  return SmemLevels<R>::on ? sizeof(R) * 2 * (size_t)pver * (size_t)block : 0;
+}
 
 // Device workspace of the compacted path, carved from one caller buffer:
 //   count  int32      queue length (zeroed at the start of every run)
@@ -78,7 +111,7 @@ struct BatchShape {
   int plume_block;    // 64, 128 or 256
   int plume_grid;     // persistent grid: SMs x resident blocks per SM
 };
-int batch_plume_occupancy(bool fp64, int block);
+int batch_plume_occupancy(bool fp64, int block, int max_pver);
 cudaError_t launch_batch(const BatchDev& b, const BatchShape& sh, bool fp64, void* ws,
                          size_t ws_bytes, cudaStream_t s, cudaEvent_t* ev);
 

@@ -7,6 +7,8 @@
 // not call cudaMalloc because it can synchronise the device or is not allowed
 // while a stream is being captured.  Such callers still pass their inputs and
 // outputs; only the scratch comes from here.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "compact.h"
@@ -23,22 +25,65 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct Cached {
+  void* ptr;
+  unsigned long long ctx_id;  // the context the address belongs to (0: unknown)
+};
+Cached g_cache[kMaxDevices] = {};
 
-// Device address of g_scratch on the current device.  In host code the symbol
-// is only a host-side stand-in, so the address is looked up once per device
-// (with that device current) and cached.
+// The current context's process-unique id, through driver entry points the
+// runtime hands out (the library does not link the driver library itself);
+// 0 if the driver cannot say.  A device reset or a destroyed and re-created
+// context gives a new id, so an address cached for the old one is not reused.
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault,
+                                         &q1) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrent>(f1);
+      get_id = reinterpret_cast<GetId>(f2);
+    }
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of g_scratch in the current device's context.  In host code
+// the symbol is only a host-side stand-in, so the address is looked up with
+// that device current and cached per device together with the context it
+// belongs to; a different context (after a device reset) is looked up anew.
 conv_status scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CONV_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return CONV_ERR_UNSUPPORTED;
+  // make the device's primary context current on this thread (initialising it
+  // if needed; no allocation), so that it has an id to compare
+  if (cudaSetDevice(dev) != cudaSuccess) return CONV_ERR_CUDA;
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  Cached& c = g_cache[dev];
+  if (!c.ptr || id == 0 || c.ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return CONV_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
+    c.ptr = p;
+    c.ctx_id = id;
   }
-  *out = g_scratch_ptr[dev];
+  *out = c.ptr;
   return CONV_OK;
 }
 

@@ -2,7 +2,7 @@
 // and then shallow convection on the deep-updated state (Alg. 1 order).  No
 // compaction: a warp whose columns do not convect still pays for the ones that
 // do, exactly the load imbalance the paper reports for its OpenMP loops
-// (Sec. III-A).
+// (Sec. IV-A).
 #include "launch.h"
 
 namespace cvg {
@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(128, PlainThreads<R>::sm / 128)
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   Column<R> c;
-  init_column(c, a.L, input_src<R>(a, i), a.ps[i]);
+  LevelBuf<R> cbuf;
+  init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
   DeepBound bound;
   bool bound_ok = false;
   if (a.mode & MODE_DEEP) {

@@ -1,6 +1,6 @@
 """The multi-step column driver on the GPU (conv_deep_shallow_run +
 conv_advance): the FP64 driver against the oracle's stepping, and the error
-growth test of the paper's correctness method (Sec. IV, after Rosinski and
+growth test of the paper's correctness method (Sec. V-B, after Rosinski and
 Williamson): the RMS temperature difference between the mixed-precision driver
 and the FP64 driver over a 2-day run (96 steps of 1800 s) must stay within the
 curve of the FP64 driver with inputs perturbed in their last FP32 bit, the
