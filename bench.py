@@ -378,19 +378,20 @@ def ours_arm(args, rank, world, local_rank):
 
     preps = {}
 
-    def prepared(grid, prec, path):
+    def prepared(grid, prec, path, mapping="auto"):
         # the step's C-ABI arguments marshalled once (api.PreparedStep): a timed
         # step is one library call, so the loop measures the GPU, not Python
-        key = (grid.name, prec, path)
+        key = (grid.name, prec, path, mapping)
         if key not in preps:
             T, q, ps, od, os_ = setup(grid, prec)
             preps[key] = api.PreparedStep(T, q, ps, api.VerticalGrid(grid.hyai, grid.hybi),
                                           dt=grid.dt, precision=prec, path=path, out_deep=od,
-                                          out_shallow=os_, workspace=ws, stream=stream)
+                                          out_shallow=os_, workspace=ws, stream=stream,
+                                          mapping=mapping)
         return preps[key]
 
-    def timed(grid, prec, path, steps, warmup, per_kernel):
-        run = prepared(grid, prec, path)
+    def timed(grid, prec, path, steps, warmup, per_kernel, mapping="auto"):
+        run = prepared(grid, prec, path, mapping)
         for _ in range(warmup):
             run()
         torch.cuda.synchronize()
@@ -453,8 +454,16 @@ def ours_arm(args, rank, world, local_rank):
             actf = int(((setup(gf, prec)[3]["flags"] & 2) > 0).sum().item())
             sweep.append({"convecting_fraction": f, "ms_per_step": msf, "kern_ms": kf,
                           "deep_active_columns": actf, "columns": gf.n_cols})
-            del bufs[(gf.name, prec)], preps[(gf.name, prec, path)]
+            del bufs[(gf.name, prec)], preps[(gf.name, prec, path, "auto")]
             torch.cuda.empty_cache()
+
+    # the trigger pass's other mapping (one column per warp) on the same step
+    alt = None
+    if path == "compact" and not args.no_sweep:
+        msw, kw_ = timed(g, prec, path, args.steps, args.warmup, True, mapping="warp")
+        alt = {"thread_per_column": {"ms_per_step": ms, "k_trigger_ms": kern[0]},
+               "warp_per_column": {"ms_per_step": msw, "k_trigger_ms": kw_[0]},
+               "chosen": "thread_per_column" if ms <= msw else "warp_per_column"}
 
     # end to end through the public API from pinned host buffers: the host
     # pipeline (conv_pipeline_run) copies the inputs in, runs the fused step and
@@ -551,6 +560,7 @@ def ours_arm(args, rank, world, local_rank):
             "baseline_fp64_plain": base,
             "speedup_vs_fp64_plain": (value / base["value"]) if base else None,
             "roofline": roof, "kernels": kernels, "convecting_fraction_sweep": sweep,
+            "trigger_mapping": alt,
             "batched_ensemble": ens, "deep_adjoint": adj,
             "tracer_transport": trn, "column_driver": drv,
             "cpu_baseline": cpu, "e2e": e2e,
@@ -581,6 +591,7 @@ def ensemble_bench(args, dev, rates=None):
                         dt=g.dt))
     b = api.Batch(mem, "mixed", device=dev)
     cfg = b.autotune(reps=2)
+    tune = b.tune_record()
     b.ws.get(b.workspace_bytes())
     s = torch.cuda.Stream(dev)
     s.wait_stream(torch.cuda.current_stream(dev))
@@ -655,7 +666,7 @@ def ensemble_bench(args, dev, rates=None):
     return {"members": len(ens), "columns": total, "levels": sorted({g.pver for g in ens}),
             "deep_active_columns": active, "precision": "mixed", "ms_per_step": ms,
             "value": total / (ms * 1e-3), "unit": UNIT, "launch": "CUDA graph replay",
-            "autotuned_shape": cfg, "gpu_launches_per_step": 2,
+            "autotuned_shape": cfg, "autotune_ms_per_run": tune, "gpu_launches_per_step": 2,
             "members_one_after_another_ms": ms_sep, "roofline": roof}
 
 

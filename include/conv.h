@@ -229,15 +229,23 @@ typedef struct {
  * one atomic per warp) and plume passes run only over the queues.  AUTO is
  * COMPACT for runs that include the deep scheme, PLAIN for shallow-only runs.
  * block_threads 0 = library default.
+ * mapping (compacted path): how the trigger pass maps columns to threads --
+ * CONV_MAP_THREAD one column per thread (the default, also for 0), or
+ * CONV_MAP_WARP one column per warp, lane k taking level k (the level-parallel
+ * parts of the pass at once: prologue, height scan, launch-level reduction, the
+ * undilute parcel's inversions; measured slower on the benchmark grid, kept as
+ * the autotuner's alternative).  Results agree to rounding: FP64 decisions and
+ * outputs as the thread mapping's within the parity tolerances.
  * stage_events (optional, may be NULL): three caller-created cudaEvent_t the
  * library records on `stream` -- [0] before its first kernel, [1] after the
  * trigger pass (plain path: after its only kernel), [2] after its last kernel
  * -- so a caller can time each pass; recording changes no work. */
 typedef enum { CONV_PATH_AUTO = 0, CONV_PATH_PLAIN = 1, CONV_PATH_COMPACT = 2 } conv_path;
+typedef enum { CONV_MAP_DEFAULT = 0, CONV_MAP_THREAD = 1, CONV_MAP_WARP = 2 } conv_mapping;
 typedef struct {
   int32_t path;
   int32_t block_threads;
-  int32_t reserved0;
+  int32_t mapping; /* conv_mapping */
   int32_t reserved1;
   void* const* stage_events;
 } conv_launch;
@@ -468,16 +476,32 @@ size_t conv_batch_workspace_bytes(const conv_batch* b);
 conv_status conv_batch_run(const conv_batch* b, void* ws, size_t ws_bytes, conv_stream stream,
                            void* const* stage_events);
 
-/* Time candidate launch shapes (trigger block 64/128/256, then plume block
- * 64/128/256 with its persistent grid) on this plan's own data, `reps` runs each
- * after one warm-up, keep the fastest in the plan and in the process-wide cache.
- * Synchronises `stream`; not capturable.  Outputs hold the last run's results. */
+/* Time candidate launch shapes on this plan's own data -- the trigger pass with
+ * one column per thread in blocks of 64/128/256 and with one column per warp
+ * (CONV_MAP_WARP), then the plume pass in blocks of 64/128/256 with its
+ * persistent grid -- `reps` runs each after one warm-up, keep the fastest in
+ * the plan and in the process-wide cache.  Synchronises `stream`; not
+ * capturable.  Outputs hold the last run's results. */
 conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_stream stream,
                                 int reps);
 
-/* Launch shape currently chosen (any pointer may be NULL). */
+/* Launch shape currently chosen (any pointer may be NULL); trigger_mapping is a
+ * conv_mapping (CONV_MAP_THREAD or CONV_MAP_WARP). */
 conv_status conv_batch_config(const conv_batch* b, int32_t* trigger_block, int32_t* plume_block,
-                              int32_t* plume_grid);
+                              int32_t* plume_grid, int32_t* trigger_mapping);
+
+/* Set the launch shape by hand: trigger_mapping CONV_MAP_THREAD or
+ * CONV_MAP_WARP, trigger_block and plume_block 64, 128 or 256 (the plume pass's
+ * persistent grid follows from its block and this device's occupancy).
+ * CONV_ERR_ARG for other values. */
+conv_status conv_batch_set_config(conv_batch* b, int32_t trigger_mapping, int32_t trigger_block,
+                                  int32_t plume_block);
+
+/* The last autotune's measurements, ms per batched run: ms[0..2] trigger blocks
+ * 64/128/256 (one column per thread), ms[3] one column per warp, ms[4..6] plume
+ * blocks 64/128/256 (each with the best trigger shape); ms holds 7 floats.
+ * CONV_ERR_ARG if the plan has not been autotuned. */
+conv_status conv_batch_tune_record(const conv_batch* b, float* ms);
 
 /* Release the plan and its device descriptor table (NULL is a no-op). */
 void conv_batch_free(conv_batch* b);

@@ -15,6 +15,7 @@ CONV_OK, CONV_ERR_ARG, CONV_ERR_CUDA, CONV_ERR_WORKSPACE, CONV_ERR_UNSUPPORTED, 
     CONV_ERR_TIMEOUT = range(6)
 CONV_FP64, CONV_MIXED = 0, 1
 CONV_PATH_AUTO, CONV_PATH_PLAIN, CONV_PATH_COMPACT = 0, 1, 2
+CONV_MAP_DEFAULT, CONV_MAP_THREAD, CONV_MAP_WARP = 0, 1, 2
 FLAG_TRIGGERED, FLAG_ACTIVE, FLAG_LIMITED, FLAG_NEWTON, FLAG_BADINPUT = 1, 2, 4, 8, 16
 EXIT_SHIFT = 8
 MAX_LEVELS = 32
@@ -64,7 +65,7 @@ class Out(C.Structure):
 
 
 class Launch(C.Structure):
-    _fields_ = [("path", C.c_int32), ("block_threads", C.c_int32), ("reserved0", C.c_int32),
+    _fields_ = [("path", C.c_int32), ("block_threads", C.c_int32), ("mapping", C.c_int32),
                 ("reserved1", C.c_int32), ("stage_events", C.POINTER(C.c_void_p))]
 
 
@@ -117,7 +118,7 @@ def lib(build: bool = True):
     L.conv_batch_run.restype = st
     L.conv_batch_autotune.argtypes = [vp, vp, C.c_size_t, vp, st]
     L.conv_batch_autotune.restype = st
-    L.conv_batch_config.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.conv_batch_config.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_int32), P(C.c_int32)]
     L.conv_batch_config.restype = st
     L.conv_batch_free.argtypes = [vp]
     L.conv_batch_free.restype = None
@@ -141,6 +142,10 @@ def lib(build: bool = True):
                                     P(Out), vp]
     L.conv_pipeline_run.restype = st
     L.conv_pipeline_free.argtypes = [vp]
+    L.conv_batch_set_config.argtypes = [vp, C.c_int32, C.c_int32, C.c_int32]
+    L.conv_batch_set_config.restype = st
+    L.conv_batch_tune_record.argtypes = [vp, vp]
+    L.conv_batch_tune_record.restype = st
     L.conv_count_triggered.argtypes = [vp, C.c_int32, C.c_int32, vp, vp]
     L.conv_count_triggered.restype = st
     L.conv_partition_columns.argtypes = [C.c_int32, C.c_int32, vp, d, d, C.c_int32, vp]

@@ -93,8 +93,14 @@ class VerticalGrid:
                       self.hybi.ctypes.data_as(dp), self.p0)
 
 
-def _launch(path: str, block_threads: int = 0, stage_events=None) -> L.Launch:
-    lc = L.Launch(_PATH[path], int(block_threads), 0, 0, None)
+_MAP = {"auto": L.CONV_MAP_DEFAULT, "thread": L.CONV_MAP_THREAD, "warp": L.CONV_MAP_WARP}
+
+
+def _launch(path: str, block_threads: int = 0, stage_events=None,
+            mapping: str = "auto") -> L.Launch:
+    if mapping not in _MAP:
+        raise ValueError(f"mapping must be one of {list(_MAP)}")
+    lc = L.Launch(_PATH[path], int(block_threads), _MAP[mapping], 0, None)
     if stage_events is not None:
         if len(stage_events) != 3:
             raise ValueError("stage_events needs three torch.cuda.Event")
@@ -198,14 +204,16 @@ def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision
                  lam=None, tau=None, deep_params=None, shallow_params=None, path="auto",
                  block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
                  workspace: Workspace | None = None, stream=None, stage_events=None,
-                 col0: int = 0):
+                 col0: int = 0, mapping: str = "auto"):
     """Deep then shallow convection (Alg. 1 order) in one fused call.
 
     Returns ``(deep_out, shallow_out)`` dicts of output tensors.  stage_events:
     optional three torch.cuda.Event the library records around its passes.
     col0: first column of the range processed (columns col0 .. col0 + n_cols - 1
     of every [pver, ld] / [ld] tensor; n_cols defaults to the rest of ld); the
-    other columns of the outputs are left untouched."""
+    other columns of the outputs are left untouched.  mapping: the compacted
+    trigger pass's mapping, "thread" (one column per thread, the default for
+    "auto") or "warp" (one column per warp, lane k = level k)."""
     pver, ld, n, inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
     col0 = int(col0)
     if n_cols is None:
@@ -217,7 +225,7 @@ def deep_shallow(T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0, precision
     dp = deep_params or L.deep_defaults()
     sp = shallow_params or L.shallow_defaults()
     g = vgrid.struct(n, ld)
-    lc = _launch(path, block_threads, stage_events)
+    lc = _launch(path, block_threads, stage_events, mapping)
     nb = int(L.lib().conv_workspace_bytes(C.byref(g), _PREC[precision], C.byref(lc)))
     wp, wn = _ws_for(T.device, workspace).get(nb)
     so_d = _out_struct(od, pver, ld, precision)
@@ -243,7 +251,7 @@ class PreparedStep:
     def __init__(self, T, q, ps, vgrid: VerticalGrid, *, dt: float = 1800.0,
                  precision="fp64", lam=None, tau=None, deep_params=None, shallow_params=None,
                  path="auto", block_threads=0, n_cols=None, out_deep=None, out_shallow=None,
-                 workspace: Workspace | None = None, stream=None):
+                 workspace: Workspace | None = None, stream=None, mapping: str = "auto"):
         pver, ld, n, self._inp = _common(T, q, ps, vgrid, n_cols, precision, lam, tau)
         self.out_deep = out_deep if out_deep is not None else new_outputs(pver, ld, precision,
                                                                           T.device)
@@ -253,8 +261,8 @@ class PreparedStep:
         self._dp = deep_params or L.deep_defaults()
         self._sp = shallow_params or L.shallow_defaults()
         self._g = vgrid.struct(n, ld)
-        self._path, self._block = path, int(block_threads)
-        lc = _launch(path, block_threads)
+        self._path, self._block, self._mapping = path, int(block_threads), mapping
+        lc = _launch(path, block_threads, mapping=mapping)
         nb = int(L.lib().conv_workspace_bytes(C.byref(self._g), _PREC[precision], C.byref(lc)))
         self._ws = _ws_for(T.device, workspace)
         self._wp, self._wn = self._ws.get(nb)
@@ -269,7 +277,7 @@ class PreparedStep:
 
     def launch_struct(self, stage_events=None) -> L.Launch:
         """A launch descriptor with stage events, to build outside a timed loop."""
-        return _launch(self._path, self._block, stage_events)
+        return _launch(self._path, self._block, stage_events, self._mapping)
 
     def __call__(self, launch: L.Launch | None = None):
         st = self._fn(*self._args, C.byref(launch if launch is not None else self._lc),
@@ -469,10 +477,27 @@ class Batch:
         return self.config()
 
     def config(self):
-        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
-        L.check(L.lib().conv_batch_config(self._h, C.byref(a), C.byref(b), C.byref(c)),
-                "conv_batch_config")
-        return {"trigger_block": a.value, "plume_block": b.value, "plume_grid": c.value}
+        a, b, c, m = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        L.check(L.lib().conv_batch_config(self._h, C.byref(a), C.byref(b), C.byref(c),
+                                          C.byref(m)), "conv_batch_config")
+        return {"trigger_mapping": "warp" if m.value == L.CONV_MAP_WARP else "thread",
+                "trigger_block": a.value, "plume_block": b.value, "plume_grid": c.value}
+
+    def set_config(self, trigger_mapping="thread", trigger_block=128, plume_block=128):
+        """Choose the launch shape by hand (see conv_batch_set_config)."""
+        m = {"thread": L.CONV_MAP_THREAD, "warp": L.CONV_MAP_WARP}[trigger_mapping]
+        L.check(L.lib().conv_batch_set_config(self._h, m, int(trigger_block), int(plume_block)),
+                "conv_batch_set_config")
+        return self.config()
+
+    def tune_record(self):
+        """The last autotune's ms per run of each candidate shape."""
+        ms = (C.c_float * 7)()
+        L.check(L.lib().conv_batch_tune_record(self._h, ms), "conv_batch_tune_record")
+        v = list(ms)
+        return {"trigger_thread_block_64": v[0], "trigger_thread_block_128": v[1],
+                "trigger_thread_block_256": v[2], "trigger_warp_per_column": v[3],
+                "plume_block_64": v[4], "plume_block_128": v[5], "plume_block_256": v[6]}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -94,6 +94,7 @@ cudaError_t launch_step_adjoint(const RunArgs& a, const double* const g[4], cons
                                 double* gT, double* gq, double* glam, double* gtau, double* obj,
                                 bool rev) {
   if (a.n == 0) return cudaSuccess;
+  NvtxRange r("conv: fused-step adjoint");
   StepArgs A{a, {g[0], g[1], g[2], g[3]}, w, gT, gq, glam, gtau, obj, rev};
   const int block = 64;
   k_step_adjoint<<<(a.n + block - 1) / block, block, 0, a.stream>>>(A);
@@ -104,6 +105,7 @@ cudaError_t launch_deep_adjoint(const RunArgs& a, const double* gP, const double
                                 const AdjW& w, double* gT, double* gq, double* glam,
                                 double* gtau, double* Pout, double* Hout) {
   if (a.n == 0) return cudaSuccess;
+  NvtxRange r("conv: deep adjoint");
   AdjArgs A{a, gP, gH, w, gT, gq, glam, gtau, Pout, Hout};
   const int block = 64;
   k_deep_adjoint<<<(a.n + block - 1) / block, block, 0, a.stream>>>(A);

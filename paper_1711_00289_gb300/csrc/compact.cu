@@ -79,11 +79,28 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
     w.levels[slot] = t.kb | (t.klcl << 8) | (t.kel << 16);
     w.cape[slot] = t.cape;
     store_deep_scalars(a, i, o);  // scalars now; tendencies and the rest in the plume pass
+    if constexpr (kThreePass) w.s_info[tag] = kShalTriggered;
     return;
   }
   out_col<R, EXT>(a.od, a, i).zero(0, c.pver);
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW)) return;
+  if constexpr (kThreePass) {
+    // the shallow pass runs later: hand it what it can reuse
+    int info = 0;
+    if (valid) {
+      const bool same_src = t.kb == c.pver - 1 && a.sp.p_top_lim == a.dp.p_top_lim &&
+                            a.sp.n_newton_lcl == a.dp.n_newton_lcl &&
+                            a.sp.n_newton_h == a.dp.n_newton_h && t.klcl >= c.ktl;
+      info = kShalValid | (same_src ? kShalSameSrc : 0) | (t.pL_exact ? kShalExact : 0) |
+             (t.newton <= Mth<R>::newton_tol ? kShalBoundOk : 0) | ((t.klcl & 0xff) << 8) |
+             ((c.ktl & 0xff) << 16);
+      w.s_pL[tag] = t.pL;
+      w.s_buoy[tag] = t.maybe_buoy;
+    }
+    w.s_info[tag] = info;
+    return;
+  }
   ShalOut s;
   const auto so = out_col<R, EXT>(a.os, a, i);
   if (!valid) {
@@ -144,7 +161,7 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   deep_plume(c, a.dp, Q, lam, tau, t, o, out_col<R, EXT>(a.od, a, i));
   if (t.newton > Mth<R>::newton_tol) o.flags |= CONV_FLAG_NEWTON;
   store_deep_scalars(a, i, o);
-  if (!(a.mode & MODE_SHALLOW)) return;
+  if (!(a.mode & MODE_SHALLOW) || kThreePass) return;
   c.s = after_deep_src<R>(a, i, false);  // limiter keeps q >= q_min up to rounding
   ShalOut s;
   shallow_column(a.sp, shal_q(a, R(0)), c, s, out_col<R, EXT>(a.os, a, i));
@@ -158,6 +175,45 @@ __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactB
   if (slot >= *w.count) return;
   const int i = w.queue[slot];
   plume_body<R, EXT, SmemLevels<R>::on>(a, w, slot, i, i);
+}
+
+// Shallow pass of the three-pass layout (column i, workspace index tag): a
+// triggered column on its deep-updated state; a column the deep scheme left as
+// it was on its own state, reusing the deep trigger's LCL and parcel (when its
+// launch layer is the lowest) and its buoyancy bound, as the trigger pass would.
+template <class R, bool EXT = false>
+__device__ __forceinline__ void shallow_body(const RunArgs& a, const CompactWs<R>& w, int i,
+                                             int tag) {
+  const int info = w.s_info[tag];
+  Column<R> c;
+  LevelBuf<R> cbuf;
+  ShalOut s;
+  const auto so = out_col<R, EXT>(a.os, a, i);
+  const ShalQ<R>& SQ = shal_q(a, R(0));
+  if (info & kShalTriggered) {
+    init_column(c, a.L, after_deep_src<R>(a, i, false), a.ps[i], cbuf);
+    shallow_column(a.sp, SQ, c, s, so);
+  } else if (!(info & kShalValid)) {
+    init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
+    shallow_column(a.sp, SQ, c, s, so);  // flags the column as bad input
+  } else {
+    init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
+    prologue(SQ.p_top_lim, c);
+    const int klcl = (info >> 8) & 0xff;
+    const ShallowSeed<R> seed{w.s_pL[tag], klcl, (info & kShalExact) != 0, w.Tp + tag,
+                              (size_t)w.cap};
+    const DeepBound bound{klcl, (info >> 16) & 0xff, w.s_buoy[tag]};
+    shallow_column(a.sp, SQ, c, s, so, (info & kShalSameSrc) ? &seed : nullptr, true,
+                   (info & kShalBoundOk) ? &bound : nullptr);
+  }
+  store_shallow_scalars(a, i, s);
+}
+
+template <class R, bool EXT>
+__global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::shallow / kCompactBlock)
+    k_shallow(const __grid_constant__ RunArgs a, CompactWs<R> w) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.n) shallow_body<R, EXT>(a, w, i, i);
 }
 
 // The compacted kernels that keep level arrays in shared memory ask for the
@@ -197,6 +253,9 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   w.levels = reinterpret_cast<int*>(base + off.levels);
   w.cape = reinterpret_cast<double*>(base + off.cape);
   w.Tp = reinterpret_cast<R*>(base + off.Tp);
+  w.s_pL = reinterpret_cast<double*>(base + off.s_pL);
+  w.s_buoy = reinterpret_cast<uint32_t*>(base + off.s_buoy);
+  w.s_info = reinterpret_cast<int32_t*>(base + off.s_info);
   w.cap = a.n;
   record_stage(a, 0);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
@@ -204,18 +263,35 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
   const size_t sm = smem_levels_bytes<R>(a.L.pver, kCompactBlock);
   prefer_shared<R>();
-  if (a.ext)
-    k_trigger<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
-  else
-    k_trigger<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
-  e = cudaGetLastError();
+  if (a.mapping == CONV_MAP_WARP) {
+    e = launch_trigger_warp(a, w);
+  } else {
+    NvtxRange r("conv: trigger pass (all columns)");
+    if (a.ext)
+      k_trigger<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+    else
+      k_trigger<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) return e;
   record_stage(a, 1);
-  if (a.ext)
-    k_plume<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
-  else
-    k_plume<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+  {
+    NvtxRange r("conv: plume pass (queued columns)");
+    if (a.ext)
+      k_plume<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+    else
+      k_plume<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+  }
   e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (kThreePass && (a.mode & MODE_SHALLOW)) {
+    NvtxRange r("conv: shallow pass (all columns)");
+    if (a.ext)
+      k_shallow<R, true><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+    else
+      k_shallow<R, false><<<grid, kCompactBlock, 0, a.stream>>>(a, w);
+    e = cudaGetLastError();
+  }
   record_stage(a, 2);
   return e;
 }
@@ -288,6 +364,15 @@ static void batch_smem_setup() {
 }
 
 template <class R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, SmThreads<R>::shallow / BLOCK)
+    k_batch_shallow(BatchDev b, CompactWs<R> w) {
+  const int g = blockIdx.x * BLOCK + threadIdx.x;
+  if (g >= b.total) return;
+  const int m = find_member(b.offsets, b.n_members, g);
+  if (b.members[m].mode & MODE_SHALLOW) shallow_body<R>(b.members[m], w, g - b.offsets[m], g);
+}
+
+template <class R, int BLOCK>
 static int plume_occupancy(int max_pver) {
   batch_smem_setup<R, BLOCK>();
   int blocks = 0;
@@ -337,14 +422,22 @@ static cudaError_t batch_t(const BatchDev& b, const BatchShape& sh, void* ws, si
   w.levels = reinterpret_cast<int*>(base + off.levels);
   w.cape = reinterpret_cast<double*>(base + off.cape);
   w.Tp = reinterpret_cast<R*>(base + off.Tp);
+  w.s_pL = reinterpret_cast<double*>(base + off.s_pL);
+  w.s_buoy = reinterpret_cast<uint32_t*>(base + off.s_buoy);
+  w.s_info = reinterpret_cast<int32_t*>(base + off.s_info);
   w.cap = b.total;
+  NvtxRange r("conv: batched run (trigger + persistent plume pass)");
   if (ev && ev[0]) cudaEventRecord(ev[0], s);
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  switch (sh.trigger_block) {
-    case 64: launch_trig<R, 64>(b, w, sh.max_pver, s); break;
-    case 256: launch_trig<R, 256>(b, w, sh.max_pver, s); break;
-    default: launch_trig<R, 128>(b, w, sh.max_pver, s); break;
+  if (sh.trigger_mapping == 1) {
+    launch_batch_trigger_warp(b, w, s);
+  } else {
+    switch (sh.trigger_block) {
+      case 64: launch_trig<R, 64>(b, w, sh.max_pver, s); break;
+      case 256: launch_trig<R, 256>(b, w, sh.max_pver, s); break;
+      default: launch_trig<R, 128>(b, w, sh.max_pver, s); break;
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -355,6 +448,10 @@ static cudaError_t batch_t(const BatchDev& b, const BatchShape& sh, void* ws, si
     default: launch_plume<R, 128>(b, w, sh.plume_grid, sh.max_pver, s); break;
   }
   e = cudaGetLastError();
+  if (kThreePass && e == cudaSuccess) {
+    k_batch_shallow<R, 128><<<(b.total + 127) / 128, 128, 0, s>>>(b, w);
+    e = cudaGetLastError();
+  }
   if (ev && ev[2]) cudaEventRecord(ev[2], s);
   return e;
 }

@@ -30,13 +30,27 @@ constexpr int kCompactBlock = 128;
 #ifndef CVG_SMEM_LEVELS
 #define CVG_SMEM_LEVELS 0
 #endif
+#ifndef CVG_SHALLOW_SM_THREADS
+#define CVG_SHALLOW_SM_THREADS 1408
+#endif
 template <class R>
 struct SmThreads {
-  static constexpr int trigger = 896, plume = 896;
+  static constexpr int trigger = 896, plume = 896, shallow = 896;
 };
 template <>
 struct SmThreads<float> {
-  static constexpr int trigger = CVG_TRIGGER_SM_THREADS, plume = CVG_PLUME_SM_THREADS;
+  static constexpr int trigger = CVG_TRIGGER_SM_THREADS, plume = CVG_PLUME_SM_THREADS,
+                       shallow = CVG_SHALLOW_SM_THREADS;
+};
+
+// ShalInfo: what the three-pass trigger pass hands the shallow pass per column.
+enum : int {
+  kShalTriggered = 1,  // the deep scheme triggered: shallow on the updated state
+  kShalValid = 2,      // valid input (otherwise the shallow pass flags bad input)
+  kShalSameSrc = 4,    // the deep launch layer is the shallow source: reuse its LCL, parcel
+  kShalExact = 8,      // the deep p_L is the FP64 value
+  kShalBoundOk = 16    // the deep trigger converged: its buoyancy bound holds
+  // bits 8-15: the deep parcel's LCL layer; bits 16-23: the deep top limit
 };
 
 // Where the compacted kernels keep each column's mid-layer heights and layer
@@ -65,6 +79,11 @@ inline size_t smem_levels_bytes(int pver, int block) {
 //   Tp     R[pver][n] undilute parcel temperature on ktl..klcl, by column (the
 //                     trigger pass writes it for every column with a parcel)
 // (n = queue capacity: the columns of the run, or of all members of a batch)
+#ifndef CVG_THREE_PASS
+#define CVG_THREE_PASS 0
+#endif
+constexpr bool kThreePass = CVG_THREE_PASS != 0;
+
 template <class R>
 struct CompactWs {
   int* count;
@@ -73,10 +92,14 @@ struct CompactWs {
   double* cape;
   R* Tp;
   int cap;  // queue capacity (columns); row stride of Tp
+  // three-pass layout: what the shallow pass takes from the trigger pass, by column
+  double* s_pL;     // deep LCL pressure
+  uint32_t* s_buoy; // DeepTrig::maybe_buoy
+  int32_t* s_info;  // packed flags and levels (ShalInfo)
 };
 
 struct WsOffsets {
-  size_t count, queue, levels, cape, Tp, total;
+  size_t count, queue, levels, cape, Tp, s_pL, s_buoy, s_info, total;
 };
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -89,7 +112,10 @@ inline WsOffsets ws_offsets(int n, int pver, size_t real_bytes) {
   o.levels = o.queue + align256(4 * nn);
   o.cape = o.levels + align256(4 * nn);
   o.Tp = o.cape + align256(8 * nn);
-  o.total = o.Tp + align256(real_bytes * (size_t)pver * nn);
+  o.s_pL = o.Tp + align256(real_bytes * (size_t)pver * nn);
+  o.s_buoy = o.s_pL + (kThreePass ? align256(8 * nn) : 0);
+  o.s_info = o.s_buoy + (kThreePass ? align256(4 * nn) : 0);
+  o.total = o.s_info + (kThreePass ? align256(4 * nn) : 0);
   return o;
 }
 
@@ -107,11 +133,19 @@ struct BatchDev {
 // Launch shape chosen by the plan (and the autotuner).
 struct BatchShape {
   int max_pver;
+  int trigger_mapping;  // 0: one column per thread; 1: one column per warp
   int trigger_block;  // 64, 128 or 256
   int plume_block;    // 64, 128 or 256
   int plume_grid;     // persistent grid: SMs x resident blocks per SM
 };
 int batch_plume_occupancy(bool fp64, int block, int max_pver);
+// The trigger pass with one column per warp (warp.cu).
+cudaError_t launch_trigger_warp(const RunArgs& a, const CompactWs<float>& w);
+cudaError_t launch_trigger_warp(const RunArgs& a, const CompactWs<double>& w);
+cudaError_t launch_batch_trigger_warp(const BatchDev& b, const CompactWs<float>& w,
+                                      cudaStream_t s);
+cudaError_t launch_batch_trigger_warp(const BatchDev& b, const CompactWs<double>& w,
+                                      cudaStream_t s);
 cudaError_t launch_batch(const BatchDev& b, const BatchShape& sh, bool fp64, void* ws,
                          size_t ws_bytes, cudaStream_t s, cudaEvent_t* ev);
 

@@ -116,12 +116,15 @@ conv_status dispatch(RunArgs& a, conv_precision prec, const conv_launch* launch,
   if (launch && (launch->path < CONV_PATH_AUTO || launch->path > CONV_PATH_COMPACT))
     return CONV_ERR_ARG;
   if (launch && (launch->block_threads < 0 || launch->block_threads > 1024)) return CONV_ERR_ARG;
+  if (launch && (launch->mapping < CONV_MAP_DEFAULT || launch->mapping > CONV_MAP_WARP))
+    return CONV_ERR_ARG;
   const int path = pick_path(launch, a.mode);
   const bool spectrum = (a.mode & cvg::MODE_DEEP) && a.dp.n_plumes > 1;
   if (spectrum && (has_flux(a.od) || has_flux(a.os))) return CONV_ERR_UNSUPPORTED;
   a.ext = has_flux(a.od) || has_flux(a.os) || ((a.mode & cvg::MODE_SHALLOW) && a.sp.evap_k > 0.0) ||
           spectrum;
   a.block = launch ? launch->block_threads : 0;
+  a.mapping = launch ? launch->mapping : CONV_MAP_DEFAULT;
   for (int i = 0; i < 3; ++i)
     a.ev[i] = (launch && launch->stage_events)
                   ? static_cast<cudaEvent_t>(launch->stage_events[i])
@@ -437,6 +440,8 @@ struct conv_batch {
   int total;
   int sms;
   cvg::BatchShape shape;
+  float tune_ms[7];  // the last autotune's measurements (conv_batch_tune_record)
+  bool tuned;
   cvg::RunArgs* d_members;
   int* d_offsets;
   std::vector<int> h_offsets;
@@ -452,6 +457,7 @@ std::map<std::pair<int, int>, int> g_last_bucket;  // (prec, pver) -> last measu
 cvg::BatchShape default_shape(bool fp64, int max_pver, int sms) {
   cvg::BatchShape sh;
   sh.max_pver = max_pver;
+  sh.trigger_mapping = 0;
   sh.trigger_block = 128;
   sh.plume_block = 128;
   sh.plume_grid = sms * cvg::batch_plume_occupancy(fp64, 128, max_pver);
@@ -578,22 +584,26 @@ conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_s
   cvg::BatchShape best = b->shape;
   float best_ms = 1e30f;
   cudaError_t err = cudaSuccess;
-  for (int tb : kBlocks) {
+  float rec[7] = {0.f};
+  for (int j = 0; j < 4 && err == cudaSuccess; ++j) {  // trigger: 3 block sizes, warp mapping
     cvg::BatchShape sh = best;
-    sh.trigger_block = tb;
+    sh.trigger_mapping = j == 3 ? 1 : 0;
+    if (j < 3) sh.trigger_block = kBlocks[j];
     float ms = 0.f;
     err = time_shape(sh, &ms);
     if (err != cudaSuccess) break;
+    rec[j] = ms / reps;
     if (ms < best_ms) { best_ms = ms; best = sh; }
   }
-  for (int pb : kBlocks) {
-    if (err != cudaSuccess) break;
+  for (int j = 0; j < 3 && err == cudaSuccess; ++j) {
+    const int pb = kBlocks[j];
     cvg::BatchShape sh = best;
     sh.plume_block = pb;
     sh.plume_grid = b->sms * cvg::batch_plume_occupancy(fp64, pb, best.max_pver);
     float ms = 0.f;
     err = time_shape(sh, &ms);
     if (err != cudaSuccess) break;
+    rec[4 + j] = ms / reps;
     if (ms < best_ms) { best_ms = ms; best = sh; }
   }
   int count = 0;
@@ -606,6 +616,8 @@ conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_s
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return CONV_ERR_CUDA;
   b->shape = best;
+  for (int j = 0; j < 7; ++j) b->tune_ms[j] = rec[j];
+  b->tuned = true;
   const int bucket = b->total > 0 ? (int)(10.0 * count / b->total) : 0;
   std::lock_guard<std::mutex> lock(g_tune_mu);
   g_tune_cache[std::make_tuple((int)b->prec, best.max_pver, bucket)] = best;
@@ -613,9 +625,30 @@ conv_status conv_batch_autotune(conv_batch* b, void* ws, size_t ws_bytes, conv_s
   return CONV_OK;
 }
 
+conv_status conv_batch_set_config(conv_batch* b, int32_t trigger_mapping, int32_t trigger_block,
+                                  int32_t plume_block) {
+  auto ok_block = [](int32_t x) { return x == 64 || x == 128 || x == 256; };
+  if (!b || (trigger_mapping != CONV_MAP_THREAD && trigger_mapping != CONV_MAP_WARP) ||
+      !ok_block(trigger_block) || !ok_block(plume_block))
+    return CONV_ERR_ARG;
+  const bool fp64 = b->prec == CONV_FP64;
+  b->shape.trigger_mapping = trigger_mapping == CONV_MAP_WARP ? 1 : 0;
+  b->shape.trigger_block = trigger_block;
+  b->shape.plume_block = plume_block;
+  b->shape.plume_grid = b->sms * cvg::batch_plume_occupancy(fp64, plume_block, b->shape.max_pver);
+  return CONV_OK;
+}
+
+conv_status conv_batch_tune_record(const conv_batch* b, float* ms) {
+  if (!b || !ms || !b->tuned) return CONV_ERR_ARG;
+  for (int j = 0; j < 7; ++j) ms[j] = b->tune_ms[j];
+  return CONV_OK;
+}
+
 conv_status conv_batch_config(const conv_batch* b, int32_t* trigger_block, int32_t* plume_block,
-                              int32_t* plume_grid) {
+                              int32_t* plume_grid, int32_t* trigger_mapping) {
   if (!b) return CONV_ERR_ARG;
+  if (trigger_mapping) *trigger_mapping = b->shape.trigger_mapping ? CONV_MAP_WARP : CONV_MAP_THREAD;
   if (trigger_block) *trigger_block = b->shape.trigger_block;
   if (plume_block) *plume_block = b->shape.plume_block;
   if (plume_grid) *plume_grid = b->shape.plume_grid;

@@ -3,12 +3,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 
 #include "column.cuh"
 
 namespace cvg {
+
+// A named NVTX range around the host-side enqueue of one pass (what Nsight
+// Systems shows beside the kernels; without a tool attached the calls return
+// at once).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 enum : int { MODE_DEEP = 1, MODE_SHALLOW = 2 };
 
@@ -49,6 +60,7 @@ struct RunArgs {
   bool ext;  // profile outputs or a scheme variant requested: the extended instantiations
   int mode;
   int block;
+  int mapping;  // conv_mapping of the compacted trigger pass
   cudaStream_t stream;
   cudaEvent_t ev[3];  // optional stage events (nullptr = none)
 };

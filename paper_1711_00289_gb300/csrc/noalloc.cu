@@ -20,7 +20,8 @@ namespace {
 // GPU that loads the library holds it until the process exits.
 constexpr size_t kScratchBytes =
     256 + 4 * CONV_NOALLOC_MAX_COLS + 4 * CONV_NOALLOC_MAX_COLS + 8 * CONV_NOALLOC_MAX_COLS +
-    8 * (size_t)CONV_MAX_LEVELS * CONV_NOALLOC_MAX_COLS;
+    8 * (size_t)CONV_MAX_LEVELS * CONV_NOALLOC_MAX_COLS +
+    (cvg::kThreePass ? (8 + 4 + 4) * (size_t)CONV_NOALLOC_MAX_COLS : 0);
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;

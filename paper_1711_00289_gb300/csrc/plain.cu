@@ -58,6 +58,7 @@ cudaError_t launch_plain(const RunArgs& a, bool fp64) {
   const int block = 128;
   const int grid = (a.n + block - 1) / block;
   record_stage(a, 0);
+  NvtxRange r("conv: plain pass (whole scheme per column)");
   if (fp64) {
     if (a.ext)
       k_plain<double, true><<<grid, block, 0, a.stream>>>(a);

@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(kTrBlock) k_transport(const __grid_constant__ 
 
 cudaError_t launch_transport(const TrArgs& a, bool fp64) {
   if (a.n == 0 || a.ntr == 0) return cudaSuccess;
+  NvtxRange r(a.mom ? "conv: momentum transport" : "conv: tracer transport");
   const int blocks = (a.n + kTrBlock - 1) / kTrBlock;
   const dim3 grid((unsigned)((a.ntr + kTrGroup - 1) / kTrGroup),
                   (unsigned)(blocks < 65535 ? blocks : 65535));

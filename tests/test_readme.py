@@ -1,5 +1,6 @@
-"""The usage shown in README.md stays valid: its Python block compiles and every
-`api.` / `S.` name it uses (code and table) exists in the package."""
+"""The usage the repository's front page shows stays valid: its Python block
+compiles and every `api.` / `S.` name it uses (code and table) exists in the
+package."""
 import os
 import re
 
