@@ -321,7 +321,7 @@ __device__ __forceinline__ int find_member(const int* off, int M, int g) {
 
 template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, SmThreads<R>::trigger / BLOCK)
-    k_batch_trigger(BatchDev b, CompactWs<R> w) {
+    k_batch_trigger(BatchDev b, const RunArgs* __restrict__ members, CompactWs<R> w) {
   const int g = blockIdx.x * BLOCK + threadIdx.x;
   const bool live = g < b.total;
   int m = 0, i = 0;
@@ -329,17 +329,17 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::trigger / BLOCK)
     m = find_member(b.offsets, b.n_members, g);
     i = g - b.offsets[m];
   }
-  trigger_body<R, false, SmemLevels<R>::on>(b.members[m], w, i, live, g);
+  trigger_body<R, false, SmemLevels<R>::on>(members[m], w, i, live, g);
 }
 
 template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
-    k_batch_plume(BatchDev b, CompactWs<R> w) {
+    k_batch_plume(BatchDev b, const RunArgs* __restrict__ members, CompactWs<R> w) {
   const int count = *w.count;
   for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
     const int g = w.queue[slot];
     const int m = find_member(b.offsets, b.n_members, g);
-    plume_body<R, false, SmemLevels<R>::on>(b.members[m], w, slot, g - b.offsets[m], g);
+    plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
   }
 }
 
@@ -365,11 +365,11 @@ static void batch_smem_setup() {
 
 template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, SmThreads<R>::shallow / BLOCK)
-    k_batch_shallow(BatchDev b, CompactWs<R> w) {
+    k_batch_shallow(BatchDev b, const RunArgs* __restrict__ members, CompactWs<R> w) {
   const int g = blockIdx.x * BLOCK + threadIdx.x;
   if (g >= b.total) return;
   const int m = find_member(b.offsets, b.n_members, g);
-  if (b.members[m].mode & MODE_SHALLOW) shallow_body<R>(b.members[m], w, g - b.offsets[m], g);
+  if (members[m].mode & MODE_SHALLOW) shallow_body<R>(members[m], w, g - b.offsets[m], g);
 }
 
 template <class R, int BLOCK>
@@ -401,13 +401,14 @@ static void launch_trig(const BatchDev& b, const CompactWs<R>& w, int max_pver,
                         cudaStream_t s) {
   batch_smem_setup<R, BLOCK>();
   k_batch_trigger<R, BLOCK><<<(b.total + BLOCK - 1) / BLOCK, BLOCK,
-                              smem_levels_bytes<R>(max_pver, BLOCK), s>>>(b, w);
+                              smem_levels_bytes<R>(max_pver, BLOCK), s>>>(b, b.members, w);
 }
 template <class R, int BLOCK>
 static void launch_plume(const BatchDev& b, const CompactWs<R>& w, int grid, int max_pver,
                          cudaStream_t s) {
   batch_smem_setup<R, BLOCK>();
-  k_batch_plume<R, BLOCK><<<grid, BLOCK, smem_levels_bytes<R>(max_pver, BLOCK), s>>>(b, w);
+  k_batch_plume<R, BLOCK><<<grid, BLOCK, smem_levels_bytes<R>(max_pver, BLOCK), s>>>(
+      b, b.members, w);
 }
 
 template <class R>
@@ -449,7 +450,7 @@ static cudaError_t batch_t(const BatchDev& b, const BatchShape& sh, void* ws, si
   }
   e = cudaGetLastError();
   if (kThreePass && e == cudaSuccess) {
-    k_batch_shallow<R, 128><<<(b.total + 127) / 128, 128, 0, s>>>(b, w);
+    k_batch_shallow<R, 128><<<(b.total + 127) / 128, 128, 0, s>>>(b, b.members, w);
     e = cudaGetLastError();
   }
   if (ev && ev[2]) cudaEventRecord(ev[2], s);

@@ -334,13 +334,14 @@ __device__ __forceinline__ int find_member_w(const int* off, int M, int g) {
 }
 
 template <class R>
-__global__ void __launch_bounds__(32 * kWarpCols, 4) k_batch_trigger_warp(BatchDev b, CompactWs<R> w) {
+__global__ void __launch_bounds__(32 * kWarpCols, 4) k_batch_trigger_warp(BatchDev b, const RunArgs* __restrict__ members,
+                                                                      CompactWs<R> w) {
   __shared__ int s_trig[kWarpCols];
   __shared__ int s_base;
   const int g = blockIdx.x * kWarpCols + (threadIdx.x >> 5);
   const bool live = g < b.total;
   const int m = live ? find_member_w(b.offsets, b.n_members, g) : 0;
-  trigger_warp_body<R, false>(b.members[m], w, live ? g - b.offsets[m] : 0, live, g, s_trig,
+  trigger_warp_body<R, false>(members[m], w, live ? g - b.offsets[m] : 0, live, g, s_trig,
                               &s_base);
 }
 
@@ -366,14 +367,14 @@ cudaError_t launch_trigger_warp(const RunArgs& a, const CompactWs<double>& w) {
 }
 cudaError_t launch_batch_trigger_warp(const BatchDev& b, const CompactWs<float>& w,
                                       cudaStream_t s) {
-  k_batch_trigger_warp<float><<<(b.total + kWarpCols - 1) / kWarpCols, 32 * kWarpCols, 0, s>>>(b,
-                                                                                              w);
+  k_batch_trigger_warp<float><<<(b.total + kWarpCols - 1) / kWarpCols, 32 * kWarpCols, 0, s>>>(
+      b, b.members, w);
   return cudaGetLastError();
 }
 cudaError_t launch_batch_trigger_warp(const BatchDev& b, const CompactWs<double>& w,
                                       cudaStream_t s) {
   k_batch_trigger_warp<double><<<(b.total + kWarpCols - 1) / kWarpCols, 32 * kWarpCols, 0, s>>>(
-      b, w);
+      b, b.members, w);
   return cudaGetLastError();
 }
 
