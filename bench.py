@@ -886,11 +886,12 @@ def l2_note(prec, n, pver):
 
 
 # the sources each measured kernel is compiled from (an ncu capture stays valid
-# while none of them changes)
+# while none of them changes); "step" covers k_trigger, k_plume and the FP64
+# plain kernel k_plain of the baseline line
 KERNEL_SOURCES = {
     "step": ("paper_1711_00289_gb300/csrc/column.cuh", "paper_1711_00289_gb300/csrc/compact.cu",
              "paper_1711_00289_gb300/csrc/compact.h", "paper_1711_00289_gb300/csrc/launch.h",
-             "include/conv.h"),
+             "paper_1711_00289_gb300/csrc/plain.cu", "include/conv.h"),
     "transport": ("paper_1711_00289_gb300/csrc/transport.cu", "paper_1711_00289_gb300/csrc/column.cuh",
                   "paper_1711_00289_gb300/csrc/launch.h", "include/conv.h"),
 }
