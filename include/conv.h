@@ -37,7 +37,9 @@
  *   - shallow rain within 1e-4 kg/kg of the autoconversion threshold: one FP64
  *     correction of the plume's saturation temperature and q_s in FP64;
  *   - moist inversions: FP32 Newton, warm-started along each vertical sequence
- *     by a tangent predictor, stopping after a correction below 0.01 K.
+ *     by a tangent predictor, stopping after a correction below 0.01 K;
+ *   - FP32 quotients: PTX div.full.f32, within 2 ulp of IEEE division
+ *     (conv_bench_f32_quotient applies it to arrays, for checking).
  * Measured against the FP64 oracle (the tests): trigger flips on at most 0.1%
  * of the columns, tendency column integrals within 1e-4 and precipitation
  * within 1e-3 relative where decisions agree.  Column scalars (ps, lambda, tau,

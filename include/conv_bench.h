@@ -39,6 +39,15 @@ typedef enum {
  * iters < 1; CONV_ERR_CUDA on a CUDA failure. */
 conv_status conv_bench_op_rate(int op, int arith, int iters, double* ops_per_s);
 
+/* The mixed path's FP32 quotient -- the division in every FP32 step of the
+ * schemes -- applied elementwise, q[i] = a[i] / b[i] for 0 <= i < n, so that
+ * it can be checked against IEEE division.  a, b, q: device arrays of n floats
+ * (q overlapping neither a nor b); asynchronous on `stream`, no allocation.
+ * CONV_ERR_ARG for n < 0 or a null array with n > 0; CONV_ERR_CUDA when the
+ * launch fails. */
+conv_status conv_bench_f32_quotient(const float* a, const float* b, float* q, int64_t n,
+                                    conv_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -107,6 +107,8 @@ def lib(build: bool = True):
     L.conv_deep_shallow_run.restype = st
     L.conv_bench_op_rate.argtypes = [st, st, st, P(C.c_double)]
     L.conv_bench_op_rate.restype = st
+    L.conv_bench_f32_quotient.argtypes = [vp, vp, vp, C.c_int64, vp]
+    L.conv_bench_f32_quotient.restype = st
     L.conv_deep_shallow_run_noalloc.argtypes = [P(Grid), P(In), P(DeepParams),
                                                 P(ShallowParams), d, st, P(Out), P(Out), vp]
     L.conv_deep_shallow_run_noalloc.restype = st
@@ -164,6 +166,11 @@ def op_rate(op: int, arith: int, iters: int = 2000) -> float:
     r = C.c_double()
     check(lib().conv_bench_op_rate(op, arith, iters, C.byref(r)), "conv_bench_op_rate")
     return r.value
+
+
+def f32_quotient(a: int, b: int, q: int, n: int, stream: int = 0) -> None:
+    """q[i] = a[i] / b[i] with the mixed path's FP32 division (device pointers)."""
+    check(lib().conv_bench_f32_quotient(a, b, q, n, stream), "conv_bench_f32_quotient")
 
 
 def status_str(s: int) -> str:

@@ -1,8 +1,12 @@
-// microbench.cu -- per-operation throughput of the current device (conv_bench.h).
-// Each thread advances 8 independent chains; every chain step is one evaluation
-// of the measured operation plus one FMA that keeps the argument bounded.
+// microbench.cu -- per-operation throughput of the current device and a check
+// of the mixed path's FP32 quotient (conv_bench.h).  Each thread of the rate
+// kernel advances 8 independent chains; every chain step is one evaluation of
+// the measured operation plus one FMA that keeps the argument bounded.  The
+// FP32 operations are the schemes' own (column.cuh: Mth<float>, div_f32), so
+// the rates weigh what the kernels execute.
 #include <cuda_runtime.h>
 
+#include "column.cuh"
 #include "conv_bench.h"
 
 namespace {
@@ -19,10 +23,10 @@ struct Ops<double> {
 };
 template <>
 struct Ops<float> {
-  static __device__ float ex(float x) { return expf(x); }
-  static __device__ float lg(float x) { return logf(x); }
-  static __device__ float dv(float a, float b) { return a / b; }
-  static __device__ float pw(float a, float b) { return powf(a, b); }
+  static __device__ float ex(float x) { return cvg::Mth<float>::es(x); }
+  static __device__ float lg(float x) { return cvg::Mth<float>::lg(x); }
+  static __device__ float dv(float a, float b) { return cvg::Mth<float>::dv(a, b); }
+  static __device__ float pw(float a, float b) { return cvg::Mth<float>::pw(a, b); }
   static __device__ float sq(float a) { return sqrtf(a); }
 };
 struct FastF {
@@ -99,7 +103,27 @@ cudaError_t run(int op, int iters, double* rate) {
   return e;
 }
 
+__global__ void k_quotient(const float* __restrict__ a, const float* __restrict__ b,
+                           float* __restrict__ q, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    q[i] = cvg::div_f32(a[i], b[i]);
+}
+
 }  // namespace
+
+extern "C" conv_status conv_bench_f32_quotient(const float* a, const float* b, float* q,
+                                               int64_t n, conv_stream stream) {
+  if (n < 0 || (n > 0 && (!a || !b || !q))) return CONV_ERR_ARG;
+  if (n == 0) return CONV_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CONV_ERR_CUDA;
+  const int64_t want = (n + 255) / 256, cap = (int64_t)sms * 8;
+  k_quotient<<<(unsigned)(want < cap ? want : cap), 256, 0, (cudaStream_t)stream>>>(a, b, q, n);
+  return cudaGetLastError() == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
 
 extern "C" conv_status conv_bench_op_rate(int op, int arith, int iters, double* ops_per_s) {
   if (!ops_per_s || iters < 1 || op < CONV_OP_FMA || op > CONV_OP_SQRT) return CONV_ERR_ARG;
