@@ -168,11 +168,62 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   store_shallow_scalars(a, i, s);
 }
 
+// Counting sort of the queue slots [base, min(base + BLOCK, count)) of one block
+// by plume depth kb - kel (0 .. CONV_MAX_LEVELS - 1, one bin per lane of warp
+// 0): returns the slot this thread runs, -1 for none.  Every thread of the
+// block calls it (it synchronises the block); within a depth the order is that
+// of the shared-memory atomics, which only decides which thread runs a column.
+template <int BLOCK>
+struct DepthSort {
+  int off[32];
+  int slot[BLOCK];
+};
+static_assert(CONV_MAX_LEVELS <= 32, "one depth bin per lane");
+template <int BLOCK>
+__device__ __forceinline__ int depth_sorted_slot(const int* __restrict__ levels, int base,
+                                                 int count, DepthSort<BLOCK>& s) {
+  static_assert(BLOCK >= 32 && BLOCK <= 1024, "block of whole warps");
+  const int t = threadIdx.x;
+  const int nv = min(BLOCK, count - base);
+  if (t < 32) s.off[t] = 0;
+  __syncthreads();
+  int key = 0, rank = 0;
+  if (t < nv) {
+    const int lvl = levels[base + t];
+    key = min(31, max(0, (lvl & 0xff) - ((lvl >> 16) & 0xff)));
+    rank = atomicAdd(&s.off[key], 1);
+  }
+  __syncthreads();
+  if (t < 32) {  // exclusive scan of the 32 bin counts
+    const int v = s.off[t];
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (t >= d) x += y;
+    }
+    s.off[t] = x - v;
+  }
+  __syncthreads();
+  if (t < nv) s.slot[s.off[key] + rank] = base + t;
+  __syncthreads();
+  return t < nv ? s.slot[t] : -1;
+}
+
 template <class R, bool EXT>
 __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactBlock)
     k_plume(const __grid_constant__ RunArgs a, CompactWs<R> w) {
-  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-  if (slot >= *w.count) return;
+  const int count = *w.count;
+  const int base = blockIdx.x * kCompactBlock;
+  if (base >= count) return;  // whole block: nothing queued this far
+  int slot = base + (int)threadIdx.x;
+  if constexpr (kPlumeSort) {
+    __shared__ DepthSort<kCompactBlock> ds;
+    slot = depth_sorted_slot<kCompactBlock>(w.levels, base, count, ds);
+    if (slot < 0) return;
+  } else {
+    if (slot >= count) return;
+  }
   const int i = w.queue[slot];
   plume_body<R, EXT, SmemLevels<R>::on>(a, w, slot, i, i);
 }
@@ -336,10 +387,22 @@ template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
     k_batch_plume(BatchDev b, const RunArgs* __restrict__ members, CompactWs<R> w) {
   const int count = *w.count;
-  for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
-    const int g = w.queue[slot];
-    const int m = find_member(b.offsets, b.n_members, g);
-    plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
+  if constexpr (kPlumeSort) {
+    __shared__ DepthSort<BLOCK> ds;
+    // block-uniform loop over the block's windows of BLOCK slots
+    for (int base = blockIdx.x * BLOCK; base < count; base += gridDim.x * BLOCK) {
+      const int slot = depth_sorted_slot<BLOCK>(w.levels, base, count, ds);
+      if (slot < 0) continue;
+      const int g = w.queue[slot];
+      const int m = find_member(b.offsets, b.n_members, g);
+      plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
+    }
+  } else {
+    for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
+      const int g = w.queue[slot];
+      const int m = find_member(b.offsets, b.n_members, g);
+      plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
+    }
   }
 }
 

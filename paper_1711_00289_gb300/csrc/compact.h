@@ -84,6 +84,18 @@ inline size_t smem_levels_bytes(int pver, int block) {
 #endif
 constexpr bool kThreePass = CVG_THREE_PASS != 0;
 
+// CVG_PLUME_SORT = 1: the plume pass regroups the queue slots of each block by
+// plume depth (kb - kel of the undilute parcel) before it runs them, so that
+// the columns of a warp take level loops of similar length; the block's set of
+// columns, and so its memory locality, stays as the trigger pass queued it.
+// Measured on the 884,736-column grid: k_plume 0.3826 ms sorted and unsorted;
+// the batched ensemble 4.55 ms against 3.92 (its persistent blocks synchronise
+// once per window of slots).  Off by default.
+#ifndef CVG_PLUME_SORT
+#define CVG_PLUME_SORT 0
+#endif
+constexpr bool kPlumeSort = CVG_PLUME_SORT != 0;
+
 template <class R>
 struct CompactWs {
   int* count;
