@@ -173,6 +173,11 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
 // 0): returns the slot this thread runs, -1 for none.  Every thread of the
 // block calls it (it synchronises the block); within a depth the order is that
 // of the shared-memory atomics, which only decides which thread runs a column.
+// Plume depth of a queued column, kb - kel of its undilute parcel (levels word).
+__device__ __forceinline__ int depth_key(int lvl) {
+  return min(31, max(0, (lvl & 0xff) - ((lvl >> 16) & 0xff)));
+}
+
 template <int BLOCK>
 struct DepthSort {
   int off[32];
@@ -189,8 +194,7 @@ __device__ __forceinline__ int depth_sorted_slot(const int* __restrict__ levels,
   __syncthreads();
   int key = 0, rank = 0;
   if (t < nv) {
-    const int lvl = levels[base + t];
-    key = min(31, max(0, (lvl & 0xff) - ((lvl >> 16) & 0xff)));
+    key = depth_key(levels[base + t]);
     rank = atomicAdd(&s.off[key], 1);
   }
   __syncthreads();
@@ -387,22 +391,10 @@ template <class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
     k_batch_plume(BatchDev b, const RunArgs* __restrict__ members, CompactWs<R> w) {
   const int count = *w.count;
-  if constexpr (kPlumeSort) {
-    __shared__ DepthSort<BLOCK> ds;
-    // block-uniform loop over the block's windows of BLOCK slots
-    for (int base = blockIdx.x * BLOCK; base < count; base += gridDim.x * BLOCK) {
-      const int slot = depth_sorted_slot<BLOCK>(w.levels, base, count, ds);
-      if (slot < 0) continue;
-      const int g = w.queue[slot];
-      const int m = find_member(b.offsets, b.n_members, g);
-      plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
-    }
-  } else {
-    for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
-      const int g = w.queue[slot];
-      const int m = find_member(b.offsets, b.n_members, g);
-      plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
-    }
+  for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
+    const int g = w.queue[slot];
+    const int m = find_member(b.offsets, b.n_members, g);
+    plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
   }
 }
 

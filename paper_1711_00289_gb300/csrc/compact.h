@@ -88,9 +88,11 @@ constexpr bool kThreePass = CVG_THREE_PASS != 0;
 // plume depth (kb - kel of the undilute parcel) before it runs them, so that
 // the columns of a warp take level loops of similar length; the block's set of
 // columns, and so its memory locality, stays as the trigger pass queued it.
-// Measured on the 884,736-column grid: k_plume 0.3826 ms sorted and unsorted;
-// the batched ensemble 4.55 ms against 3.92 (its persistent blocks synchronise
-// once per window of slots).  Off by default.
+// Measured on the 884,736-column grid: k_plume 0.3826 ms sorted and unsorted.
+// Off by default; the batched plume pass never sorts (a block-synchronised
+// sort took the ensemble from 3.92 to 4.55 ms, a warp-synchronised one over
+// 256-slot windows to 7.9 ms: on its uncorrelated columns, regrouping a
+// window's slots breaks the coalescing of the per-level column loads).
 #ifndef CVG_PLUME_SORT
 #define CVG_PLUME_SORT 0
 #endif
