@@ -654,11 +654,18 @@ __device__ __forceinline__ void init_column(Column<R>& c, const Levels& L, const
 }
 
 // Keep zm and dl in a block-shared array instead: lv = this thread's first word
-// of 2 pver levels x stride words (zm on levels 0..pver-1, then dl).
+// of 2 pver levels x stride words (zm on levels 0..pver-1, then dl); which = 2
+// (zm) or 3 (dl): only that array, pver levels x stride words.
 template <class R>
-__device__ __forceinline__ void bind_levels(Column<R>& c, R* lv, int stride) {
-  c.zm = LevelArr<R>{lv, stride};
-  c.dl = LevelArr<R>{lv + c.pver * stride, stride};
+__device__ __forceinline__ void bind_levels(Column<R>& c, R* lv, int stride, int which = 1) {
+  if (which == 1) {
+    c.zm = LevelArr<R>{lv, stride};
+    c.dl = LevelArr<R>{lv + c.pver * stride, stride};
+  } else if (which == 2) {
+    c.zm = LevelArr<R>{lv, stride};
+  } else {
+    c.dl = LevelArr<R>{lv, stride};
+  }
 }
 
 __device__ __forceinline__ bool in_range(double T, double q) {

@@ -19,9 +19,9 @@
 namespace cvg {
 
 // This thread's slice of the block's shared level arrays (nullptr: none).
-template <class R>
+template <class R, int PASS>
 __device__ __forceinline__ R* smem_levels() {
-  if constexpr (SmemLevels<R>::on) {
+  if constexpr (SmemLevels<R, PASS>::on) {
     extern __shared__ __align__(16) unsigned char cvg_smem[];
     return reinterpret_cast<R*>(cvg_smem) + threadIdx.x;
   } else {
@@ -47,7 +47,9 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
   bool valid = false;
   if (live) {
     init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
-    if constexpr (SMEM) bind_levels(c, smem_levels<R>(), blockDim.x);
+    if constexpr (SMEM)
+      bind_levels(c, smem_levels<R, kPassTrigger>(), blockDim.x,
+                  SmemLevels<R, kPassTrigger>::which);
     o.prec = o.cape = o.mb = o.cons = 0.0;
     o.flags = 0;
     o.kb = o.klcl = o.ktop = o.kaux = -1;
@@ -125,7 +127,7 @@ template <class R, bool EXT>
 __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::trigger / kCompactBlock)
     k_trigger(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  trigger_body<R, EXT, SmemLevels<R>::on>(a, w, i, i < a.n, i);
+  trigger_body<R, EXT, SmemLevels<R, kPassTrigger>::on>(a, w, i, i < a.n, i);
 }
 
 // Plume pass of the column in queue slot `slot`: column i of member a, queued
@@ -136,7 +138,8 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   Column<R> c;
   LevelBuf<R> cbuf;
   init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
-  if constexpr (SMEM) bind_levels(c, smem_levels<R>(), blockDim.x);
+  if constexpr (SMEM)
+    bind_levels(c, smem_levels<R, kPassPlume>(), blockDim.x, SmemLevels<R, kPassPlume>::which);
   DeepTrig<R> t;
   const int lvl = w.levels[slot];
   t.kb = lvl & 0xff;
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactB
     if (slot >= count) return;
   }
   const int i = w.queue[slot];
-  plume_body<R, EXT, SmemLevels<R>::on>(a, w, slot, i, i);
+  plume_body<R, EXT, SmemLevels<R, kPassPlume>::on>(a, w, slot, i, i);
 }
 
 // Shallow pass of the three-pass layout (column i, workspace index tag): a
@@ -271,25 +274,42 @@ __global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::shallow / kCompac
   if (i < a.n) shallow_body<R, EXT>(a, w, i, i);
 }
 
-// The compacted kernels that keep level arrays in shared memory ask for the
-// largest shared-memory carve-out, so that their resident blocks fit (set once
-// per kernel, before its first launch).
+// Kernels that keep level arrays in shared memory get a carve-out that fits
+// their resident blocks at the largest level count (plus the 1 KB the device
+// reserves per block), the rest of the unified L1 / shared memory staying L1
+// for the local arrays.  Set once per kernel, before its first launch.
+template <class R, int PASS>
+static void set_carveout(const void* f, int block, int blocks_per_sm) {
+  if constexpr (SmemLevels<R, PASS>::on) {
+    int dev = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        per_sm <= 0)
+      return;
+    const size_t most = smem_levels_bytes<R, PASS>(CONV_MAX_LEVELS, block);
+    const size_t need = (size_t)blocks_per_sm * (most + 1024);
+    const size_t pct = (100 * need + per_sm - 1) / per_sm;
+    cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)(pct > 100 ? 100 : pct));
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+  } else {
+    (void)f, (void)block, (void)blocks_per_sm;
+  }
+}
+
 template <class R>
 static void prefer_shared() {
-  if constexpr (SmemLevels<R>::on) {
-    static const bool done = [] {
-      cudaFuncSetAttribute(k_trigger<R, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-      cudaFuncSetAttribute(k_trigger<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-      cudaFuncSetAttribute(k_plume<R, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-      cudaFuncSetAttribute(k_plume<R, true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-      return true;
-    }();
-    (void)done;
-  }
+  static const bool done = [] {
+    constexpr int tb = SmThreads<R>::trigger / kCompactBlock;
+    constexpr int pb = SmThreads<R>::plume / kCompactBlock;
+    set_carveout<R, kPassTrigger>((const void*)k_trigger<R, false>, kCompactBlock, tb);
+    set_carveout<R, kPassTrigger>((const void*)k_trigger<R, true>, kCompactBlock, tb);
+    set_carveout<R, kPassPlume>((const void*)k_plume<R, false>, kCompactBlock, pb);
+    set_carveout<R, kPassPlume>((const void*)k_plume<R, true>, kCompactBlock, pb);
+    return true;
+  }();
+  (void)done;
 }
 
 size_t compact_workspace_bytes(int n, int pver, bool fp64) {
@@ -316,16 +336,17 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
   if (e != cudaSuccess) return e;
   const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
-  const size_t sm = smem_levels_bytes<R>(a.L.pver, kCompactBlock);
+  const size_t sm_t = smem_levels_bytes<R, kPassTrigger>(a.L.pver, kCompactBlock);
+  const size_t sm_p = smem_levels_bytes<R, kPassPlume>(a.L.pver, kCompactBlock);
   prefer_shared<R>();
   if (a.mapping == CONV_MAP_WARP) {
     e = launch_trigger_warp(a, w);
   } else {
     NvtxRange r("conv: trigger pass (all columns)");
     if (a.ext)
-      k_trigger<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+      k_trigger<R, true><<<grid, kCompactBlock, sm_t, a.stream>>>(a, w);
     else
-      k_trigger<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+      k_trigger<R, false><<<grid, kCompactBlock, sm_t, a.stream>>>(a, w);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
@@ -333,9 +354,9 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   {
     NvtxRange r("conv: plume pass (queued columns)");
     if (a.ext)
-      k_plume<R, true><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+      k_plume<R, true><<<grid, kCompactBlock, sm_p, a.stream>>>(a, w);
     else
-      k_plume<R, false><<<grid, kCompactBlock, sm, a.stream>>>(a, w);
+      k_plume<R, false><<<grid, kCompactBlock, sm_p, a.stream>>>(a, w);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -384,7 +405,7 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::trigger / BLOCK)
     m = find_member(b.offsets, b.n_members, g);
     i = g - b.offsets[m];
   }
-  trigger_body<R, false, SmemLevels<R>::on>(members[m], w, i, live, g);
+  trigger_body<R, false, SmemLevels<R, kPassTrigger>::on>(members[m], w, i, live, g);
 }
 
 template <class R, int BLOCK>
@@ -394,28 +415,23 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
   for (int slot = blockIdx.x * BLOCK + threadIdx.x; slot < count; slot += gridDim.x * BLOCK) {
     const int g = w.queue[slot];
     const int m = find_member(b.offsets, b.n_members, g);
-    plume_body<R, false, SmemLevels<R>::on>(members[m], w, slot, g - b.offsets[m], g);
+    plume_body<R, false, SmemLevels<R, kPassPlume>::on>(members[m], w, slot, g - b.offsets[m],
+                                                        g);
   }
 }
 
-// Shared-memory set-up of the batch kernels at one block size: the largest
-// carve-out, and the dynamic size of the largest level count (a 256-thread
-// block of 32-level columns needs 64 KB, above the default 48 KB limit).
+// Shared-memory set-up of the batch kernels at one block size: the carve-out
+// and the dynamic size of the largest level count (set_carveout).
 template <class R, int BLOCK>
 static void batch_smem_setup() {
-  if constexpr (SmemLevels<R>::on) {
-    static const bool done = [] {
-      const int most = (int)smem_levels_bytes<R>(CONV_MAX_LEVELS, BLOCK);
-      for (const void* f : {(const void*)k_batch_trigger<R, BLOCK>,
-                            (const void*)k_batch_plume<R, BLOCK>}) {
-        cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-      }
-      return true;
-    }();
-    (void)done;
-  }
+  static const bool done = [] {
+    set_carveout<R, kPassTrigger>((const void*)k_batch_trigger<R, BLOCK>, BLOCK,
+                                  SmThreads<R>::trigger / BLOCK);
+    set_carveout<R, kPassPlume>((const void*)k_batch_plume<R, BLOCK>, BLOCK,
+                                SmThreads<R>::plume / BLOCK);
+    return true;
+  }();
+  (void)done;
 }
 
 template <class R, int BLOCK>
@@ -432,7 +448,7 @@ static int plume_occupancy(int max_pver) {
   batch_smem_setup<R, BLOCK>();
   int blocks = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_batch_plume<R, BLOCK>, BLOCK,
-                                                    smem_levels_bytes<R>(max_pver, BLOCK)) !=
+                                                    smem_levels_bytes<R, kPassPlume>(max_pver, BLOCK)) !=
       cudaSuccess)
     return 1;
   return blocks < 1 ? 1 : blocks;
@@ -456,13 +472,14 @@ static void launch_trig(const BatchDev& b, const CompactWs<R>& w, int max_pver,
                         cudaStream_t s) {
   batch_smem_setup<R, BLOCK>();
   k_batch_trigger<R, BLOCK><<<(b.total + BLOCK - 1) / BLOCK, BLOCK,
-                              smem_levels_bytes<R>(max_pver, BLOCK), s>>>(b, b.members, w);
+                              smem_levels_bytes<R, kPassTrigger>(max_pver, BLOCK), s>>>(b, b.members,
+                                                                                     w);
 }
 template <class R, int BLOCK>
 static void launch_plume(const BatchDev& b, const CompactWs<R>& w, int grid, int max_pver,
                          cudaStream_t s) {
   batch_smem_setup<R, BLOCK>();
-  k_batch_plume<R, BLOCK><<<grid, BLOCK, smem_levels_bytes<R>(max_pver, BLOCK), s>>>(
+  k_batch_plume<R, BLOCK><<<grid, BLOCK, smem_levels_bytes<R, kPassPlume>(max_pver, BLOCK), s>>>(
       b, b.members, w);
 }
 

@@ -22,13 +22,20 @@ constexpr int kCompactBlock = 128;
 #ifndef CVG_PLUME_SM_THREADS
 #define CVG_PLUME_SM_THREADS 896
 #endif
-// Level arrays in shared memory (1) or in each thread's local memory (0, the
-// default): measured on the 884,736-column step, shared memory limits the
-// trigger pass to 896 resident threads per SM (7 blocks of 30 KB) and made it
-// 9% slower (0.544 against 0.498 ms); the plume pass gained 3% (0.444 against
-// 0.459 ms) and the batched ensemble lost 13%.
-#ifndef CVG_SMEM_LEVELS
-#define CVG_SMEM_LEVELS 0
+// Where each pass of the mixed path keeps a column's level arrays zm (mid-layer
+// heights) and dl (layer log-thicknesses): 0 both in the thread's local array,
+// 1 both in shared memory, 2 zm in shared memory, 3 dl in shared memory.
+// Measured on the 884,736-column step (trigger / plume pass, ms): 0: 0.473 /
+// 0.383; 1: 0.537 / 0.383 (30 KB per 128-thread block leaves the trigger pass
+// 7 resident blocks per SM); 2: 0.454 / 0.384; 3: 0.446 / 0.384.  With dl in
+// shared memory (15 KB per block, 11 blocks per SM) the trigger pass's local
+// traffic drops; the plume pass, at 7 blocks per SM, already hits L1 on 57% of
+// its local loads and gains nothing.
+#ifndef CVG_SMEM_LEVELS_TRIGGER
+#define CVG_SMEM_LEVELS_TRIGGER 3
+#endif
+#ifndef CVG_SMEM_LEVELS_PLUME
+#define CVG_SMEM_LEVELS_PLUME 0
 #endif
 #ifndef CVG_SHALLOW_SM_THREADS
 #define CVG_SHALLOW_SM_THREADS 1408
@@ -53,22 +60,31 @@ enum : int {
   // bits 8-15: the deep parcel's LCL layer; bits 16-23: the deep top limit
 };
 
-// Where the compacted kernels keep each column's mid-layer heights and layer
-// log-thicknesses (Column::zm, dl): in shared memory, 2 pver levels x block
-// words per block (level-major, thread innermost), for the mixed path; in the
-// threads' own local arrays for FP64, where the 8-byte words would leave room
-// for too few blocks per SM.
-template <class R>
+// Shared-memory placement of the level arrays per pass (kPassTrigger: the
+// trigger kernels, kPassPlume: the plume kernels): level-major, the thread
+// index innermost, pver levels x block words per array.  FP64 keeps both in
+// the threads' local arrays: its 8-byte words would leave room for too few
+// blocks per SM.
+enum : int { kPassTrigger = 0, kPassPlume = 1 };
+template <class R, int PASS>
 struct SmemLevels {
+  static constexpr int which = 0;
   static constexpr bool on = false;
 };
-template <>
-struct SmemLevels<float> {
-  static constexpr bool on = CVG_SMEM_LEVELS != 0;
+template <int PASS>
+struct SmemLevels<float, PASS> {
+  static constexpr int which =
+      PASS == kPassTrigger ? CVG_SMEM_LEVELS_TRIGGER : CVG_SMEM_LEVELS_PLUME;
+  static constexpr bool on = which != 0;
 };
-template <class R>
+template <class R, int PASS>
 inline size_t smem_levels_bytes(int pver, int block) {
-  return SmemLevels<R>::on ? sizeof(R) * 2 * (size_t)pver * (size_t)block : 0;
+  if constexpr (SmemLevels<R, PASS>::on) {
+    const size_t arrays = SmemLevels<R, PASS>::which == 1 ? 2 : 1;
+    return sizeof(R) * arrays * (size_t)pver * (size_t)block;
+  } else {
+    return 0;
+  }
 }
 
 // Device workspace of the compacted path, carved from one caller buffer:
