@@ -124,7 +124,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
 }
 
 template <class R, bool EXT>
-__global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::trigger / kCompactBlock)
+__global__ void __launch_bounds__(kTriggerBlock, SmThreads<R>::trigger / kTriggerBlock)
     k_trigger(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   trigger_body<R, EXT, SmemLevels<R, kPassTrigger>::on>(a, w, i, i < a.n, i);
@@ -218,15 +218,15 @@ __device__ __forceinline__ int depth_sorted_slot(const int* __restrict__ levels,
 }
 
 template <class R, bool EXT>
-__global__ void __launch_bounds__(kCompactBlock, SmThreads<R>::plume / kCompactBlock)
+__global__ void __launch_bounds__(kPlumeBlock, SmThreads<R>::plume / kPlumeBlock)
     k_plume(const __grid_constant__ RunArgs a, CompactWs<R> w) {
   const int count = *w.count;
-  const int base = blockIdx.x * kCompactBlock;
+  const int base = blockIdx.x * kPlumeBlock;
   if (base >= count) return;  // whole block: nothing queued this far
   int slot = base + (int)threadIdx.x;
   if constexpr (kPlumeSort) {
-    __shared__ DepthSort<kCompactBlock> ds;
-    slot = depth_sorted_slot<kCompactBlock>(w.levels, base, count, ds);
+    __shared__ DepthSort<kPlumeBlock> ds;
+    slot = depth_sorted_slot<kPlumeBlock>(w.levels, base, count, ds);
     if (slot < 0) return;
   } else {
     if (slot >= count) return;
@@ -301,12 +301,12 @@ static void set_carveout(const void* f, int block, int blocks_per_sm) {
 template <class R>
 static void prefer_shared() {
   static const bool done = [] {
-    constexpr int tb = SmThreads<R>::trigger / kCompactBlock;
-    constexpr int pb = SmThreads<R>::plume / kCompactBlock;
-    set_carveout<R, kPassTrigger>((const void*)k_trigger<R, false>, kCompactBlock, tb);
-    set_carveout<R, kPassTrigger>((const void*)k_trigger<R, true>, kCompactBlock, tb);
-    set_carveout<R, kPassPlume>((const void*)k_plume<R, false>, kCompactBlock, pb);
-    set_carveout<R, kPassPlume>((const void*)k_plume<R, true>, kCompactBlock, pb);
+    constexpr int tb = SmThreads<R>::trigger / kTriggerBlock;
+    constexpr int pb = SmThreads<R>::plume / kPlumeBlock;
+    set_carveout<R, kPassTrigger>((const void*)k_trigger<R, false>, kTriggerBlock, tb);
+    set_carveout<R, kPassTrigger>((const void*)k_trigger<R, true>, kTriggerBlock, tb);
+    set_carveout<R, kPassPlume>((const void*)k_plume<R, false>, kPlumeBlock, pb);
+    set_carveout<R, kPassPlume>((const void*)k_plume<R, true>, kPlumeBlock, pb);
     return true;
   }();
   (void)done;
@@ -336,17 +336,19 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   cudaError_t e = cudaMemsetAsync(w.count, 0, sizeof(int), a.stream);
   if (e != cudaSuccess) return e;
   const int grid = (a.n + kCompactBlock - 1) / kCompactBlock;
-  const size_t sm_t = smem_levels_bytes<R, kPassTrigger>(a.L.pver, kCompactBlock);
-  const size_t sm_p = smem_levels_bytes<R, kPassPlume>(a.L.pver, kCompactBlock);
+  const int grid_t = (a.n + kTriggerBlock - 1) / kTriggerBlock;
+  const int grid_p = (a.n + kPlumeBlock - 1) / kPlumeBlock;
+  const size_t sm_t = smem_levels_bytes<R, kPassTrigger>(a.L.pver, kTriggerBlock);
+  const size_t sm_p = smem_levels_bytes<R, kPassPlume>(a.L.pver, kPlumeBlock);
   prefer_shared<R>();
   if (a.mapping == CONV_MAP_WARP) {
     e = launch_trigger_warp(a, w);
   } else {
     NvtxRange r("conv: trigger pass (all columns)");
     if (a.ext)
-      k_trigger<R, true><<<grid, kCompactBlock, sm_t, a.stream>>>(a, w);
+      k_trigger<R, true><<<grid_t, kTriggerBlock, sm_t, a.stream>>>(a, w);
     else
-      k_trigger<R, false><<<grid, kCompactBlock, sm_t, a.stream>>>(a, w);
+      k_trigger<R, false><<<grid_t, kTriggerBlock, sm_t, a.stream>>>(a, w);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) return e;
@@ -354,9 +356,9 @@ static cudaError_t launch_t(const RunArgs& a, void* ws, size_t ws_bytes) {
   {
     NvtxRange r("conv: plume pass (queued columns)");
     if (a.ext)
-      k_plume<R, true><<<grid, kCompactBlock, sm_p, a.stream>>>(a, w);
+      k_plume<R, true><<<grid_p, kPlumeBlock, sm_p, a.stream>>>(a, w);
     else
-      k_plume<R, false><<<grid, kCompactBlock, sm_p, a.stream>>>(a, w);
+      k_plume<R, false><<<grid_p, kPlumeBlock, sm_p, a.stream>>>(a, w);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

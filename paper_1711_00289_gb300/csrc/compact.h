@@ -6,18 +6,28 @@
 namespace cvg {
 
 constexpr int kCompactBlock = 128;
+// Block sizes of the single-grid trigger and plume passes.
+#ifndef CVG_TRIGGER_BLOCK
+#define CVG_TRIGGER_BLOCK 128
+#endif
+#ifndef CVG_PLUME_BLOCK
+#define CVG_PLUME_BLOCK 128
+#endif
+constexpr int kTriggerBlock = CVG_TRIGGER_BLOCK, kPlumeBlock = CVG_PLUME_BLOCK;
 
 // Resident threads per SM the compacted kernels are compiled for (register cap
 // 65536 / threads).  The mixed kernels are latency-bound chains of dependent
 // FP32 operations: more resident warps hide more of that latency, until the
 // spills of a tighter cap cost more.  Measured sweeps of the caps put the
-// trigger pass at 1408 threads per SM (40 registers; 1664 threads, 32
-// registers, was 21% slower; 1024 threads, 64 registers, 50% slower) and the
-// plume pass at 896 (72 registers; 768 was 18% slower, 1024 2% slower).  The
+// trigger pass at 1280 threads per SM (48 registers: 0.433 ms, against 0.445 at
+// 1408 threads and 40 registers, and 0.461 at 1024 threads and 64 registers,
+// with the FP32 quotients and shared-memory log-thicknesses of the current
+// kernel; 256-thread blocks at the same caps were no faster) and the plume
+// pass at 896 (72 registers; 768 was 18% slower, 1024 2% slower).  The
 // FP64 kernels are bound by the FP64 pipe and need enough warps in flight to
 // keep it fed: 896 threads (72 registers).  (Build-time overrides, for sweeps.)
 #ifndef CVG_TRIGGER_SM_THREADS
-#define CVG_TRIGGER_SM_THREADS 1408
+#define CVG_TRIGGER_SM_THREADS 1280
 #endif
 #ifndef CVG_PLUME_SM_THREADS
 #define CVG_PLUME_SM_THREADS 896

@@ -88,6 +88,16 @@ struct TrSrc {
 // convective-scale pressure gradient, coefficient cp_up for the updraft and
 // cp_down for the downdraft -- and the environment of layer k loses the same
 // (the pressure force the plume exerts), so column momentum is conserved.
+// Quotients of the transport recurrences: the tracer instantiation divides with
+// IEEE a / b (25 FP32 tracers on the 884,736-column grid: 1.57 ms, against
+// 1.66 ms with the schemes' div.full.f32), the momentum instantiation with the
+// schemes' FP32 quotient (0.168 ms against 0.179).
+template <class R, bool MOM>
+__device__ __forceinline__ R tq(R a, R b) {
+  if constexpr (MOM) return Mth<R>::dv(a, b);
+  else return a / b;
+}
+
 template <class R, int G, bool MOM = false>
 __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLevels<R>& L, R ps,
                                       int pver, size_t ld, size_t tstr, int i, const Plume& p,
@@ -143,7 +153,7 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
         if (k0 + j > kb - 1) break;
         const R mk = mv[j];
         if (mk > R(0)) {
-          const R r = Mth<R>::dv(mk - mprev, mk);
+          const R r = tq<R, MOM>(mk - mprev, mk);
 #pragma unroll
           for (int g = 0; g < G; ++g) {
             cd[g] = cd[g] + r * (cv[g][j] - cd[g]);
@@ -189,8 +199,8 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
       const int k = k0 - j;
       if (k < kt) break;
       const R muk = muv[j], duk = duv[j], mdk = mdv[j];
-      const R rm = Mth<R>::dv(R(1), layer_mass<R>(L, ps, k));
-      const R ru = muk > R(0) ? Mth<R>::dv(muk - mu1 + duk, muk) : R(0);
+      const R rm = tq<R, MOM>(R(1), layer_mass<R>(L, ps, k));
+      const R ru = muk > R(0) ? tq<R, MOM>(muk - mu1 + duk, muk) : R(0);
 #pragma unroll
       for (int g = 0; g < G; ++g) {
         if (g >= ng) continue;
@@ -206,7 +216,7 @@ __device__ __forceinline__ void stage(const TrScheme& S, bool down, const ShLeve
           const R pu = cp_up * (mu1 - duk) * (ck[g] - cb[g]);
           t -= pu + cp_down * mdu[j] * (ck[g] - cup);
           put(g, k, t * rm);
-          cu[g] = muk > R(0) ? cu[g] + ru * (ck[g] - cu[g]) + Mth<R>::dv(pu, muk) : R(0);
+          cu[g] = muk > R(0) ? cu[g] + ru * (ck[g] - cu[g]) + tq<R, MOM>(pu, muk) : R(0);
         } else {
           put(g, k, t * rm);
           cu[g] = muk > R(0) ? cu[g] + ru * (ck[g] - cu[g]) : R(0);
