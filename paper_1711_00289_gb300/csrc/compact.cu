@@ -34,7 +34,7 @@ __device__ __forceinline__ R* smem_levels() {
 // (the column index, or a batch-wide index), `live` false for padding lanes.
 // SMEM: the column's level arrays live in the block's shared memory
 // (smem_levels), not in the thread's local arrays.
-template <class R, bool EXT = false, bool SMEM = false>
+template <class R, bool EXT = false, bool SMEM = false, int PASS = kPassTrigger>
 __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R>& w, int i,
                                              bool live, int tag) {
   Column<R> c;
@@ -48,8 +48,7 @@ __device__ __forceinline__ void trigger_body(const RunArgs& a, const CompactWs<R
   if (live) {
     init_column(c, a.L, input_src<R>(a, i), a.ps[i], cbuf);
     if constexpr (SMEM)
-      bind_levels(c, smem_levels<R, kPassTrigger>(), blockDim.x,
-                  SmemLevels<R, kPassTrigger>::which);
+      bind_levels(c, smem_levels<R, PASS>(), blockDim.x, SmemLevels<R, PASS>::which);
     o.prec = o.cape = o.mb = o.cons = 0.0;
     o.flags = 0;
     o.kb = o.klcl = o.ktop = o.kaux = -1;
@@ -407,7 +406,8 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::trigger / BLOCK)
     m = find_member(b.offsets, b.n_members, g);
     i = g - b.offsets[m];
   }
-  trigger_body<R, false, SmemLevels<R, kPassTrigger>::on>(members[m], w, i, live, g);
+  trigger_body<R, false, SmemLevels<R, kPassBatchTrigger>::on, kPassBatchTrigger>(members[m], w, i,
+                                                                                 live, g);
 }
 
 template <class R, int BLOCK>
@@ -427,8 +427,8 @@ __global__ void __launch_bounds__(BLOCK, SmThreads<R>::plume / BLOCK)
 template <class R, int BLOCK>
 static void batch_smem_setup() {
   static const bool done = [] {
-    set_carveout<R, kPassTrigger>((const void*)k_batch_trigger<R, BLOCK>, BLOCK,
-                                  SmThreads<R>::trigger / BLOCK);
+    set_carveout<R, kPassBatchTrigger>((const void*)k_batch_trigger<R, BLOCK>, BLOCK,
+                                       SmThreads<R>::trigger / BLOCK);
     set_carveout<R, kPassPlume>((const void*)k_batch_plume<R, BLOCK>, BLOCK,
                                 SmThreads<R>::plume / BLOCK);
     return true;
@@ -474,7 +474,7 @@ static void launch_trig(const BatchDev& b, const CompactWs<R>& w, int max_pver,
                         cudaStream_t s) {
   batch_smem_setup<R, BLOCK>();
   k_batch_trigger<R, BLOCK><<<(b.total + BLOCK - 1) / BLOCK, BLOCK,
-                              smem_levels_bytes<R, kPassTrigger>(max_pver, BLOCK), s>>>(b, b.members,
+                              smem_levels_bytes<R, kPassBatchTrigger>(max_pver, BLOCK), s>>>(b, b.members,
                                                                                      w);
 }
 template <class R, int BLOCK>

@@ -47,6 +47,12 @@ constexpr int kTriggerBlock = CVG_TRIGGER_BLOCK, kPlumeBlock = CVG_PLUME_BLOCK;
 #ifndef CVG_SMEM_LEVELS_PLUME
 #define CVG_SMEM_LEVELS_PLUME 0
 #endif
+// The batched trigger pass (256-thread blocks after autotuning, 5 per SM: 30 KB
+// of shared memory each for dl) keeps both arrays local: the 64-member
+// ensemble ran 3.86 ms per step that way, 4.00 ms with dl shared, 4.05 with zm.
+#ifndef CVG_SMEM_LEVELS_BATCH_TRIGGER
+#define CVG_SMEM_LEVELS_BATCH_TRIGGER 0
+#endif
 #ifndef CVG_SHALLOW_SM_THREADS
 #define CVG_SHALLOW_SM_THREADS 1408
 #endif
@@ -75,7 +81,7 @@ enum : int {
 // index innermost, pver levels x block words per array.  FP64 keeps both in
 // the threads' local arrays: its 8-byte words would leave room for too few
 // blocks per SM.
-enum : int { kPassTrigger = 0, kPassPlume = 1 };
+enum : int { kPassTrigger = 0, kPassPlume = 1, kPassBatchTrigger = 2 };
 template <class R, int PASS>
 struct SmemLevels {
   static constexpr int which = 0;
@@ -83,8 +89,9 @@ struct SmemLevels {
 };
 template <int PASS>
 struct SmemLevels<float, PASS> {
-  static constexpr int which =
-      PASS == kPassTrigger ? CVG_SMEM_LEVELS_TRIGGER : CVG_SMEM_LEVELS_PLUME;
+  static constexpr int which = PASS == kPassTrigger        ? CVG_SMEM_LEVELS_TRIGGER
+                               : PASS == kPassBatchTrigger ? CVG_SMEM_LEVELS_BATCH_TRIGGER
+                                                           : CVG_SMEM_LEVELS_PLUME;
   static constexpr bool on = which != 0;
 };
 template <class R, int PASS>
