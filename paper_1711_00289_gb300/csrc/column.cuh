@@ -1451,9 +1451,11 @@ __device__ __forceinline__ void shallow_column(const conv_shallow_params& P, con
     MoistSeq<R> seq;
     seq.have = false;
     // a column the deep scheme found stable: first try to settle exit E2 (no LFC)
-    // by bounds alone
-    const bool no_lfc =
-        bound != nullptr && seed == nullptr && certainly_no_lfc(c, *bound, hsrc, klcl, plfc);
+    // by bounds alone.  With a seed the parcel above the LCL is the deep parcel
+    // itself (same source layer, LCL and temperatures; the mixed path's q_s
+    // differs from the deep trigger's linearised one by ~1e-9 kg/kg, far inside
+    // kBuoyMargin), so the deep trigger's buoyancy bits decide every layer.
+    const bool no_lfc = bound != nullptr && certainly_no_lfc(c, *bound, hsrc, klcl, plfc);
     for (int k = ks; !no_lfc && k >= ktl; --k) {
       const R pm = c.pm(k);
       if (!(pm >= plfc)) break;
