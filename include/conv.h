@@ -33,7 +33,8 @@
  *     threshold, so that every comparison made with it comes out as in FP64;
  *   - CAPE, CIN and the column conservation sums: FP32 terms added in
  *     compensated FP32 arithmetic (TwoSum; the sum of the terms is exact to
- *     ~2^-48 relative, each term carrying its own FP32 rounding, ~1e-7);
+ *     ~2^-48 relative, each term carrying its own FP32 rounding, ~1e-7); the
+ *     conservation ratio cons_err from them in FP32 with error-free products;
  *   - shallow rain within 1e-4 kg/kg of the autoconversion threshold: one FP64
  *     correction of the plume's saturation temperature and q_s in FP64;
  *   - moist inversions: FP32 Newton, warm-started along each vertical sequence
