@@ -48,6 +48,17 @@ conv_status conv_bench_op_rate(int op, int arith, int iters, double* ops_per_s);
 conv_status conv_bench_f32_quotient(const float* a, const float* b, float* q, int64_t n,
                                     conv_stream stream);
 
+/* The LCL pressure of n parcels (T [K], q [kg/kg], p [Pa]; device arrays) by the
+ * mixed path's FP32 solve (pL32, without its FP64 correction; p itself for a
+ * parcel saturated where it is) and by the FP64 solve (pL64), each with at most
+ * n_newton Newton steps from the Bolton first guess (the schemes' lifting
+ * condensation level, Sec. II-A), so that the FP32 error can be checked against the band in
+ * which the mixed path corrects it in FP64.  Asynchronous on `stream`, no
+ * allocation.  CONV_ERR_ARG for n < 0, n_newton < 1 or a null array with
+ * n > 0; CONV_ERR_CUDA when the launch fails. */
+conv_status conv_bench_lcl(const float* T, const float* q, const float* p, float* pL32,
+                           double* pL64, int64_t n, int n_newton, conv_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,8 @@ def lib(build: bool = True):
     L.conv_bench_op_rate.restype = st
     L.conv_bench_f32_quotient.argtypes = [vp, vp, vp, C.c_int64, vp]
     L.conv_bench_f32_quotient.restype = st
+    L.conv_bench_lcl.argtypes = [vp, vp, vp, vp, vp, C.c_int64, st, vp]
+    L.conv_bench_lcl.restype = st
     L.conv_deep_shallow_run_noalloc.argtypes = [P(Grid), P(In), P(DeepParams),
                                                 P(ShallowParams), d, st, P(Out), P(Out), vp]
     L.conv_deep_shallow_run_noalloc.restype = st
@@ -171,6 +173,12 @@ def op_rate(op: int, arith: int, iters: int = 2000) -> float:
 def f32_quotient(a: int, b: int, q: int, n: int, stream: int = 0) -> None:
     """q[i] = a[i] / b[i] with the mixed path's FP32 division (device pointers)."""
     check(lib().conv_bench_f32_quotient(a, b, q, n, stream), "conv_bench_f32_quotient")
+
+
+def lcl_pressures(T: int, q: int, p: int, pL32: int, pL64: int, n: int, n_newton: int = 6,
+                  stream: int = 0) -> None:
+    """FP32 and FP64 LCL pressures of n parcels (device pointers)."""
+    check(lib().conv_bench_lcl(T, q, p, pL32, pL64, n, n_newton, stream), "conv_bench_lcl")
 
 
 def status_str(s: int) -> str:

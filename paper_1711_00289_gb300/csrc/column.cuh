@@ -315,38 +315,44 @@ struct LclF32 {
   float pL;      // FP32 LCL pressure
   bool saturated;  // parcel saturated at its level: p_L = p_b exactly
 };
+// The FP32 LCL Newton iteration stops after a correction below kLclStop (K),
+// or after n_newton steps.
+constexpr float kLclStop = 1e-4f;
 __device__ __forceinline__ LclF32 lcl_f32(float Tb, float qb, float pb, int n_newton,
                                           float& newton) {
   LclF32 s;
   const float esb =
-      (float)ES0 * expf(fdiv_ieee((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
+      (float)ES0 * expf(div_f32((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
   float Db = pb - (float)ONE_M_EPS * esb;
   if (Db < 1e-3f * pb) Db = 1e-3f * pb;
-  s.saturated = qb >= fdiv_ieee((float)EPSV * esb, Db);
+  s.saturated = qb >= div_f32((float)EPSV * esb, Db);
   if (s.saturated) {
     s.T = Tb;
     s.rGp = 0.f;
     s.pL = pb;
     return s;
   }
-  const float eb = fdiv_ieee(qb * pb, (float)EPSV + (float)ONE_M_EPS * qb);
+  const float eb = div_f32(qb * pb, (float)EPSV + (float)ONE_M_EPS * qb);
   const float lnrh =
-      logf(eb) - ((float)LN_ES0 + fdiv_ieee((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
-  const float c1 = fdiv_ieee((float)(ESA * ESC), Tb - (float)EST1);
-  float T = fdiv_ieee(1.f, fdiv_ieee(1.f, Tb - 55.f) - lnrh * (1.f / 2840.f)) + 55.f;
+      logf(eb) - ((float)LN_ES0 + div_f32((float)ESA * (Tb - (float)EST0), Tb - (float)EST1));
+  const float c1 = div_f32((float)(ESA * ESC), Tb - (float)EST1);
+  float T = div_f32(1.f, div_f32(1.f, Tb - 55.f) - lnrh * (1.f / 2840.f)) + 55.f;
   float rGp = 0.f, step = 0.f;
   for (int it = 0; it < n_newton; ++it) {
-    const float r = fdiv_ieee(1.f, T - (float)EST1);
-    const float G = c1 * (T - Tb) * r - lnrh - (float)INV_KAPPA * logf(fdiv_ieee(T, Tb));
-    const float Gp = (float)(ESA * ESC) * r * r - fdiv_ieee((float)INV_KAPPA, T);
-    rGp = fdiv_ieee(1.f, Gp);
+    const float r = div_f32(1.f, T - (float)EST1);
+    const float G = c1 * (T - Tb) * r - lnrh - (float)INV_KAPPA * logf(div_f32(T, Tb));
+    const float Gp = (float)(ESA * ESC) * r * r - div_f32((float)INV_KAPPA, T);
+    rGp = div_f32(1.f, Gp);
     step = G * rGp;
     T -= step;
+    // converged: the error left, ~(G''/2G') step^2, is far below FP32 resolution
+    // of T, and p_L moves by < 1e-8 relative, inside the 2e-5 decision band
+    if (fabsf(step) < kLclStop) break;
   }
   newton = fmaxf(newton, fabsf(step));
   s.T = T;
   s.rGp = rGp;
-  s.pL = pb * expf((float)INV_KAPPA * logf(fdiv_ieee(T, Tb)));
+  s.pL = pb * expf((float)INV_KAPPA * logf(div_f32(T, Tb)));
   return s;
 }
 

@@ -110,7 +110,34 @@ __global__ void k_quotient(const float* __restrict__ a, const float* __restrict_
     q[i] = cvg::div_f32(a[i], b[i]);
 }
 
+__global__ void k_lcl(const float* __restrict__ T, const float* __restrict__ q,
+                      const float* __restrict__ p, float* __restrict__ pL32,
+                      double* __restrict__ pL64, int64_t n, int n_newton) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float nf = 0.f, nd = 0.f;
+    const cvg::LclF32 s = cvg::lcl_f32(T[i], q[i], p[i], n_newton, nf);
+    pL32[i] = s.saturated ? p[i] : s.pL;
+    pL64[i] = cvg::lcl_p((double)T[i], (double)q[i], (double)p[i], n_newton, nd);
+  }
+}
+
 }  // namespace
+
+extern "C" conv_status conv_bench_lcl(const float* T, const float* q, const float* p,
+                                      float* pL32, double* pL64, int64_t n, int n_newton,
+                                      conv_stream stream) {
+  if (n < 0 || n_newton < 1 || (n > 0 && (!T || !q || !p || !pL32 || !pL64))) return CONV_ERR_ARG;
+  if (n == 0) return CONV_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return CONV_ERR_CUDA;
+  const int64_t want = (n + 255) / 256, cap = (int64_t)sms * 8;
+  k_lcl<<<(unsigned)(want < cap ? want : cap), 256, 0, (cudaStream_t)stream>>>(T, q, p, pL32, pL64,
+                                                                             n, n_newton);
+  return cudaGetLastError() == cudaSuccess ? CONV_OK : CONV_ERR_CUDA;
+}
 
 extern "C" conv_status conv_bench_f32_quotient(const float* a, const float* b, float* q,
                                                int64_t n, conv_stream stream) {
