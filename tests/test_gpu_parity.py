@@ -254,3 +254,41 @@ def test_every_column_convecting(oracle, path):
     md, ms_ = run_gpu(g, "mixed", path)
     r = mixed_report(md, rd, layer_mass(g), None, rd["prec"] + rs["prec"])
     check_mixed(r, "deep", 2e-3)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_no_column_convecting(oracle, path):
+    """The other degenerate load: no column triggers the deep scheme (a CAPE
+    threshold no column reaches), so the compacted path's queue stays empty and
+    the plume pass has nothing to do; the shallow scheme then runs on every
+    column's own state in the trigger pass, plumes included.
+
+    FP64 against the oracle as everywhere.  Mixed: against the oracle on the
+    mixed path's own inputs (the FP32 profiles, exactly converted): shallow-only
+    trace rain here is conditioned so that rounding the inputs to FP32 alone
+    moves the FP64 definition's precipitation by up to 7.5e-4, half the total
+    difference from the unrounded oracle; the budget measures the arithmetic."""
+    import copy
+
+    from paper_1711_00289_gb300 import _lib as L
+    from tests.test_oracle_random import _random_columns
+
+    g = _random_columns(5, n=4000)
+    dpar = oracle.deep_params(capelmt=1e9)
+    rd, rs = oracle.deep_shallow(g, dpar=dpar, threads=THREADS)
+    assert not ((rd["flags"] & 1) > 0).any()
+    assert ((rs["flags"] & 2) > 0).sum() > 100  # active shallow plumes
+    dp = L.deep_defaults()
+    dp.capelmt = 1e9
+    gd, gs = run_gpu(g, "fp64", path, deep_params=dp)
+    assert_fp64_parity(gd, rd, what="deep")
+    assert_fp64_parity(gs, rs, what="shallow")
+    assert not gd["dTdt"].any() and not gd["dqdt"].any() and not gd["prec"].any()
+    g32 = copy.copy(g)
+    g32.T = g.T.astype(np.float32).astype(np.float64)
+    g32.q = g.q.astype(np.float32).astype(np.float64)
+    r32d, r32s = oracle.deep_shallow(g32, dpar=dpar, threads=THREADS)
+    md, ms_ = run_gpu(g, "mixed", path, deep_params=dp)
+    r = mixed_report(ms_, r32s, layer_mass(g32), same_decisions(md, r32d),
+                     r32d["prec"] + r32s["prec"])
+    check_mixed(r, "shallow")
