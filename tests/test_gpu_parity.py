@@ -86,6 +86,29 @@ def test_other_level_counts(oracle, path, pver):
 
 
 @pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("pver", [4, 8, 26, 32])
+def test_mixed_other_level_counts(oracle, path, pver):
+    """The mixed path at the level counts the ABI accepts besides 30 (its level
+    arrays, in shared memory in the trigger pass, are sized by the level count;
+    on 8 levels a warm-started moist inversion needs up to four Newton steps),
+    within the mixed budget against the FP64 oracle on the mixed path's own
+    FP32 inputs (trace deep precipitation on 8 levels moves by up to 7.9e-4
+    when the oracle's inputs alone are rounded to FP32)."""
+    import copy
+
+    g = S.column_set(4096, seed=7 + pver, pver=pver)
+    g32 = copy.copy(g)
+    g32.T = g.T.astype(np.float32).astype(np.float64)
+    g32.q = g.q.astype(np.float32).astype(np.float64)
+    rd, rs = oracle.deep_shallow(g32, threads=THREADS)
+    md, ms_ = run_gpu(g, "mixed", path)
+    m = layer_mass(g32)
+    psurf = rd["prec"] + rs["prec"]
+    check_mixed(mixed_report(md, rd, m, None, psurf), f"deep pver={pver}")
+    check_mixed(mixed_report(ms_, rs, m, same_decisions(md, rd), psurf), f"shallow pver={pver}")
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_bad_inputs_flagged_and_zeroed(oracle, path):
     g = S.column_set(64, seed=5)
     g.T[3, 1] = np.nan
