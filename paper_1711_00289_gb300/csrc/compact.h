@@ -37,10 +37,11 @@ constexpr int kTriggerBlock = CVG_TRIGGER_BLOCK, kPlumeBlock = CVG_PLUME_BLOCK;
 // 1 both in shared memory, 2 zm in shared memory, 3 dl in shared memory.
 // Measured on the 884,736-column step (trigger / plume pass, ms): 0: 0.473 /
 // 0.383; 1: 0.537 / 0.383 (30 KB per 128-thread block leaves the trigger pass
-// 7 resident blocks per SM); 2: 0.454 / 0.384; 3: 0.446 / 0.384.  With dl in
-// shared memory (15 KB per block, 11 blocks per SM) the trigger pass's local
-// traffic drops; the plume pass, at 7 blocks per SM, already hits L1 on 57% of
-// its local loads and gains nothing.
+// 7 resident blocks per SM); 2: 0.454 / 0.384; 3: 0.446 / 0.384 (measured at
+// 1408 threads per SM).  With dl in shared memory (15 KB per 128-thread block,
+// 10-11 blocks per SM) the trigger pass's local traffic drops; the plume pass,
+// at 7 blocks per SM, already hits L1 on 57% of its local loads and gains
+// nothing.
 #ifndef CVG_SMEM_LEVELS_TRIGGER
 #define CVG_SMEM_LEVELS_TRIGGER 3
 #endif
