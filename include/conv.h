@@ -37,8 +37,12 @@
  *     conservation ratio cons_err from them in FP32 with error-free products;
  *   - shallow rain within 1e-4 kg/kg of the autoconversion threshold: one FP64
  *     correction of the plume's saturation temperature and q_s in FP64;
+ *   - deep updraft condensate within 3e-6 kg/kg of zero: the same FP64
+ *     correction, so that the cloud top and the rain profile are decided as
+ *     in FP64;
  *   - moist inversions: FP32 Newton, warm-started along each vertical sequence
- *     by a tangent predictor, stopping after a correction below 0.01 K;
+ *     by a tangent predictor, at most four steps, stopping after a correction
+ *     below 0.01 K;
  *   - FP32 quotients: PTX div.full.f32, within 2 ulp of IEEE division
  *     (conv_bench_f32_quotient applies it to arrays, for checking).
  * Measured against the FP64 oracle (the tests): trigger flips on at most 0.1%
@@ -189,7 +193,8 @@ typedef struct {
 /* Outputs of one scheme (DEVICE pointers).  dTdt (K/s), dqdt (kg/kg/s):
  * [pver][ld], element type as T.  prec (kg m-2 s-1), cape (deep: CAPE J/kg;
  * shallow: CIN J/kg), mb (cloud-base mass flux, kg m-2 s-1), cons_err (relative
- * column enthalpy + water residual, computed in FP64): [ld] double.  flags and
+ * column enthalpy + water residual; FP64, or in MIXED the compensated FP32
+ * evaluation listed under Precision): [ld] double.  flags and
  * level indices: [ld] int32; kb = launch/source layer, klcl = LCL layer,
  * ktop = cloud-top layer (-1 unless active), kaux = deep: downdraft top layer
  * (-1 unless active) / shallow: LFC layer (-1 if none).

@@ -5,12 +5,16 @@
 //   R = double  the FP64 path: every operation FP64, every Newton solve as the
 //               scheme defines it (fixed LCL count; moist inversions stop on a
 //               1e-7 K convergence test);
-//   R = float   the mixed path: bulk FP32 with FP64 islands for the LCL Newton
-//               iteration (FP32 iterations, then one FP64 Newton correction with
-//               an FP64 residual), the CAPE integral that drives the trigger and
-//               the column conservation sums.  Moist inversions are warm-started
-//               from the previous level's solution by a tangent predictor and take
-//               kWarmSteps Newton steps to FP32 convergence.
+//   R = float   the mixed path: bulk FP32 with FP64 islands where a decision
+//               turns on a small difference: the LCL (FP32 Newton iterations,
+//               then one FP64 Newton correction with an FP64 residual where p_L
+//               lies within kLclBand of a comparison), shallow rain near the
+//               autoconversion threshold (kDrizzleBand) and deep condensate near
+//               zero (kDeepDrizzleBand).  CAPE, CIN and the column conservation
+//               sums add FP32 terms in compensated (TwoSum) arithmetic.  Moist
+//               inversions are warm-started from the previous level's solution
+//               by a tangent predictor and take up to kWarmSteps Newton steps to
+//               FP32 convergence.
 //
 // The schemes (paper Sec. II-A; Alg. 1 deep then shallow; Alg. 2 entrainment and
 // precipitation loops; Alg. 3 shallow early exits with zeroed outputs) follow the
