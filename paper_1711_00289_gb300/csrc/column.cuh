@@ -705,8 +705,10 @@ __device__ __forceinline__ bool in_range(float T, float q) {
 // Heights, log-thicknesses and top limit (shared by both schemes), in the same
 // pass over the profile as the input check: returns false for a column whose
 // ps, T or q is out of range or not finite (CONV_FLAG_BADINPUT), whose derived
-// values are then meaningless and unused.
-template <class R>
+// values are then meaningless and unused.  DL = false keeps the log-thicknesses
+// already in c.dl: they depend on ps alone, so a column whose T and q have
+// been updated (the shallow scheme after the deep one) needs only new heights.
+template <class R, bool DL = true>
 __device__ __forceinline__ bool prologue(R ptl, Column<R>& c) {
   const auto P = c.press();
   const int pver = c.pver;
@@ -729,8 +731,13 @@ __device__ __forceinline__ bool prologue(R ptl, Column<R>& c) {
     ok = ok && in_range(Tk, qk);
     const R tv = virt(Tk, qk);
     const R scale = R(RD / GRAV) * tv;
-    const R dl = Mth<R>::lg(Mth<R>::dv(pi_lo, pi_hi));
-    c.dl[k] = dl;
+    R dl;
+    if constexpr (DL) {
+      dl = Mth<R>::lg(Mth<R>::dv(pi_lo, pi_hi));
+      c.dl[k] = dl;
+    } else {
+      dl = c.dl[k];
+    }
     const R zm = zi + scale * Mth<R>::lg(Mth<R>::dv(pi_lo, pm));
     zi = zi + scale * dl;
     c.zm[k] = zm;

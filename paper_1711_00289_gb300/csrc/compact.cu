@@ -165,8 +165,13 @@ __device__ __forceinline__ void plume_body(const RunArgs& a, const CompactWs<R>&
   store_deep_scalars(a, i, o);
   if (!(a.mode & MODE_SHALLOW) || kThreePass) return;
   c.s = after_deep_src<R>(a, i, false);  // limiter keeps q >= q_min up to rounding
+  // Same ps, so the deep prologue's log-thicknesses stand: only the heights are
+  // rebuilt.  An updated state out of range leaves the full check to the scheme,
+  // which flags the column as bad input.
+  const ShalQ<R>& SQ = shal_q(a, R(0));
+  const bool ok = prologue<R, false>(SQ.p_top_lim, c);
   ShalOut s;
-  shallow_column(a.sp, shal_q(a, R(0)), c, s, out_col<R, EXT>(a.os, a, i));
+  shallow_column(a.sp, SQ, c, s, out_col<R, EXT>(a.os, a, i), (const ShallowSeed<R>*)nullptr, ok);
   store_shallow_scalars(a, i, s);
 }
 
