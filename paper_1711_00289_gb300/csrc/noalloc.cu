@@ -39,11 +39,14 @@ Cached g_cache[kMaxDevices] = {};
 unsigned long long current_context_id() {
   using GetCurrent = CUresult (*)(CUcontext*);
   using GetId = CUresult (*)(CUcontext, unsigned long long*);
-  static GetCurrent get_current = nullptr;
-  static GetId get_id = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  struct Entry {
+    GetCurrent get_current = nullptr;
+    GetId get_id = nullptr;
+  };
+  // looked up once, by the first caller (a function-local static's
+  // initialisation is thread-safe)
+  static const Entry e = [] {
+    Entry r;
     void* f1 = nullptr;
     void* f2 = nullptr;
     cudaDriverEntryPointQueryResult q1, q2;
@@ -53,14 +56,15 @@ unsigned long long current_context_id() {
         cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
             cudaSuccess &&
         q2 == cudaDriverEntryPointSuccess) {
-      get_current = reinterpret_cast<GetCurrent>(f1);
-      get_id = reinterpret_cast<GetId>(f2);
+      r.get_current = reinterpret_cast<GetCurrent>(f1);
+      r.get_id = reinterpret_cast<GetId>(f2);
     }
-  }
-  if (!get_current || !get_id) return 0;
+    return r;
+  }();
+  if (!e.get_current || !e.get_id) return 0;
   CUcontext ctx = nullptr;
   unsigned long long id = 0;
-  if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  if (e.get_current(&ctx) != CUDA_SUCCESS || !ctx || e.get_id(ctx, &id) != CUDA_SUCCESS) return 0;
   return id;
 }
 
