@@ -419,12 +419,29 @@ def ours_arm(args, rank, world, local_rank):
                     statistics.mean(e[1].elapsed_time(e[2]) for e in evs))
         return ms, kern
 
+    def soak(grid, prec, path, seconds):
+        # the step run untimed for `seconds` right before the timed steps, so
+        # that the clock samples (nvidia-smi every 100 ms, longer than a short
+        # timed region) see the GPU under this load; returns the steps run
+        run = prepared(grid, prec, path)
+        n = 0
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            for _ in range(20):
+                run()
+            torch.cuda.synchronize()
+            n += 20
+        return n
+
     prec, path = args.precision, args.path
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.3)
+    n_soak = soak(g, prec, path, 0.6)
     ms, kern = timed(g, prec, path, args.steps, args.warmup, True)
     clk = clocks.stop()
+    clk["window"] = ("nvidia-smi every 100 ms from 0.3 s before a 0.6 s untimed run "
+                     f"of the same step ({n_soak} steps) through the warm-up and timed steps")
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_value(world, n, ms)
     od = setup(g, prec)[3]
