@@ -69,6 +69,25 @@ def test_partition_balances_better_than_an_even_split():
     assert abs(work(bal)[0] - work(bal)[1]) <= c.max()
 
 
+@pytest.mark.parametrize("n,block,parts", [(1000, 128, 4), (884736, 1024, 8), (100, 128, 4),
+                                          (0, 128, 2), (1024, 128, 8), (1024, 128, 16)])
+def test_partition_degenerate_cases(n, block, parts):
+    """No convection anywhere: the split is by columns alone, each bound the
+    block boundary nearest its share.  More ranks than blocks, or no columns:
+    the ranges still tile [0, n) in order, the surplus ranks empty."""
+    nb = -(-n // block)
+    b = shard.partition(np.zeros(nb, np.int32), n, parts, block=block)
+    assert b.shape == (parts + 1,) and b[0] == 0 and b[-1] == n and np.all(np.diff(b) >= 0)
+    assert np.all((b[1:-1] % block == 0) | (b[1:-1] == n))
+    edges = np.minimum(np.arange(nb + 1) * block, n)
+    for r in range(1, parts):
+        target = n * r / parts
+        assert abs(b[r] - target) <= np.min(np.abs(edges - target)) + 1e-9
+    assert int(np.count_nonzero(np.diff(b))) <= nb
+    if n % block == 0 and nb % parts == 0:  # an exact split: equal ranges
+        assert np.all(np.diff(b) == n // parts)
+
+
 @pytest.mark.parametrize("kw", [dict(n_cols=-1), dict(block=0), dict(n_parts=0),
                                 dict(w_all=0.0, w_active=0.0), dict(w_all=-1.0),
                                 dict(count=200), dict(count=-1)])
